@@ -1,0 +1,432 @@
+"""FP64 CPU oracle of the Fast-Grasp'D grasp-search step.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / reference leg of ``bench.py`` may import or call this module.
+The product (the CUDA library and its Python binding) never does, and shares no
+code with it: the two meet only through the seeded inputs of ``synth``.
+
+What it computes, step by step, in the paper's order (Sec. III-C, Sec. IV-A):
+
+  FK        p = FK(q_h): base pose (t, w) with R_b = Exp(w), then for every link
+            T_l = T_parent(l) * T_fix_l * Rot(a_l, theta_j(l)); points p_i = R_l s_i + t_l.
+  SDF       trilinear interpolation of a voxel grid (the Grasp'D representation of
+            Sec. III-A), with the analytic gradient of the interpolant, an excess
+            distance outside the grid, and dilation phi_hat = phi - r (Sec. III-B).
+  PBD       M = 7 one-step simulations with test velocities 0, +-x, +-y, +-z (Sec. IV-A);
+            object at its canonical pose; each hand point gives the constraint
+            C = max(0, -phi) (Sec. III-C) on the plane through the query, and the
+            single-constraint projection of Eq. (1) with J = [n^T, (d x n)^T];
+            Coulomb friction at position level; corrections averaged over the
+            active contacts (Jacobi reading of the Gauss-Seidel step).
+  Loss      L_stable of Eq. (2), L_range (Eq. 3), L_limit (Eq. 4) and an optional
+            penetration sum; L = L_stable + w_r L_range + w_l L_limit + w_pen L_pen.
+  Gradient  reverse mode (torch autograd in float64) with the paper's leaky rule:
+            dC/dphi = -1 in contact and -alpha outside (Sec. III-C, "Leaky gradient").
+  Update    q <- q - lr * dL/dq (Sec. IV-A); dilation r decreases linearly to 0.
+
+Every branch the method takes (clamp side, voxel cell, contact flag, friction
+regime, zero norms, active joint limits) is a recorded *decision*.  ``evaluate``
+either takes decisions from the current values (the method itself) or is handed a
+frozen set, which turns the loss into one smooth piece; finite differences of that
+piece pin the autograd gradient, including the leaky part (see ``tests``).
+"""
+
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+F64 = torch.float64
+
+# Sec. IV-A: zero velocity plus positive and negative velocity along each axis.
+TEST_DIRECTIONS = ((0, 0, 0), (1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1))
+M_SIMS = len(TEST_DIRECTIONS)
+
+
+# ----------------------------------------------------------------------------- inputs
+
+@dataclass
+class Hand:
+    L: int
+    J: int
+    D: int
+    P: int
+    parent: list
+    T_fix: torch.Tensor        # [L,3,4]
+    axis: torch.Tensor         # [L,3]
+    q_low: torch.Tensor        # [J]
+    q_up: torch.Tensor         # [J]
+    s: torch.Tensor            # [P,3] link-local points
+    link: torch.Tensor         # [P] long
+
+    @staticmethod
+    def from_synth(h: dict) -> "Hand":
+        t = lambda a: torch.as_tensor(np.asarray(a, dtype=np.float64))
+        return Hand(h["L"], h["J"], h["D"], h["P"], [int(v) for v in h["parent"]],
+                    t(h["T_fix"]), t(h["axis"]), t(h["q_low"]), t(h["q_up"]),
+                    t(h["pts_local"]), torch.as_tensor(h["link_of_point"]).long())
+
+
+@dataclass
+class Obj:
+    grid: torch.Tensor         # [nz,ny,nx] float64
+    origin: torch.Tensor       # [3]
+    pitch: float
+    dims: tuple                # (nx, ny, nz)
+    inv_mass: float
+    inv_inertia: float
+
+    @staticmethod
+    def from_synth(o: dict) -> "Obj":
+        g = o["grid"].detach().to("cpu", F64)
+        nz, ny, nx = g.shape
+        return Obj(g, torch.as_tensor(np.asarray(o["origin"], dtype=np.float64)),
+                   float(o["pitch"]), (nx, ny, nz), 1.0 / float(o["mass"]), 1.0 / float(o["inertia"]))
+
+
+@dataclass
+class Params:
+    alpha_leak: float = 0.1
+    dt: float = 1e-3
+    v_test: float = 1.0
+    mu: float = 0.5
+    lr: float = 1e-3
+    r0: float = 0.004
+    w_range: float = 0.1
+    w_limit: float = 1.0
+    w_pen: float = 0.0
+    schedule: str = "fixed"
+
+    @staticmethod
+    def from_dict(d: dict) -> "Params":
+        keys = Params.__dataclass_fields__.keys()
+        return Params(**{k: d[k] for k in keys if k in d})
+
+
+def dilation_radius(p: Params, step: int, total_steps: int) -> float:
+    """Sec. III-B: the surface is the r-level set and r decreases linearly to 0.
+    Reading: r_k = r0 * max(0, 1 - k / (K - 1)) over a K-step run ("linear"), or a
+    constant r0 ("fixed")."""
+    if p.schedule == "fixed":
+        return p.r0
+    return p.r0 * max(0.0, 1.0 - step / max(total_steps - 1, 1))
+
+
+# ----------------------------------------------------------------------------- FK
+
+def skew(w: torch.Tensor) -> torch.Tensor:
+    z = torch.zeros_like(w[..., 0])
+    return torch.stack([torch.stack([z, -w[..., 2], w[..., 1]], -1),
+                        torch.stack([w[..., 2], z, -w[..., 0]], -1),
+                        torch.stack([-w[..., 1], w[..., 0], z], -1)], -2)
+
+
+def so3_exp(w: torch.Tensor) -> torch.Tensor:
+    """Rodrigues: Exp(w) = I + sin(a)/a [w]x + (1 - cos a)/a^2 [w]x^2, a = |w|;
+    the series I + [w]x + [w]x^2/2 below |w| = 1e-8."""
+    a2 = (w * w).sum(-1)
+    small = a2 < 1e-16
+    a = torch.sqrt(torch.where(small, torch.ones_like(a2), a2))
+    c1 = torch.where(small, 1.0 - a2 / 6.0, torch.sin(a) / a)
+    c2 = torch.where(small, 0.5 - a2 / 24.0, (1.0 - torch.cos(a)) / (a * a))
+    K = skew(w)
+    eye = torch.eye(3, dtype=w.dtype).expand(K.shape)
+    return eye + c1[..., None, None] * K + c2[..., None, None] * (K @ K)
+
+
+def axis_rotation(axis: torch.Tensor, theta: torch.Tensor) -> torch.Tensor:
+    """Rotation by theta about the unit axis (Rodrigues with a unit axis)."""
+    K = skew(axis).expand(theta.shape + (3, 3))
+    eye = torch.eye(3, dtype=theta.dtype).expand(K.shape)
+    return eye + torch.sin(theta)[..., None, None] * K + (1.0 - torch.cos(theta))[..., None, None] * (K @ K)
+
+
+def forward_kinematics(hand: Hand, q: torch.Tensor):
+    """Link frames for q = (t, w, theta): returns R [B,L,3,3], o [B,L,3] (Sec. III-C, p = FK(q_h))."""
+    t, w, th = q[:, 0:3], q[:, 3:6], q[:, 6:]
+    Rs, os_ = [so3_exp(w)], [t]
+    for l in range(1, hand.L):
+        par = hand.parent[l]
+        Rf, tf = hand.T_fix[l, :, :3], hand.T_fix[l, :, 3]
+        Rj = axis_rotation(hand.axis[l], th[:, l - 1])
+        Rs.append(Rs[par] @ Rf @ Rj)
+        os_.append(os_[par] + (Rs[par] @ tf[:, None])[..., 0])
+    return torch.stack(Rs, 1), torch.stack(os_, 1)
+
+
+def hand_points(hand: Hand, R: torch.Tensor, o: torch.Tensor) -> torch.Tensor:
+    """p_i = R_l(i) s_i + o_l(i) for all points: [B,P,3]."""
+    Rl, ol = R[:, hand.link], o[:, hand.link]
+    return (Rl @ hand.s[None, :, :, None])[..., 0] + ol
+
+
+# ----------------------------------------------------------------------------- SDF
+
+def _safe_norm(x: torch.Tensor, nonzero: torch.Tensor):
+    sq = (x * x).sum(-1)
+    return torch.where(nonzero, torch.sqrt(torch.where(nonzero, sq, torch.ones_like(sq))),
+                       torch.zeros_like(sq))
+
+
+def sdf_decisions(obj: Obj, p: torch.Tensor) -> dict:
+    """Branches of the grid lookup: per axis clamped below/above, and the cell index
+    i0 = min(floor(clamp(u, 0, n-1)), n-2)."""
+    with torch.no_grad():
+        n = torch.tensor(obj.dims, dtype=F64)
+        u = (p - obj.origin) / obj.pitch
+        lo, hi = u < 0, u > n - 1
+        uc = torch.minimum(torch.maximum(u, torch.zeros_like(u)), n - 1)
+        i0 = torch.minimum(torch.floor(uc), n - 2).long()
+    return {"lo": lo, "hi": hi, "i0": i0}
+
+
+def sdf_eval(obj: Obj, p: torch.Tensor, dec: dict):
+    """phi and its gradient for given branch decisions (Sec. III-A grid + trilinear).
+
+    u = (p - origin)/h; u_c = u clamped into [0, n-1] (per the decisions);
+    f = u_c - i0; phi = trilinear(G, i0, f) + h |u - u_c|;
+    grad = (1/h) d trilinear/d f on unclamped axes + (u - u_c)/|u - u_c| outside."""
+    n = torch.tensor(obj.dims, dtype=F64)
+    h = obj.pitch
+    u = (p - obj.origin) / h
+    lo, hi, i0 = dec["lo"], dec["hi"], dec["i0"]
+    uc = torch.where(lo, torch.zeros_like(u), torch.where(hi, (n - 1).expand_as(u), u))
+    du = u - uc
+    outside = lo.any(-1) | hi.any(-1)
+    e = h * _safe_norm(du, outside)
+    f = uc - i0.to(F64)
+    ix, iy, iz = i0[..., 0], i0[..., 1], i0[..., 2]
+    G = obj.grid
+    val = torch.zeros_like(f[..., 0])
+    dval = [torch.zeros_like(val) for _ in range(3)]
+    for a in (0, 1):
+        for b in (0, 1):
+            for c in (0, 1):
+                corner = G[iz + c, iy + b, ix + a]
+                wx = f[..., 0] if a else 1.0 - f[..., 0]
+                wy = f[..., 1] if b else 1.0 - f[..., 1]
+                wz = f[..., 2] if c else 1.0 - f[..., 2]
+                sx, sy, sz = (1.0 if a else -1.0), (1.0 if b else -1.0), (1.0 if c else -1.0)
+                val = val + wx * wy * wz * corner
+                dval[0] = dval[0] + sx * wy * wz * corner
+                dval[1] = dval[1] + wx * sy * wz * corner
+                dval[2] = dval[2] + wx * wy * sz * corner
+    interior = ~(lo | hi)
+    g_tri = torch.stack(dval, -1) / h * interior.to(F64)
+    den = _safe_norm(du, outside)[..., None]
+    g_out = torch.where(outside[..., None], du / torch.where(outside[..., None], den, torch.ones_like(den)),
+                        torch.zeros_like(du))
+    return val + e, g_tri + g_out
+
+
+def sdf_query(obj: Obj, p: torch.Tensor, r: float):
+    """Dilated SDF phi_hat = phi - r (Sec. III-B) and the gradient of phi, for points p [...,3]."""
+    phi, grad = sdf_eval(obj, p, sdf_decisions(obj, p))
+    return phi - r, grad
+
+
+# ----------------------------------------------------------------------------- step
+
+@dataclass
+class Decisions:
+    sdf: dict = None
+    grad_nz: torch.Tensor = None     # [B,P]   |grad phi| > 0
+    kappa: torch.Tensor = None       # [B,P,M] contact flag phi_m < 0
+    has_t: torch.Tensor = None       # [B,P,M] tangential displacement sigma > 0
+    static: torch.Tensor = None      # [B,P,M] sigma <= mu C
+    anchor: torch.Tensor = None      # [B,P,M] phi_m at the decision state (leak surrogate)
+    v_nz: torch.Tensor = None        # [B,M]   |x_dot+| > 0
+    w_nz: torch.Tensor = None        # [B,M]   |theta_dot+| > 0
+    range_nz: torch.Tensor = None    # [B]     |theta - mid| > 0
+    above: torch.Tensor = None       # [B,J]   theta > q_up
+    below: torch.Tensor = None       # [B,J]   theta < q_low
+    ncontact: torch.Tensor = None    # [B,M]   N_m (a constant in the gradient)
+
+
+def _cross(a, b):
+    return torch.linalg.cross(a, b, dim=-1)
+
+
+def _dot(a, b):
+    return (a * b).sum(-1)
+
+
+def evaluate(hand: Hand, obj: Obj, q: torch.Tensor, r: float, prm: Params,
+             dec: Decisions | None = None, anchor_mode: bool = False) -> dict:
+    """One grasp-metric evaluation for a batch of candidates on one object.
+
+    With ``dec=None`` every decision is taken from the current values (the method).
+    With a frozen ``dec`` the same arithmetic is evaluated on that branch; with
+    ``anchor_mode`` non-contact constraints use C = -alpha (phi_m - anchor), whose
+    value is 0 at the anchor state and whose slope is the leaky -alpha.
+    Returns a dict of per-candidate tensors and the decisions used."""
+    take = dec is None
+    if take:
+        dec = Decisions()
+    B = q.shape[0]
+    R, o = forward_kinematics(hand, q)
+    p = hand_points(hand, R, o)                                      # [B,P,3]
+    if take:
+        dec.sdf = sdf_decisions(obj, p)
+    phi, grad = sdf_eval(obj, p, dec.sdf)
+    phi_hat = phi - r
+    if take:
+        dec.grad_nz = (grad.detach() * grad.detach()).sum(-1) > 0
+    gnorm = _safe_norm(grad, dec.grad_nz)
+    nrm = grad / torch.where(dec.grad_nz, gnorm, torch.ones_like(gnorm))[..., None]
+
+    V = torch.tensor(TEST_DIRECTIONS, dtype=F64) * prm.v_test         # [M,3]
+    v = V[None, None]                                                 # [1,1,M,3]
+    x_pred = prm.dt * v                                               # symplectic Euler, x^- = 0
+    n_ = nrm[:, :, None, :]                                           # [B,P,1,3]
+    p_ = p[:, :, None, :]
+    # constraint on the plane through the query: phi(p - x_pred) ~ phi_hat - n . x_pred
+    phi_m = phi_hat[..., None] - _dot(n_, x_pred)                     # [B,P,M]
+    if take:
+        dec.kappa = phi_m.detach() < 0
+    if anchor_mode:
+        anchor = dec.anchor
+    else:
+        anchor = phi_m.detach()
+        if take:
+            dec.anchor = anchor
+    alpha = prm.alpha_leak
+    # C = max(0, -phi_m); outside contact the value is 0 and the slope is -alpha
+    C = torch.where(dec.kappa, -phi_m, -alpha * (phi_m - anchor))
+    d = p_ - x_pred                                                   # lever arm from the object centre
+    u_n = _cross(d, n_.expand_as(d))
+    w_n = obj.inv_mass + obj.inv_inertia * _dot(u_n, u_n)        # J M^-1 J^T, Eq. (1)
+    lam_n = C / w_n
+    s = prm.dt * (v - _dot(v, n_)[..., None] * n_)                    # tangential displacement
+    if take:
+        dec.has_t = (s.detach() * s.detach()).sum(-1) > 0
+    sig = _safe_norm(s, dec.has_t)
+    t_hat = s / torch.where(dec.has_t, sig, torch.ones_like(sig))[..., None]
+    u_t = _cross(d, t_hat)
+    w_t = obj.inv_mass + obj.inv_inertia * _dot(u_t, u_t)
+    if take:
+        dec.static = sig.detach() <= prm.mu * C.detach()
+    lam_t = torch.where(dec.has_t, torch.where(dec.static, sig, prm.mu * C) / w_t, torch.zeros_like(sig))
+    f = -(lam_n[..., None] * n_ + lam_t[..., None] * t_hat)          # [B,P,M,3]
+    W_lin = f.sum(1)                                                  # [B,M,3]
+    W_ang = _cross(d, f).sum(1)
+    if take:
+        dec.ncontact = dec.kappa.sum(1).to(F64)                       # [B,M]
+    Nc = torch.clamp(dec.ncontact, min=1.0)
+    dx = W_lin * obj.inv_mass / Nc[..., None]                         # averaged position correction
+    dth = W_ang * obj.inv_inertia / Nc[..., None]
+    xdot = V[None] + dx / prm.dt                                      # x_dot+ = (x+ - x-)/dt
+    thdot = dth / prm.dt
+    if take:
+        dec.v_nz = (xdot.detach() ** 2).sum(-1) > 0
+        dec.w_nz = (thdot.detach() ** 2).sum(-1) > 0
+    L_stable = (_safe_norm(xdot, dec.v_nz) + _safe_norm(thdot, dec.w_nz)).sum(-1) / M_SIMS   # Eq. (2)
+
+    th = q[:, 6:]
+    mid = 0.5 * (hand.q_up + hand.q_low)
+    if take:
+        dec.range_nz = ((th.detach() - mid) ** 2).sum(-1) > 0
+        dec.above = th.detach() > hand.q_up
+        dec.below = th.detach() < hand.q_low
+    L_range = _safe_norm(th - mid, dec.range_nz)                                             # Eq. (3)
+    L_limit = (torch.where(dec.above, th - hand.q_up, torch.zeros_like(th)) +
+               torch.where(dec.below, hand.q_low - th, torch.zeros_like(th))).sum(-1)        # Eq. (4)
+    L_pen = C[..., 0].sum(-1)
+    L = L_stable + prm.w_range * L_range + prm.w_limit * L_limit + prm.w_pen * L_pen
+    return {"L": L, "L_stable": L_stable, "L_range": L_range, "L_limit": L_limit, "L_pen": L_pen,
+            "W": torch.cat([W_lin, W_ang], -1), "N": dec.ncontact, "kappa": dec.kappa,
+            "points": p, "phi_hat": phi_hat, "grad_phi": grad, "phi_m": phi_m, "C": C,
+            "sigma": sig, "dec": dec}
+
+
+def loss_and_grad(hand: Hand, obj: Obj, q32, r: float, prm: Params, alpha=None):
+    """Loss, gradient dL/dq (leaky rule) and the forward outputs for candidates q [B,D]."""
+    if alpha is not None:
+        prm = Params(**{**prm.__dict__, "alpha_leak": alpha})
+    q = torch.as_tensor(np.asarray(q32, dtype=np.float64)).clone().requires_grad_(True)
+    out = evaluate(hand, obj, q, r, prm)
+    (g,) = torch.autograd.grad(out["L"].sum(), q)
+    out["grad"] = g
+    return out
+
+
+# ----------------------------------------------------------------------------- driver
+
+class Setup:
+    """Hand, objects and parameters of one workload, converted for the oracle."""
+
+    def __init__(self, hand: dict, objects: list, params: dict):
+        self.hand = Hand.from_synth(hand)
+        self.objs = [Obj.from_synth(o) for o in objects]
+        self.prm = Params.from_dict(params)
+
+
+def batch_loss_and_grad(setup: Setup, q32: np.ndarray, obj_of_cand: np.ndarray, r: float,
+                        chunk: int = 8) -> dict:
+    """loss_and_grad over a mixed-object batch, processed per object in small chunks."""
+    B = q32.shape[0]
+    res = {"L": np.zeros(B), "grad": np.zeros((B, setup.hand.D)), "W": np.zeros((B, M_SIMS, 6)),
+           "N": np.zeros((B, M_SIMS)), "kappa": np.zeros((B, setup.hand.P, M_SIMS), dtype=bool),
+           "L_stable": np.zeros(B)}
+    for k in np.unique(obj_of_cand):
+        idx = np.nonzero(obj_of_cand == k)[0]
+        for s in range(0, len(idx), chunk):
+            sel = idx[s:s + chunk]
+            out = loss_and_grad(setup.hand, setup.objs[int(k)], q32[sel], r, setup.prm)
+            res["L"][sel] = out["L"].detach().numpy()
+            res["L_stable"][sel] = out["L_stable"].detach().numpy()
+            res["grad"][sel] = out["grad"].numpy()
+            res["W"][sel] = out["W"].detach().numpy()
+            res["N"][sel] = out["N"].numpy()
+            res["kappa"][sel] = out["kappa"].numpy()
+    return res
+
+
+def optimize(setup: Setup, q32: np.ndarray, obj_of_cand: np.ndarray, step0: int, nsteps: int,
+             total_steps: int, round_to_f32: bool = False) -> tuple[np.ndarray, np.ndarray]:
+    """nsteps of gradient descent q <- q - lr dL/dq (Sec. IV-A).  Returns (q, loss at
+    the last step before its update)."""
+    q = np.asarray(q32, dtype=np.float64).copy()
+    last = None
+    for k in range(step0, step0 + nsteps):
+        r = dilation_radius(setup.prm, k, total_steps)
+        res = batch_loss_and_grad(setup, q, obj_of_cand, r)
+        q = q - setup.prm.lr * res["grad"]
+        if round_to_f32:
+            q = q.astype(np.float32).astype(np.float64)
+        last = res["L"]
+    return q, last
+
+
+# ----------------------------------------------------------------------------- guard band
+
+def guard_margins(hand: Hand, obj: Obj, q32, r: float, prm: Params) -> dict:
+    """Distances of every decision from its threshold, per candidate (minimum over
+    points): voxel faces / clamp planes (in voxels), |phi_m| for the contact flag
+    (metres), |sigma - mu C| for the friction regime of contact points (metres) and
+    sigma / (dt V) = sin(angle between n and v_m) for the moving simulations, where a
+    normal nearly parallel to the test velocity leaves the friction direction
+    ill-conditioned."""
+    with torch.no_grad():
+        q = torch.as_tensor(np.asarray(q32, dtype=np.float64))
+        out = evaluate(hand, obj, q, r, prm)
+        u = (out["points"] - obj.origin) / obj.pitch
+        face = (u - torch.round(u)).abs().amin(dim=(-1, -2))
+        phim = out["phi_m"].abs().amin(dim=(-1, -2))
+        kap = out["kappa"]
+        fr = (out["sigma"] - prm.mu * out["C"]).abs()
+        fr = torch.where(kap & out["dec"].has_t, fr, torch.full_like(fr, float("inf"))).amin(dim=(-1, -2))
+        par = (out["sigma"][..., 1:] / (prm.dt * prm.v_test)).amin(dim=(-1, -2))
+    return {"face": face.numpy(), "phi": phim.numpy(), "friction": fr.numpy(), "parallel": par.numpy()}
+
+
+def clean_candidates(hand: Hand, obj: Obj, q32, r: float, prm: Params, face_tol: float = 1e-5,
+                     phi_tol: float = 1e-6, fr_tol: float = 1e-6, par_tol: float = 1e-3) -> np.ndarray:
+    """Candidates whose decisions all sit outside the guard band, so that a float32
+    evaluation takes the same branches as this float64 one."""
+    m = guard_margins(hand, obj, q32, r, prm)
+    return ((m["face"] > face_tol) & (m["phi"] > phi_tol) & (m["friction"] > fr_tol)
+            & (m["parallel"] > par_tol))
