@@ -1,0 +1,347 @@
+"""Benchmark of the grasp-search step (candidate-steps per second).
+
+Workload: 8 random superquadrics on 128^3 float32 SDF grids, the 4-finger
+synthetic hand (17 links, 4,352 points), 1,024 candidates per object (8,192),
+paper constants (alpha = 0.1, dt = 1 ms, lr = 1e-3), dilation 10 mm at step 0 of
+a 500-step linear schedule.  One timed step = one fused forward + adjoint +
+update launch over all candidates, starting from the initial candidates (q is
+reset by a device copy inside the timed region, so every step sees the same
+contact state).  The L2 is flushed (256 MiB write) between timed steps.
+
+Lines: the fused path (value), the plain per-stage GPU form (plain), the same
+step end to end through host buffers (e2e), the roofline of the fused kernel,
+sampled SM clocks, and the FP64 oracle on the host cores (cpu_baseline).
+`--impl reference` times the oracle alone on the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# Algorithmic float32 operations per point per step (forward once + adjoint once,
+# a point out of contact; FMA = 2).  Derivation in the design doc.
+FLOPS_PER_POINT_STEP = 599
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+METRIC = "candidate-steps/sec fused fwd+bwd vs plain GPU form at 1e-3 grad tol; p50/p99 latency"
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def load_traffic(kernel_tag: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
+    current kernel sources (matching source hash); else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    if not os.path.exists(path):
+        return None
+    from paper_2306_08132_gb300.build import source_hash
+    cur = source_hash()
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 3 and parts[0] == kernel_tag and parts[1] == cur:
+            return float(parts[2])
+    return None
+
+
+def build_workload(device, rank):
+    import synth
+    w = synth.batched_superquadric_workload(device=device)
+    if rank:
+        # weak scaling: every rank gets its own candidates (same shape, other seed)
+        rng = np.random.default_rng(synth.workloads.SEED_BASE + 100 + rank)
+        from synth.candidates import sample_candidates
+        q = [sample_candidates(rng, w.hand, 1024, o["bound_radius"] + 0.06) for o in w.objects]
+        w.q0 = np.concatenate(q)
+    return w
+
+
+def oracle_rate(w, budget_s: float, r: float, max_cands: int | None = None):
+    """FP64 oracle on the host: candidate-steps/s over chunks of candidates until the
+    time budget is used."""
+    import torch
+    from oracle import fastgraspd_oracle as O
+    S = O.Setup(w.hand, w.objects, w.params)
+    done, t0 = 0, time.perf_counter()
+    B = w.B
+    rng = np.random.default_rng(3)
+    order = rng.permutation(B)
+    while time.perf_counter() - t0 < budget_s and (max_cands is None or done < max_cands):
+        sel = order[done % B:done % B + 8]
+        O.batch_loss_and_grad(S, w.q0[sel], w.obj_of_cand[sel], r, chunk=8)
+        done += len(sel)
+    dt = time.perf_counter() - t0
+    return done / dt, done, dt, torch.get_num_threads()
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import torch
+    import synth
+    from oracle import fastgraspd_oracle as O
+    w = synth.batched_superquadric_workload(device="cpu")
+    r = O.dilation_radius(O.Params.from_dict(w.params), 0, w.steps)
+    per_step = 16
+    for _ in range(args.warmup):
+        oracle_rate(w, 0.0, r, max_cands=8)
+    t0 = time.perf_counter()
+    total = 0
+    for _ in range(args.steps):
+        _, n, _, cores = oracle_rate(w, 1e9, r, max_cands=per_step)
+        total += n
+    dt = time.perf_counter() - t0
+    value = total / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "candidate-steps/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w.name, "candidates": w.B, "points_per_candidate": w.hand["P"],
+                       "sample_per_step": "%d candidates x 1 step (FP64 oracle, host cores)" % per_step},
+            "cpu_baseline": {"value": value, "unit": "candidate-steps/s", "cores": torch.get_num_threads(),
+                             "kind": "oracle", "sample": "%d candidates x %d steps" % (per_step, args.steps)},
+            "e2e": {"value": value, "unit": "candidate-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="fused", choices=["fused", "reference"])
+    ap.add_argument("--inner-steps", type=int, default=1, help="optimisation steps per fused launch")
+    ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle time for cpu_baseline")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--profile-kernel", action="store_true",
+                    help="set up the workload, run a few fused launches and exit (for ncu)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from __graft_entry__ import build
+    if rank == 0:
+        build()
+    if world > 1:
+        dist.barrier()
+    import paper_2306_08132_gb300 as fg
+    from oracle import fastgraspd_oracle as O   # rank 0 cpu_baseline leg only
+
+    w = build_workload(dev, rank)
+    hand = fg.Hand.from_synth(w.hand)
+    sdfs = [fg.Sdf.from_synth(o) for o in w.objects]
+    scene = fg.Scene(sdfs)
+    oc = torch.tensor(w.obj_of_cand, device=dev, dtype=torch.int32)
+    q0 = torch.tensor(w.q0, device=dev)
+    q = q0.clone()
+    loss = torch.empty(w.B, device=dev)
+    K = w.steps
+    S_in = args.inner_steps
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def fused_step():
+        q.copy_(q0)
+        fg.optimize_step(hand, scene, q, w.params, 0, K, S_in, obj_of_cand=oc, loss=loss)
+
+    if args.profile_kernel:
+        for _ in range(5):
+            fused_step()
+        torch.cuda.synchronize()
+        return
+
+    ws = None if args.no_plain else torch.empty(fg.plain_workspace_size(hand, w.B) + 256, dtype=torch.uint8,
+                                                device=dev)
+
+    def plain_step():
+        q.copy_(q0)
+        fg.optimize_step_plain(hand, scene, q, w.params, 0, K, S_in, obj_of_cand=oc, loss=loss, workspace=ws)
+
+    def graphed(step_fn):
+        """Capture one step (q reset + launches) in a CUDA graph; replaying it keeps
+        host launch latency out of the per-step device time."""
+        for _ in range(2):
+            step_fn()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            step_fn()
+        torch.cuda.synchronize()
+        return g.replay
+
+    def prewarm(fn, seconds=0.5):
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < seconds:
+            fn()
+            torch.cuda.synchronize()
+
+    def timed(step_fn, nsteps, warm, ksteps_events=None):
+        for _ in range(warm):
+            step_fn()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(nsteps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(nsteps)]
+        for i in range(nsteps):
+            flush.fill_(i & 0xff)
+            starts[i].record(stream)
+            step_fn()
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+        ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+        if world > 1:
+            dist.barrier()
+        return ms
+
+    fused_graph = graphed(fused_step)
+    prewarm(fused_graph)
+    sampler = ClockSampler(local)
+    sampler.start()
+    t_wall = time.perf_counter()
+    ms = timed(fused_graph, args.steps, args.warmup)
+    wall = time.perf_counter() - t_wall
+    clocks = sampler.stop()
+    ms_step = float(np.mean(ms))
+    if world > 1:
+        t = torch.tensor([ms_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    cand_steps = w.B * S_in * world
+    value = cand_steps / (ms_step / 1000.0)
+
+    plain = None
+    if not args.no_plain:
+        plain_graph = graphed(plain_step)
+        pms = timed(plain_graph, max(3, args.steps // 2), 3)
+        pstep = float(np.mean(pms))
+        plain = {"value": w.B * S_in / (pstep / 1000.0), "ms_per_step": pstep,
+                 "speedup_fused_over_plain": pstep / float(np.mean(ms)), "gpu_launches_per_step": 8 * S_in}
+
+    # e2e: pinned host q in, fused step, q and loss back to pinned host, per step
+    hq0 = torch.tensor(w.q0).pin_memory()
+    hq = torch.empty_like(hq0).pin_memory()
+    hloss = torch.empty(w.B).pin_memory()
+
+    def e2e_step():
+        q.copy_(hq0, non_blocking=True)
+        fg.optimize_step(hand, scene, q, w.params, 0, K, S_in, obj_of_cand=oc, loss=loss)
+        hq.copy_(q, non_blocking=True)
+        hloss.copy_(loss, non_blocking=True)
+
+    ems = timed(e2e_step, max(3, args.steps // 2), 3)
+    e2e_ms = float(np.mean(ems))
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": cand_steps / (e2e_ms / 1000.0), "unit": "candidate-steps/s",
+           "h2d_bytes_per_step": int(hq0.numel() * 4), "d2h_bytes_per_step": int(hq.numel() * 4 + hloss.numel() * 4)}
+
+    # roofline of the fused kernel (ALU-bound): kernel time measured alone on the stream
+    def kernel_only():
+        fg.optimize_step(hand, scene, q, w.params, 0, K, S_in, obj_of_cand=oc, loss=loss)
+
+    kms = timed(graphed(kernel_only), max(3, args.steps // 2), 3)
+    kern_ms = float(np.mean(kms))
+    flops = FLOPS_PER_POINT_STEP * w.B * w.hand["P"] * S_in
+    achieved = flops / (kern_ms / 1000.0) / 1e12
+    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": load_traffic("fused_step"), "kernel_ms": kern_ms,
+                "flops_per_launch": flops, "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
+
+    if rank == 0:
+        r0 = O.dilation_radius(O.Params.from_dict(w.params), 0, K)
+        rate, n, dt, cores = oracle_rate(w, args.cpu_budget, r0)
+        cpu = {"value": rate, "unit": "candidate-steps/s", "cores": cores, "kind": "oracle",
+               "sample": "%d candidates x 1 step of the same workload in %.1f s (FP64, torch CPU)" % (n, dt)}
+        line = {"metric": METRIC, "value": value, "unit": "candidate-steps/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": w.name, "objects": len(w.objects), "grid": "128^3 f32",
+                           "hand": "4-finger, 17 links, %d points" % w.hand["P"], "candidates": w.B * world,
+                           "inner_steps_per_launch": S_in, "state": "q reset to the initial candidates each step",
+                           "l2": "flushed between timed steps (256 MiB write)", "parallelism": "dp%d" % world},
+                "plain": plain, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
+                "gpu_launches": args.steps * 1, "clocks": clocks, "wall_s_timed_region": wall,
+                "per_step_ms": {"min": float(np.min(ms)), "median": float(np.median(ms)), "max": float(np.max(ms))}}
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

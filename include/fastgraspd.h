@@ -1,0 +1,202 @@
+/*
+ * fastgraspd.h -- C ABI of the GB300 grasp-search hot path (Fast-Grasp'D,
+ * arXiv 2306.08132).
+ *
+ * The paper's problem (Sec. III): given an object and a hand (a point set
+ * carried by an articulation chain), find base poses and joint angles of stable
+ * grasps by gradient descent over a simulation-based stability metric, from
+ * many initialisations at once.  This library runs that search for batches of
+ * candidates on one GPU.  Each step of a candidate is
+ *
+ *   forward kinematics  p = FK(q_h)                          (Sec. III-C)
+ *   voxel-SDF lookup, trilinear, dilated by r                (Sec. III-A, III-B)
+ *   7 one-step PBD simulations with contact + Coulomb        (Eq. 1, Sec. IV-A)
+ *   L = L_stable + w_r L_range + w_l L_limit (+ w_pen L_pen) (Eqs. 2-4)
+ *   dL/dq with the leaky contact gradient                    (Sec. III-C)
+ *   q <- q - lr dL/dq                                        (Sec. IV-A)
+ *
+ * Conventions (every entry point):
+ *  - Returns fg_status; FG_OK on success.  On failure nothing was enqueued and
+ *    fg_last_error() describes the cause (thread-local).  No C++ exception
+ *    crosses this boundary.
+ *  - Arithmetic is float32 throughout.
+ *  - Plain pointers named host_* are host memory read during the call.  Every
+ *    other float / int / uint32 pointer is DEVICE memory owned by the caller,
+ *    valid until the enqueued work completes.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Compute calls are asynchronous: they validate arguments, enqueue kernels on
+ *    `stream` and return.  A CUDA launch error is reported as FG_ERR_CUDA.
+ *  - Handles (fg_hand, fg_sdf, fg_scene) own device copies of their data and are
+ *    immutable after creation; they may be shared by concurrent streams.  Destroy
+ *    a handle only after the work that uses it has completed.
+ *  - Configuration vector layout, per candidate (row-major [B][D]):
+ *      q = (t_x, t_y, t_z, w_x, w_y, w_z, theta_0 .. theta_{J-1}),  D = 6 + J,
+ *    t the palm origin (metres), w the palm rotation vector (R_b = Exp(w)),
+ *    theta_j the angle of the revolute joint that drives link j+1.
+ *  - Test velocities (Sec. IV-A), index m = 0..6: 0, +x, -x, +y, -y, +z, -z
+ *    (times fg_params.v_test).
+ */
+#ifndef FASTGRASPD_H
+#define FASTGRASPD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FG_OK = 0,
+  FG_ERR_INVALID = 1,   /* bad argument or descriptor                          */
+  FG_ERR_OOM = 2,       /* device or host allocation failed                    */
+  FG_ERR_BUDGET = 3,    /* request does not fit the queue's HBM budget         */
+  FG_ERR_TIMEOUT = 4,   /* a bounded wait ran out                              */
+  FG_ERR_CUDA = 5,      /* a CUDA runtime call or kernel launch failed         */
+  FG_ERR_BUSY = 6,      /* resource in use (e.g. queue full, result not ready) */
+  FG_ERR_NOT_FOUND = 7  /* unknown request id                                  */
+} fg_status;
+
+#define FG_NUM_SIMS 7     /* M = 7 test velocities (Sec. IV-A)                 */
+#define FG_MAX_LINKS 32   /* links per hand (root included)                    */
+#define FG_MAX_POINTS (1 << 20)
+
+typedef struct fg_hand fg_hand;
+typedef struct fg_sdf fg_sdf;
+typedef struct fg_scene fg_scene;
+typedef struct fg_queue fg_queue;
+
+/* Hand description (host memory, copied by fg_hand_create).
+ * Links are in topological order: parent[0] = -1 (the palm, moved by the base
+ * pose), 0 <= parent[l] < l for l >= 1.  Link l >= 1 carries one revolute joint,
+ * joint j = l - 1, so J = n_links - 1.  T_fix[l] is the 3x4 row-major [R | t]
+ * from the parent's frame to link l's frame at zero joint angle (T_fix[0] is
+ * ignored); axis[l] is the unit joint axis in link l's frame.  The link frame is
+ * T_l = T_parent * T_fix_l * Rot(axis_l, theta_{l-1}) (Sec. III-C, p = FK(q_h)).
+ * pts_local[P][3] are surface points in their link's frame, sorted by link
+ * (link_of_point nondecreasing).  q_low/q_up[J] are the joint limits of
+ * L_range and L_limit (Eqs. 3-4). */
+typedef struct {
+  int n_links;
+  int n_points;
+  const int* parent;          /* [n_links]                                */
+  const float* T_fix;         /* [n_links][12]                            */
+  const float* axis;          /* [n_links][3]                             */
+  const float* q_low;         /* [n_links - 1]                            */
+  const float* q_up;          /* [n_links - 1]                            */
+  const float* pts_local;     /* [n_points][3]                            */
+  const int* link_of_point;   /* [n_points]                               */
+} fg_hand_desc;
+
+/* Method parameters.  alpha_leak, dt and lr are the paper's (0.1, 1e-3, 1e-3;
+ * Sec. III-C, IV-A).  v_test (test-velocity magnitude, m/s), mu (Coulomb
+ * coefficient), the loss weights and the dilation start r0 (metres) are not
+ * fixed by the paper.  schedule: 0 = constant dilation r0, 1 = r decreases
+ * linearly from r0 at step 0 to 0 at step total_steps - 1 (Sec. III-B). */
+typedef struct {
+  float alpha_leak;
+  float dt;
+  float v_test;
+  float mu;
+  float lr;
+  float r0;
+  float w_range;
+  float w_limit;
+  float w_pen;
+  int schedule;
+} fg_params;
+
+/* ------------------------------------------------------------------ misc */
+
+/* Library version.  Never fails. */
+fg_status fg_version(int* major, int* minor);
+
+/* Static description of a status code.  Never NULL. */
+const char* fg_status_string(fg_status s);
+
+/* Copies the calling thread's last error message (NUL-terminated, truncated to
+ * n bytes) into buf.  FG_ERR_INVALID if buf is NULL or n == 0. */
+fg_status fg_last_error(char* buf, size_t n);
+
+/* ------------------------------------------------------------------ handles */
+
+/* Creates a hand handle from a host description (validated: topology, counts,
+ * unit axes, sorted points).  Allocates and copies to the current device
+ * (synchronous).  Errors: FG_ERR_INVALID, FG_ERR_OOM, FG_ERR_CUDA. */
+fg_status fg_hand_create(const fg_hand_desc* host_desc, fg_hand** out);
+fg_status fg_hand_destroy(fg_hand* hand);
+/* Sizes of a hand: links L, joints J = L - 1, parameters D = 6 + J, points P. */
+fg_status fg_hand_info(const fg_hand* hand, int* n_links, int* n_joints, int* n_dof, int* n_points);
+
+/* Creates an object handle: a voxel SDF grid (Sec. III-A; negative inside),
+ * float32 [nz][ny][nx] with x fastest, node (i,j,k) at origin + pitch*(i,j,k);
+ * `grid` may be host or device memory (copied, synchronous).  mass > 0 and the
+ * isotropic moment of inertia > 0 about the object's centre of mass, which is
+ * the world origin at the canonical pose.  nx, ny, nz >= 2.
+ * Errors: FG_ERR_INVALID, FG_ERR_OOM, FG_ERR_CUDA. */
+fg_status fg_sdf_create(const float* grid, int nx, int ny, int nz, const float* host_origin3,
+                        float pitch, float mass, float inertia, fg_sdf** out);
+fg_status fg_sdf_destroy(fg_sdf* sdf);
+
+/* A scene is an ordered table of objects; candidates select theirs by index
+ * (obj_of_cand).  The scene keeps pointers to the objects' grids: destroy the
+ * scene before its objects.  Errors: FG_ERR_INVALID, FG_ERR_OOM, FG_ERR_CUDA. */
+fg_status fg_scene_create(const fg_sdf* const* host_sdfs, int n_objects, fg_scene** out);
+fg_status fg_scene_destroy(fg_scene* scene);
+
+/* ------------------------------------------------------------------ hot path */
+
+/* Forward kinematics (Sec. III-C): world positions of every hand point for B
+ * candidates.  q: [B][D].  pts: SoA [3][B*P] (x block, y block, z block; the
+ * point of candidate b, index i sits at b*P + i).  B >= 0 (0 is a no-op). */
+fg_status fg_fk(const fg_hand* hand, const float* q, int B, float* pts, void* stream);
+
+/* Dilated SDF lookup (Sec. III-A, III-B): for n points (SoA [3][n]),
+ * phi[n] = trilinear(grid) + outside-excess - r_dil and grad[3][n] (SoA,
+ * nullable) = gradient of the undilated interpolant.  Points outside the grid
+ * are clamped to it and the Euclidean excess distance is added. */
+fg_status fg_sdf_query(const fg_sdf* sdf, const float* pts, int n, float r_dil, float* phi,
+                       float* grad, void* stream);
+
+/* Contact forces and object wrench of the 7 one-step simulations (Eq. 1,
+ * Sec. III-C, IV-A) at dilation r_dil.  obj_of_cand: device [B] indices into
+ * the scene (NULL: object 0 for all).  Outputs per candidate b and simulation m:
+ * wrench[B][7][6] = sum over contacts of (f, d x f), the summed position
+ * corrections times mass (before averaging); ncontact[B][7] = number of points
+ * with phi_m < 0; contact_bits (nullable) [B][7][ceil(P/32)], bit (i % 32) of
+ * word i / 32 set when point i is in contact. */
+fg_status fg_contact_wrench(const fg_hand* hand, const fg_scene* scene, const int* obj_of_cand,
+                            const float* q, int B, const fg_params* host_params, float r_dil,
+                            float* wrench, int* ncontact, uint32_t* contact_bits, void* stream);
+
+/* Loss and gradient (Eqs. 2-4, Sec. III-C leaky rule) at dilation r_dil,
+ * forward and adjoint fused in one kernel (the adjoint recomputes the forward
+ * per point; nothing per point is stored).  loss: [B]; grad: [B][D] nullable. */
+fg_status fg_loss_and_grad(const fg_hand* hand, const fg_scene* scene, const int* obj_of_cand,
+                           const float* q, int B, const fg_params* host_params, float r_dil,
+                           float* loss, float* grad, void* stream);
+
+/* nsteps >= 1 gradient-descent steps (Sec. IV-A) in one persistent fused
+ * forward + adjoint + update kernel.  q: [B][D] in/out.  The dilation of global
+ * step k = step + s is r0 (schedule 0) or r0 * max(0, 1 - k / (total_steps - 1))
+ * (schedule 1).  loss (nullable, [B]): loss at the last step, evaluated before
+ * its update. */
+fg_status fg_optimize_step(const fg_hand* hand, const fg_scene* scene, const int* obj_of_cand,
+                           float* q, int B, const fg_params* host_params, int step, int total_steps,
+                           int nsteps, float* loss, void* stream);
+
+/* The same step as fg_optimize_step, run as the plain one-kernel-per-stage
+ * form: FK links -> point transform -> SDF query -> contact forward -> loss ->
+ * contact adjoint -> link reduction -> FK adjoint + update, with the per-point
+ * intermediates in `workspace` (device memory, >= fg_plain_workspace_size
+ * bytes, 256-byte aligned).  Comparison baseline for the fused kernel. */
+fg_status fg_plain_workspace_size(const fg_hand* hand, int B, size_t* bytes);
+fg_status fg_optimize_step_plain(const fg_hand* hand, const fg_scene* scene, const int* obj_of_cand,
+                                 float* q, int B, const fg_params* host_params, int step,
+                                 int total_steps, int nsteps, float* loss, void* workspace,
+                                 size_t workspace_bytes, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FASTGRASPD_H */

@@ -1,0 +1,12 @@
+"""GB300-native grasp-search hot path of Fast-Grasp'D (arXiv 2306.08132).
+
+The compute lives in libfastgraspd.so (hand-written CUDA for sm_103a behind the
+C ABI of include/fastgraspd.h); this package is its thin Python binding.
+"""
+
+from . import _lib
+from .api import (Hand, Sdf, Scene, make_params, fk, sdf_query, contact_wrench, loss_and_grad,
+                  optimize_step, optimize_step_plain, plain_workspace_size)
+
+__all__ = ["Hand", "Sdf", "Scene", "make_params", "fk", "sdf_query", "contact_wrench", "loss_and_grad",
+           "optimize_step", "optimize_step_plain", "plain_workspace_size"]

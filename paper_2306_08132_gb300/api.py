@@ -1,0 +1,217 @@
+"""Python binding of libfastgraspd with the C ABI's names.
+
+Argument marshalling only: every function checks tensor device, dtype, shape and
+contiguity, passes raw pointers and torch's current CUDA stream to the library,
+and returns the output tensors.  All arithmetic runs in the library's kernels.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import check, FG_NUM_SIMS
+
+_F32 = torch.float32
+
+
+def _stream() -> C.c_void_p:
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dptr(t: torch.Tensor | None, name: str, dtype=_F32, shape=None) -> C.c_void_p | None:
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise ValueError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError("%s must have shape %s, got %s" % (name, tuple(shape), tuple(t.shape)))
+    return C.c_void_p(t.data_ptr())
+
+
+def make_params(d: dict) -> _lib.Params:
+    sched = d.get("schedule", "fixed")
+    if isinstance(sched, str):
+        sched = {"fixed": 0, "linear": 1}[sched]
+    return _lib.Params(float(d["alpha_leak"]), float(d["dt"]), float(d["v_test"]), float(d["mu"]),
+                       float(d["lr"]), float(d["r0"]), float(d["w_range"]), float(d["w_limit"]),
+                       float(d["w_pen"]), int(sched))
+
+
+class Hand:
+    """fg_hand: link tree, joint limits and link-local surface points."""
+
+    def __init__(self, parent, T_fix, axis, q_low, q_up, pts_local, link_of_point):
+        lib = _lib.load()
+        self._keep = [np.ascontiguousarray(parent, dtype=np.int32),
+                      np.ascontiguousarray(np.asarray(T_fix, dtype=np.float32).reshape(-1, 12)),
+                      np.ascontiguousarray(np.asarray(axis, dtype=np.float32).reshape(-1, 3)),
+                      np.ascontiguousarray(q_low, dtype=np.float32),
+                      np.ascontiguousarray(q_up, dtype=np.float32),
+                      np.ascontiguousarray(np.asarray(pts_local, dtype=np.float32).reshape(-1, 3)),
+                      np.ascontiguousarray(link_of_point, dtype=np.int32)]
+        par, tf, ax, lo, up, pts, lop = self._keep
+        ptr = lambda a, t: a.ctypes.data_as(C.POINTER(t))
+        desc = _lib.HandDesc(len(par), len(lop), ptr(par, C.c_int), ptr(tf, C.c_float), ptr(ax, C.c_float),
+                             ptr(lo, C.c_float), ptr(up, C.c_float), ptr(pts, C.c_float), ptr(lop, C.c_int))
+        h = C.c_void_p()
+        check(lib.fg_hand_create(C.byref(desc), C.byref(h)), "fg_hand_create")
+        self.handle = h
+        vals = [C.c_int() for _ in range(4)]
+        check(lib.fg_hand_info(h, *[C.byref(v) for v in vals]), "fg_hand_info")
+        self.L, self.J, self.D, self.P = [v.value for v in vals]
+
+    @classmethod
+    def from_synth(cls, h: dict) -> "Hand":
+        return cls(h["parent"], h["T_fix"], h["axis"], h["q_low"], h["q_up"], h["pts_local"], h["link_of_point"])
+
+    def __del__(self):
+        if getattr(self, "handle", None) is not None and _lib._lib is not None:
+            _lib._lib.fg_hand_destroy(self.handle)
+            self.handle = None
+
+
+class Sdf:
+    """fg_sdf: a voxel SDF grid [nz, ny, nx] (x fastest) with the object's mass properties."""
+
+    def __init__(self, grid: torch.Tensor, origin, pitch: float, mass: float, inertia: float):
+        lib = _lib.load()
+        g = grid.detach().to(_F32).contiguous()
+        nz, ny, nx = g.shape
+        org = (C.c_float * 3)(*[float(v) for v in origin])
+        h = C.c_void_p()
+        check(lib.fg_sdf_create(C.c_void_p(g.data_ptr()), nx, ny, nz, org, float(pitch), float(mass),
+                                float(inertia), C.byref(h)), "fg_sdf_create")
+        self.handle = h
+        self.dims = (nx, ny, nz)
+
+    @classmethod
+    def from_synth(cls, o: dict) -> "Sdf":
+        return cls(o["grid"], o["origin"], o["pitch"], o["mass"], o["inertia"])
+
+    def __del__(self):
+        if getattr(self, "handle", None) is not None and _lib._lib is not None:
+            _lib._lib.fg_sdf_destroy(self.handle)
+            self.handle = None
+
+
+class Scene:
+    """fg_scene: ordered table of objects, indexed by obj_of_cand."""
+
+    def __init__(self, sdfs):
+        lib = _lib.load()
+        self.sdfs = list(sdfs)
+        arr = (C.c_void_p * len(self.sdfs))(*[s.handle.value for s in self.sdfs])
+        h = C.c_void_p()
+        check(lib.fg_scene_create(arr, len(self.sdfs), C.byref(h)), "fg_scene_create")
+        self.handle = h
+
+    def __del__(self):
+        if getattr(self, "handle", None) is not None and _lib._lib is not None:
+            _lib._lib.fg_scene_destroy(self.handle)
+            self.handle = None
+
+
+def fk(hand: Hand, q: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+    B = q.shape[0]
+    _dptr(q, "q", shape=(B, hand.D))
+    if out is None:
+        out = torch.empty(3, B * hand.P, device=q.device, dtype=_F32)
+    check(_lib.load().fg_fk(hand.handle, _dptr(q, "q"), B, _dptr(out, "pts", shape=(3, B * hand.P)), _stream()),
+          "fg_fk")
+    return out
+
+
+def sdf_query(sdf: Sdf, pts: torch.Tensor, r_dil: float, want_grad: bool = True):
+    n = pts.shape[1]
+    _dptr(pts, "pts", shape=(3, n))
+    phi = torch.empty(n, device=pts.device, dtype=_F32)
+    grad = torch.empty(3, n, device=pts.device, dtype=_F32) if want_grad else None
+    check(_lib.load().fg_sdf_query(sdf.handle, _dptr(pts, "pts"), n, float(r_dil), _dptr(phi, "phi"),
+                                   _dptr(grad, "grad"), _stream()), "fg_sdf_query")
+    return phi, grad
+
+
+def _oc(obj_of_cand, B):
+    if obj_of_cand is None:
+        return None
+    return _dptr(obj_of_cand, "obj_of_cand", dtype=torch.int32, shape=(B,))
+
+
+def contact_wrench(hand: Hand, scene: Scene, q: torch.Tensor, params: dict, r_dil: float,
+                   obj_of_cand: torch.Tensor | None = None, want_bits: bool = False):
+    B = q.shape[0]
+    _dptr(q, "q", shape=(B, hand.D))
+    dev = q.device
+    wrench = torch.empty(B, FG_NUM_SIMS, 6, device=dev, dtype=_F32)
+    ncontact = torch.empty(B, FG_NUM_SIMS, device=dev, dtype=torch.int32)
+    nwords = (hand.P + 31) // 32
+    bits = torch.empty(B, FG_NUM_SIMS, nwords, device=dev, dtype=torch.int32) if want_bits else None
+    prm = make_params(params)
+    check(_lib.load().fg_contact_wrench(hand.handle, scene.handle, _oc(obj_of_cand, B), _dptr(q, "q"), B,
+                                        C.byref(prm), float(r_dil), _dptr(wrench, "wrench"),
+                                        _dptr(ncontact, "ncontact", dtype=torch.int32),
+                                        _dptr(bits, "bits", dtype=torch.int32), _stream()), "fg_contact_wrench")
+    return wrench, ncontact, bits
+
+
+def loss_and_grad(hand: Hand, scene: Scene, q: torch.Tensor, params: dict, r_dil: float,
+                  obj_of_cand: torch.Tensor | None = None, want_grad: bool = True):
+    B = q.shape[0]
+    _dptr(q, "q", shape=(B, hand.D))
+    loss = torch.empty(B, device=q.device, dtype=_F32)
+    grad = torch.empty(B, hand.D, device=q.device, dtype=_F32) if want_grad else None
+    prm = make_params(params)
+    check(_lib.load().fg_loss_and_grad(hand.handle, scene.handle, _oc(obj_of_cand, B), _dptr(q, "q"), B,
+                                       C.byref(prm), float(r_dil), _dptr(loss, "loss"), _dptr(grad, "grad"),
+                                       _stream()), "fg_loss_and_grad")
+    return loss, grad
+
+
+def optimize_step(hand: Hand, scene: Scene, q: torch.Tensor, params: dict, step: int, total_steps: int,
+                  nsteps: int = 1, obj_of_cand: torch.Tensor | None = None, loss: torch.Tensor | None = None):
+    """In-place gradient descent on q for nsteps (fused persistent kernel); returns the loss tensor."""
+    B = q.shape[0]
+    _dptr(q, "q", shape=(B, hand.D))
+    if loss is None:
+        loss = torch.empty(B, device=q.device, dtype=_F32)
+    prm = make_params(params)
+    check(_lib.load().fg_optimize_step(hand.handle, scene.handle, _oc(obj_of_cand, B), _dptr(q, "q"), B,
+                                       C.byref(prm), int(step), int(total_steps), int(nsteps),
+                                       _dptr(loss, "loss", shape=(B,)), _stream()), "fg_optimize_step")
+    return loss
+
+
+def plain_workspace_size(hand: Hand, B: int) -> int:
+    n = C.c_size_t()
+    check(_lib.load().fg_plain_workspace_size(hand.handle, B, C.byref(n)), "fg_plain_workspace_size")
+    return n.value
+
+
+def optimize_step_plain(hand: Hand, scene: Scene, q: torch.Tensor, params: dict, step: int, total_steps: int,
+                        nsteps: int = 1, obj_of_cand: torch.Tensor | None = None,
+                        loss: torch.Tensor | None = None, workspace: torch.Tensor | None = None):
+    """The same step through the plain one-kernel-per-stage form (workspace in device memory)."""
+    B = q.shape[0]
+    _dptr(q, "q", shape=(B, hand.D))
+    need = plain_workspace_size(hand, B)
+    if workspace is None:
+        workspace = torch.empty(need + 256, device=q.device, dtype=torch.uint8)
+    base = workspace.data_ptr()
+    aligned = (base + 255) // 256 * 256
+    avail = workspace.numel() - (aligned - base)
+    if loss is None:
+        loss = torch.empty(B, device=q.device, dtype=_F32)
+    prm = make_params(params)
+    check(_lib.load().fg_optimize_step_plain(hand.handle, scene.handle, _oc(obj_of_cand, B), _dptr(q, "q"), B,
+                                             C.byref(prm), int(step), int(total_steps), int(nsteps),
+                                             _dptr(loss, "loss", shape=(B,)), C.c_void_p(aligned), avail,
+                                             _stream()), "fg_optimize_step_plain")
+    return loss

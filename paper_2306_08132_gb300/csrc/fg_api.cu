@@ -1,0 +1,414 @@
+// C ABI entry points: validation, handles, error reporting and dispatch.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "fg_internal.h"
+
+namespace fg {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+fg_status cuda_status(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return FG_OK;
+  set_error(std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")");
+  return e == cudaErrorMemoryAllocation ? FG_ERR_OOM : FG_ERR_CUDA;
+}
+
+int device_sm_count() {
+  static int cached[64];
+  static bool init[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+  if (!init[dev]) {
+    int n = 1;
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    cached[dev] = n > 0 ? n : 1;
+    init[dev] = true;
+  }
+  return cached[dev];
+}
+
+ParamsDev params_from(const fg_params* p) {
+  ParamsDev d;
+  d.alpha = p->alpha_leak;
+  d.dt = p->dt;
+  d.V = p->v_test;
+  d.mu = p->mu;
+  d.lr = p->lr;
+  d.r0 = p->r0;
+  d.w_range = p->w_range;
+  d.w_limit = p->w_limit;
+  d.w_pen = p->w_pen;
+  d.schedule = p->schedule;
+  return d;
+}
+
+static fg_status invalid(const std::string& msg) {
+  set_error(msg);
+  return FG_ERR_INVALID;
+}
+
+static fg_status check_params(const fg_params* p) {
+  if (!p) return invalid("params is NULL");
+  if (!(p->dt > 0.0f) || !std::isfinite(p->dt)) return invalid("params.dt must be > 0");
+  if (!(p->v_test >= 0.0f) || !std::isfinite(p->v_test)) return invalid("params.v_test must be >= 0");
+  if (!(p->mu >= 0.0f) || !std::isfinite(p->mu)) return invalid("params.mu must be >= 0");
+  if (!(p->alpha_leak >= 0.0f && p->alpha_leak <= 1.0f)) return invalid("params.alpha_leak must be in [0, 1]");
+  if (!(p->r0 >= 0.0f) || !std::isfinite(p->r0)) return invalid("params.r0 must be >= 0");
+  if (!std::isfinite(p->lr) || !std::isfinite(p->w_range) || !std::isfinite(p->w_limit) || !std::isfinite(p->w_pen))
+    return invalid("params has a non-finite weight");
+  if (p->schedule != 0 && p->schedule != 1) return invalid("params.schedule must be 0 or 1");
+  return FG_OK;
+}
+
+}  // namespace fg
+
+using namespace fg;
+
+extern "C" {
+
+fg_status fg_version(int* major, int* minor) {
+  if (major) *major = 1;
+  if (minor) *minor = 0;
+  return FG_OK;
+}
+
+const char* fg_status_string(fg_status s) {
+  switch (s) {
+    case FG_OK: return "FG_OK";
+    case FG_ERR_INVALID: return "FG_ERR_INVALID";
+    case FG_ERR_OOM: return "FG_ERR_OOM";
+    case FG_ERR_BUDGET: return "FG_ERR_BUDGET";
+    case FG_ERR_TIMEOUT: return "FG_ERR_TIMEOUT";
+    case FG_ERR_CUDA: return "FG_ERR_CUDA";
+    case FG_ERR_BUSY: return "FG_ERR_BUSY";
+    case FG_ERR_NOT_FOUND: return "FG_ERR_NOT_FOUND";
+  }
+  return "FG_ERR_UNKNOWN";
+}
+
+fg_status fg_last_error(char* buf, size_t n) {
+  if (!buf || n == 0) return FG_ERR_INVALID;
+  size_t k = g_last_error.size() < n - 1 ? g_last_error.size() : n - 1;
+  std::memcpy(buf, g_last_error.data(), k);
+  buf[k] = '\0';
+  return FG_OK;
+}
+
+fg_status fg_hand_create(const fg_hand_desc* d, fg_hand** out) {
+  if (!d || !out) return invalid("fg_hand_create: NULL argument");
+  *out = nullptr;
+  const int L = d->n_links, P = d->n_points;
+  if (L < 1 || L > FG_MAX_LINKS) return invalid("fg_hand_create: n_links must be in [1, 32]");
+  if (P < 1 || P > FG_MAX_POINTS) return invalid("fg_hand_create: n_points must be in [1, 2^20]");
+  if (!d->parent || !d->T_fix || !d->pts_local || !d->link_of_point || (L > 1 && (!d->axis || !d->q_low || !d->q_up)))
+    return invalid("fg_hand_create: NULL array in descriptor");
+  if (d->parent[0] != -1) return invalid("fg_hand_create: parent[0] must be -1");
+  HandDev H;
+  std::memset(&H, 0, sizeof(H));
+  H.L = L;
+  H.J = L - 1;
+  H.D = 6 + L - 1;
+  H.P = P;
+  H.parent[0] = -1;
+  H.depth[0] = 0;
+  for (int l = 1; l < L; ++l) {
+    int p = d->parent[l];
+    if (p < 0 || p >= l) return invalid("fg_hand_create: links must be in topological order (0 <= parent[l] < l)");
+    H.parent[l] = p;
+    H.depth[l] = H.depth[p] + 1;
+    if (H.depth[l] > H.max_depth) H.max_depth = H.depth[l];
+  }
+  // subtree sizes and depth-first preorder check: descendants of l are exactly [l+1, l+size)
+  int size[FG_MAX_LINKS];
+  for (int l = 0; l < L; ++l) size[l] = 1;
+  for (int l = L - 1; l >= 1; --l) size[H.parent[l]] += size[l];
+  for (int l = 0; l < L; ++l) {
+    H.subtree_end[l] = l + size[l];
+    for (int k = l + 1; k < l + size[l]; ++k) {
+      int a = k;
+      while (a > l) a = H.parent[a];
+      if (a != l) return invalid("fg_hand_create: links must be in depth-first preorder (contiguous subtrees)");
+    }
+  }
+  for (int l = 0; l < L; ++l)
+    for (int k = 0; k < 12; ++k) {
+      float v = d->T_fix[12 * l + k];
+      if (!std::isfinite(v)) return invalid("fg_hand_create: non-finite T_fix");
+      H.T_fix[l][k] = v;
+    }
+  for (int l = 1; l < L; ++l) {
+    float n2 = 0.0f;
+    for (int k = 0; k < 3; ++k) {
+      H.axis[l][k] = d->axis[3 * l + k];
+      n2 += H.axis[l][k] * H.axis[l][k];
+    }
+    if (!(std::fabs(n2 - 1.0f) < 1e-4f)) return invalid("fg_hand_create: joint axes must be unit vectors");
+    H.q_low[l - 1] = d->q_low[l - 1];
+    H.q_up[l - 1] = d->q_up[l - 1];
+    if (!(H.q_low[l - 1] <= H.q_up[l - 1])) return invalid("fg_hand_create: q_low must be <= q_up");
+  }
+  std::vector<float4> pts(P);
+  int prev = 0;
+  H.aligned32 = 1;
+  for (int i = 0; i < P; ++i) {
+    int l = d->link_of_point[i];
+    if (l < 0 || l >= L || l < prev) return invalid("fg_hand_create: link_of_point must be nondecreasing in [0, L)");
+    if (l != prev && (i & 31)) H.aligned32 = 0;
+    prev = l;
+    float x = d->pts_local[3 * i], y = d->pts_local[3 * i + 1], z = d->pts_local[3 * i + 2];
+    if (!std::isfinite(x) || !std::isfinite(y) || !std::isfinite(z)) return invalid("fg_hand_create: non-finite point");
+    pts[i] = make_float4(x, y, z, (float)l);
+  }
+  fg_hand* h = new (std::nothrow) fg_hand;
+  if (!h) return FG_ERR_OOM;
+  std::memset(h, 0, sizeof(*h));
+  cudaError_t e = cudaMalloc(&h->pts, sizeof(float4) * P);
+  if (e != cudaSuccess) {
+    delete h;
+    return cuda_status(e, "fg_hand_create: cudaMalloc");
+  }
+  e = cudaMalloc(&h->dev, sizeof(HandDev));
+  if (e != cudaSuccess) {
+    cudaFree(h->pts);
+    delete h;
+    return cuda_status(e, "fg_hand_create: cudaMalloc");
+  }
+  H.pts = h->pts;
+  e = cudaMemcpy(h->pts, pts.data(), sizeof(float4) * P, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->dev, &H, sizeof(HandDev), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(h->pts);
+    cudaFree(h->dev);
+    delete h;
+    return cuda_status(e, "fg_hand_create: cudaMemcpy");
+  }
+  h->host = H;
+  for (int l = 0; l < L; ++l) h->subtree_end[l] = H.subtree_end[l];
+  *out = h;
+  return FG_OK;
+}
+
+fg_status fg_hand_destroy(fg_hand* h) {
+  if (!h) return FG_OK;
+  cudaFree(h->pts);
+  cudaFree(h->dev);
+  delete h;
+  return FG_OK;
+}
+
+fg_status fg_hand_info(const fg_hand* h, int* nl, int* nj, int* nd, int* np) {
+  if (!h) return invalid("fg_hand_info: NULL hand");
+  if (nl) *nl = h->host.L;
+  if (nj) *nj = h->host.J;
+  if (nd) *nd = h->host.D;
+  if (np) *np = h->host.P;
+  return FG_OK;
+}
+
+fg_status fg_sdf_create(const float* grid, int nx, int ny, int nz, const float* origin, float pitch, float mass,
+                        float inertia, fg_sdf** out) {
+  if (!grid || !origin || !out) return invalid("fg_sdf_create: NULL argument");
+  *out = nullptr;
+  if (nx < 2 || ny < 2 || nz < 2) return invalid("fg_sdf_create: grid dimensions must be >= 2");
+  if ((double)nx * ny * nz > 2147483647.0) return invalid("fg_sdf_create: grid has more than 2^31 nodes");
+  if (!(pitch > 0.0f) || !std::isfinite(pitch)) return invalid("fg_sdf_create: pitch must be > 0");
+  if (!(mass > 0.0f) || !(inertia > 0.0f) || !std::isfinite(mass) || !std::isfinite(inertia))
+    return invalid("fg_sdf_create: mass and inertia must be > 0");
+  for (int k = 0; k < 3; ++k)
+    if (!std::isfinite(origin[k])) return invalid("fg_sdf_create: non-finite origin");
+  fg_sdf* s = new (std::nothrow) fg_sdf;
+  if (!s) return FG_ERR_OOM;
+  s->bytes = sizeof(float) * (size_t)nx * ny * nz;
+  cudaError_t e = cudaMalloc(&s->grid, s->bytes);
+  if (e != cudaSuccess) {
+    delete s;
+    return cuda_status(e, "fg_sdf_create: cudaMalloc");
+  }
+  e = cudaMemcpy(s->grid, grid, s->bytes, cudaMemcpyDefault);
+  if (e != cudaSuccess) {
+    cudaFree(s->grid);
+    delete s;
+    return cuda_status(e, "fg_sdf_create: cudaMemcpy");
+  }
+  ObjDev& o = s->host;
+  std::memset(&o, 0, sizeof(o));
+  o.grid = s->grid;
+  o.nx = nx;
+  o.ny = ny;
+  o.nz = nz;
+  o.ox = origin[0];
+  o.oy = origin[1];
+  o.oz = origin[2];
+  o.h = pitch;
+  o.inv_h = 1.0f / pitch;
+  o.inv_mass = 1.0f / mass;
+  o.inv_inertia = 1.0f / inertia;
+  *out = s;
+  return FG_OK;
+}
+
+fg_status fg_sdf_destroy(fg_sdf* s) {
+  if (!s) return FG_OK;
+  cudaFree(s->grid);
+  delete s;
+  return FG_OK;
+}
+
+fg_status fg_scene_create(const fg_sdf* const* sdfs, int n, fg_scene** out) {
+  if (!sdfs || !out || n < 1) return invalid("fg_scene_create: need n >= 1 objects");
+  *out = nullptr;
+  std::vector<ObjDev> tab(n);
+  for (int i = 0; i < n; ++i) {
+    if (!sdfs[i]) return invalid("fg_scene_create: NULL object");
+    tab[i] = sdfs[i]->host;
+  }
+  fg_scene* sc = new (std::nothrow) fg_scene;
+  if (!sc) return FG_ERR_OOM;
+  sc->n = n;
+  cudaError_t e = cudaMalloc(&sc->dev, sizeof(ObjDev) * n);
+  if (e != cudaSuccess) {
+    delete sc;
+    return cuda_status(e, "fg_scene_create: cudaMalloc");
+  }
+  e = cudaMemcpy(sc->dev, tab.data(), sizeof(ObjDev) * n, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(sc->dev);
+    delete sc;
+    return cuda_status(e, "fg_scene_create: cudaMemcpy");
+  }
+  *out = sc;
+  return FG_OK;
+}
+
+fg_status fg_scene_destroy(fg_scene* sc) {
+  if (!sc) return FG_OK;
+  cudaFree(sc->dev);
+  delete sc;
+  return FG_OK;
+}
+
+fg_status fg_fk(const fg_hand* h, const float* q, int B, float* pts, void* stream) {
+  if (!h) return invalid("fg_fk: NULL hand");
+  if (B < 0) return invalid("fg_fk: B < 0");
+  if (B == 0) return FG_OK;
+  if (!q || !pts) return invalid("fg_fk: NULL buffer");
+  if ((size_t)B * h->host.P > (size_t)1 << 40) return invalid("fg_fk: B * P too large");
+  return cuda_status(launch_fk_points(h, q, B, pts, (cudaStream_t)stream), "fg_fk");
+}
+
+fg_status fg_sdf_query(const fg_sdf* s, const float* pts, int n, float r, float* phi, float* grad, void* stream) {
+  if (!s) return invalid("fg_sdf_query: NULL sdf");
+  if (n < 0) return invalid("fg_sdf_query: n < 0");
+  if (n == 0) return FG_OK;
+  if (!pts || !phi) return invalid("fg_sdf_query: NULL buffer");
+  if (!std::isfinite(r)) return invalid("fg_sdf_query: non-finite r_dil");
+  return cuda_status(launch_sdf_query(s->host, pts, n, r, phi, grad, (cudaStream_t)stream), "fg_sdf_query");
+}
+
+static fg_status check_common(const char* fn, const fg_hand* h, const fg_scene* sc, int B, const fg_params* p) {
+  if (!h || !sc) return invalid(std::string(fn) + ": NULL hand or scene");
+  if (B < 0) return invalid(std::string(fn) + ": B < 0");
+  return check_params(p);
+}
+
+fg_status fg_contact_wrench(const fg_hand* h, const fg_scene* sc, const int* oc, const float* q, int B,
+                            const fg_params* p, float r, float* wrench, int* ncontact, uint32_t* bits,
+                            void* stream) {
+  fg_status st = check_common("fg_contact_wrench", h, sc, B, p);
+  if (st != FG_OK) return st;
+  if (B == 0) return FG_OK;
+  if (!q || !wrench || !ncontact) return invalid("fg_contact_wrench: NULL buffer");
+  if (!std::isfinite(r)) return invalid("fg_contact_wrench: non-finite r_dil");
+  FusedArgs a{};
+  a.hand = h->dev;
+  a.objs = sc->dev;
+  a.n_obj = sc->n;
+  a.obj_of_cand = oc;
+  a.q = const_cast<float*>(q);
+  a.B = B;
+  a.P = params_from(p);
+  a.r_fixed = r;
+  a.nsteps = 1;
+  a.wrench = wrench;
+  a.ncontact = ncontact;
+  a.bits = bits;
+  return cuda_status(launch_fused(kModeWrench, a, h, (cudaStream_t)stream), "fg_contact_wrench");
+}
+
+fg_status fg_loss_and_grad(const fg_hand* h, const fg_scene* sc, const int* oc, const float* q, int B,
+                           const fg_params* p, float r, float* loss, float* grad, void* stream) {
+  fg_status st = check_common("fg_loss_and_grad", h, sc, B, p);
+  if (st != FG_OK) return st;
+  if (B == 0) return FG_OK;
+  if (!q || !loss) return invalid("fg_loss_and_grad: NULL buffer");
+  if (!std::isfinite(r)) return invalid("fg_loss_and_grad: non-finite r_dil");
+  FusedArgs a{};
+  a.hand = h->dev;
+  a.objs = sc->dev;
+  a.n_obj = sc->n;
+  a.obj_of_cand = oc;
+  a.q = const_cast<float*>(q);
+  a.B = B;
+  a.P = params_from(p);
+  a.r_fixed = r;
+  a.nsteps = 1;
+  a.loss = loss;
+  a.grad = grad;
+  return cuda_status(launch_fused(kModeLossGrad, a, h, (cudaStream_t)stream), "fg_loss_and_grad");
+}
+
+fg_status fg_optimize_step(const fg_hand* h, const fg_scene* sc, const int* oc, float* q, int B, const fg_params* p,
+                           int step, int total_steps, int nsteps, float* loss, void* stream) {
+  fg_status st = check_common("fg_optimize_step", h, sc, B, p);
+  if (st != FG_OK) return st;
+  if (nsteps < 1) return invalid("fg_optimize_step: nsteps must be >= 1");
+  if (step < 0 || total_steps < 1) return invalid("fg_optimize_step: need step >= 0 and total_steps >= 1");
+  if (B == 0) return FG_OK;
+  if (!q) return invalid("fg_optimize_step: NULL q");
+  FusedArgs a{};
+  a.hand = h->dev;
+  a.objs = sc->dev;
+  a.n_obj = sc->n;
+  a.obj_of_cand = oc;
+  a.q = q;
+  a.B = B;
+  a.P = params_from(p);
+  a.step0 = step;
+  a.total_steps = total_steps;
+  a.nsteps = nsteps;
+  a.loss = loss;
+  return cuda_status(launch_fused(kModeOptimize, a, h, (cudaStream_t)stream), "fg_optimize_step");
+}
+
+fg_status fg_plain_workspace_size(const fg_hand* h, int B, size_t* bytes) {
+  if (!h || !bytes || B < 0) return invalid("fg_plain_workspace_size: bad argument");
+  *bytes = plain_workspace_bytes(h, B);
+  return FG_OK;
+}
+
+fg_status fg_optimize_step_plain(const fg_hand* h, const fg_scene* sc, const int* oc, float* q, int B,
+                                 const fg_params* p, int step, int total_steps, int nsteps, float* loss, void* ws,
+                                 size_t ws_bytes, void* stream) {
+  fg_status st = check_common("fg_optimize_step_plain", h, sc, B, p);
+  if (st != FG_OK) return st;
+  if (nsteps < 1) return invalid("fg_optimize_step_plain: nsteps must be >= 1");
+  if (step < 0 || total_steps < 1) return invalid("fg_optimize_step_plain: need step >= 0 and total_steps >= 1");
+  if (B == 0) return FG_OK;
+  if (!q || !ws) return invalid("fg_optimize_step_plain: NULL buffer");
+  if (((uintptr_t)ws & 255) != 0) return invalid("fg_optimize_step_plain: workspace must be 256-byte aligned");
+  if (ws_bytes < plain_workspace_bytes(h, B)) return invalid("fg_optimize_step_plain: workspace too small");
+  return cuda_status(launch_plain_step(h, sc, oc, q, B, params_from(p), step, total_steps, nsteps, loss, ws,
+                                       (cudaStream_t)stream),
+                     "fg_optimize_step_plain");
+}
+
+}  // extern "C"

@@ -1,0 +1,543 @@
+// Device-side data layouts and per-point arithmetic of the grasp-search step.
+//
+// Everything a kernel needs about one step of one candidate lives here, written
+// once and used by the fused kernel (fg_fused.cu) and the per-stage kernels
+// (fg_plain.cu).  The arithmetic that decides a branch (point position, grid
+// cell, interpolated value and normal, contact flag, friction regime) is spelled
+// with explicit round-to-nearest intrinsics so that every call site rounds
+// identically and the forward sweep, the adjoint sweep and the per-stage form
+// agree bit for bit on every decision.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fastgraspd.h"
+
+namespace fg {
+
+constexpr int kSims = FG_NUM_SIMS;
+constexpr int kMaxLinks = FG_MAX_LINKS;
+
+struct HandDev {
+  int L, J, D, P;
+  int max_depth;
+  int aligned32;                 // every link starts at a multiple of 32 points
+  int parent[kMaxLinks];
+  int depth[kMaxLinks];
+  float T_fix[kMaxLinks][12];    // row-major [R | t]
+  float axis[kMaxLinks][3];
+  float q_low[kMaxLinks];        // per joint j = l - 1
+  float q_up[kMaxLinks];
+  int subtree_end[kMaxLinks];    // links are in depth-first preorder: subtree(l) = [l, subtree_end[l])
+  const float4* pts;             // [P] (x, y, z, link index as float)
+};
+
+struct ObjDev {
+  const float* grid;             // [nz][ny][nx]
+  int nx, ny, nz, pad0;
+  float ox, oy, oz;              // origin
+  float inv_h, h;                // 1/pitch, pitch
+  float inv_mass, inv_inertia;
+  float pad1;
+};
+
+struct ParamsDev {
+  float alpha, dt, V, mu, lr, r0, w_range, w_limit, w_pen;
+  int schedule;
+};
+
+// -------------------------------------------------------------------- rounding
+__device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float mul_(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float add_(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sub_(float a, float b) { return __fsub_rn(a, b); }
+
+struct Frame {                   // rotation (row-major) and origin of a link
+  float R[9];
+  float o[3];
+};
+
+// ------------------------------------------------------------------ kinematics
+
+// Rotation by angle |w| about w (Rodrigues).  (1 - cos a)/a^2 is evaluated as
+// (sin(a/2)/(a/2))^2 / 2, which has no cancellation at small angles.
+__device__ inline void so3_exp(const float w[3], float R[9]) {
+  float a2 = fma_(w[0], w[0], fma_(w[1], w[1], mul_(w[2], w[2])));
+  float c1, c2;
+  if (a2 < 1e-12f) {
+    c1 = sub_(1.0f, mul_(a2, 1.0f / 6.0f));
+    c2 = sub_(0.5f, mul_(a2, 1.0f / 24.0f));
+  } else {
+    float a = sqrtf(a2);
+    float sh, ch, s, c;
+    sincosf(0.5f * a, &sh, &ch);
+    s = mul_(2.0f, mul_(sh, ch));             // sin a
+    c1 = __fdiv_rn(s, a);
+    float sa = __fdiv_rn(sh, mul_(0.5f, a));
+    c2 = mul_(0.5f, mul_(sa, sa));
+    (void)c;
+  }
+  // R = I + c1 K + c2 K^2, K = [w]x, K^2 = w w^T - a2 I
+  float x = w[0], y = w[1], z = w[2];
+  R[0] = fma_(c2, sub_(mul_(x, x), a2), 1.0f);
+  R[4] = fma_(c2, sub_(mul_(y, y), a2), 1.0f);
+  R[8] = fma_(c2, sub_(mul_(z, z), a2), 1.0f);
+  float xy = mul_(c2, mul_(x, y)), xz = mul_(c2, mul_(x, z)), yz = mul_(c2, mul_(y, z));
+  float cx = mul_(c1, x), cy = mul_(c1, y), cz = mul_(c1, z);
+  R[1] = sub_(xy, cz); R[3] = add_(xy, cz);
+  R[2] = add_(xz, cy); R[6] = sub_(xz, cy);
+  R[5] = sub_(yz, cx); R[7] = add_(yz, cx);
+}
+
+// Rotation by theta about a unit axis.
+__device__ inline void axis_rot(const float a[3], float theta, float R[9]) {
+  float sh, ch;
+  sincosf(0.5f * theta, &sh, &ch);
+  float s = mul_(2.0f, mul_(sh, ch));
+  float v = mul_(2.0f, mul_(sh, sh));        // 1 - cos theta
+  float x = a[0], y = a[1], z = a[2];
+  R[0] = fma_(v, sub_(mul_(x, x), 1.0f), 1.0f);
+  R[4] = fma_(v, sub_(mul_(y, y), 1.0f), 1.0f);
+  R[8] = fma_(v, sub_(mul_(z, z), 1.0f), 1.0f);
+  float xy = mul_(v, mul_(x, y)), xz = mul_(v, mul_(x, z)), yz = mul_(v, mul_(y, z));
+  float sx = mul_(s, x), sy = mul_(s, y), sz = mul_(s, z);
+  R[1] = sub_(xy, sz); R[3] = add_(xy, sz);
+  R[2] = add_(xz, sy); R[6] = sub_(xz, sy);
+  R[5] = sub_(yz, sx); R[7] = add_(yz, sx);
+}
+
+__device__ inline void matmul3(const float A[9], const float B[9], float C[9]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+      C[3 * i + j] = fma_(A[3 * i], B[j], fma_(A[3 * i + 1], B[3 + j], mul_(A[3 * i + 2], B[6 + j])));
+}
+
+__device__ inline void matvec3(const float A[9], const float v[3], float out[3]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i) out[i] = fma_(A[3 * i], v[0], fma_(A[3 * i + 1], v[1], mul_(A[3 * i + 2], v[2])));
+}
+
+// Frame of link l >= 1 from its parent's frame: T_l = T_par * T_fix_l * Rot(axis_l, theta).
+__device__ inline void link_frame(const HandDev& H, int l, const Frame& par, float theta, Frame& out) {
+  float Rf[9], Rj[9], tmp[9], tf[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    Rf[3 * i] = H.T_fix[l][4 * i];
+    Rf[3 * i + 1] = H.T_fix[l][4 * i + 1];
+    Rf[3 * i + 2] = H.T_fix[l][4 * i + 2];
+    tf[i] = H.T_fix[l][4 * i + 3];
+  }
+  axis_rot(H.axis[l], theta, Rj);
+  matmul3(par.R, Rf, tmp);
+  matmul3(tmp, Rj, out.R);
+  float d[3];
+  matvec3(par.R, tf, d);
+  out.o[0] = add_(par.o[0], d[0]);
+  out.o[1] = add_(par.o[1], d[1]);
+  out.o[2] = add_(par.o[2], d[2]);
+}
+
+__device__ inline void root_frame(const float* q, Frame& out) {
+  float w[3] = {q[3], q[4], q[5]};
+  so3_exp(w, out.R);
+  out.o[0] = q[0];
+  out.o[1] = q[1];
+  out.o[2] = q[2];
+}
+
+// Point in world coordinates: p = R s + o.
+__device__ __forceinline__ void transform_point(const float* R, const float* o, float sx, float sy, float sz,
+                                                float p[3]) {
+  p[0] = fma_(R[0], sx, fma_(R[1], sy, fma_(R[2], sz, o[0])));
+  p[1] = fma_(R[3], sx, fma_(R[4], sy, fma_(R[5], sz, o[1])));
+  p[2] = fma_(R[6], sx, fma_(R[7], sy, fma_(R[8], sz, o[2])));
+}
+
+// ------------------------------------------------------------------------- SDF
+
+// Result of one grid lookup.  g is the gradient of the undilated SDF; Hxy, Hxz,
+// Hyz the mixed second derivatives of the trilinear part (zero on clamped axes);
+// when the point lies outside the grid, eh = (u - u_c)/|u - u_c| and e the excess.
+struct SdfSample {
+  float phi;
+  float g[3];
+  float hxy, hxz, hyz;
+  float eh[3];
+  float e;
+  bool outside;
+};
+
+template <bool kHess>
+__device__ __forceinline__ void sdf_lookup(const ObjDev& O, const float p[3], SdfSample& s) {
+  const float n_max[3] = {(float)(O.nx - 1), (float)(O.ny - 1), (float)(O.nz - 1)};
+  const float org[3] = {O.ox, O.oy, O.oz};
+  float u[3], uc[3], du[3], f[3];
+  int i0[3];
+  bool clamped[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    u[k] = mul_(sub_(p[k], org[k]), O.inv_h);
+    bool lo = u[k] < 0.0f, hi = u[k] > n_max[k];
+    clamped[k] = lo || hi;
+    uc[k] = lo ? 0.0f : (hi ? n_max[k] : u[k]);
+    du[k] = sub_(u[k], uc[k]);
+    int ii = (int)floorf(uc[k]);
+    int cap = (int)n_max[k] - 1;
+    i0[k] = ii < cap ? ii : cap;
+    f[k] = sub_(uc[k], (float)i0[k]);
+  }
+  const int sx = 1, sy = O.nx, sz = O.nx * O.ny;
+  const float* G = O.grid + ((size_t)i0[2] * O.ny + i0[1]) * O.nx + i0[0];
+  float c000 = __ldg(G), c100 = __ldg(G + sx);
+  float c010 = __ldg(G + sy), c110 = __ldg(G + sy + sx);
+  float c001 = __ldg(G + sz), c101 = __ldg(G + sz + sx);
+  float c011 = __ldg(G + sz + sy), c111 = __ldg(G + sz + sy + sx);
+  // trilinear in differences: x first, then y, then z
+  float dx00 = sub_(c100, c000), dx10 = sub_(c110, c010), dx01 = sub_(c101, c001), dx11 = sub_(c111, c011);
+  float x00 = fma_(f[0], dx00, c000), x10 = fma_(f[0], dx10, c010);
+  float x01 = fma_(f[0], dx01, c001), x11 = fma_(f[0], dx11, c011);
+  float dy0 = sub_(x10, x00), dy1 = sub_(x11, x01);
+  float y0 = fma_(f[1], dy0, x00), y1 = fma_(f[1], dy1, x01);
+  float dz = sub_(y1, y0);
+  float val = fma_(f[2], dz, y0);
+  float ey0 = sub_(dx10, dx00), ey1 = sub_(dx11, dx01);
+  float a0 = fma_(f[1], ey0, dx00), a1 = fma_(f[1], ey1, dx01);
+  float dax = sub_(a1, a0);
+  float gx = fma_(f[2], dax, a0);             // d/dfx
+  float ddy = sub_(dy1, dy0);
+  float gy = fma_(f[2], ddy, dy0);            // d/dfy
+  float gz = dz;                              // d/dfz
+  s.g[0] = clamped[0] ? 0.0f : mul_(gx, O.inv_h);
+  s.g[1] = clamped[1] ? 0.0f : mul_(gy, O.inv_h);
+  s.g[2] = clamped[2] ? 0.0f : mul_(gz, O.inv_h);
+  if (kHess) {
+    float ih2 = mul_(O.inv_h, O.inv_h);
+    float hxy = fma_(f[2], sub_(ey1, ey0), ey0);
+    s.hxy = (clamped[0] || clamped[1]) ? 0.0f : mul_(hxy, ih2);
+    s.hxz = (clamped[0] || clamped[2]) ? 0.0f : mul_(dax, ih2);
+    s.hyz = (clamped[1] || clamped[2]) ? 0.0f : mul_(ddy, ih2);
+  }
+  s.outside = clamped[0] || clamped[1] || clamped[2];
+  s.e = 0.0f;
+  s.eh[0] = s.eh[1] = s.eh[2] = 0.0f;
+  if (s.outside) {
+    float dn2 = fma_(du[0], du[0], fma_(du[1], du[1], mul_(du[2], du[2])));
+    float dn = sqrtf(dn2);
+    float r = __fdiv_rn(1.0f, dn);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      s.eh[k] = mul_(du[k], r);
+      s.g[k] = add_(s.g[k], s.eh[k]);
+    }
+    s.e = mul_(O.h, dn);
+  }
+  s.phi = add_(val, s.e);
+}
+
+// ------------------------------------------------------------------ contact sims
+//
+// Simulation m has test velocity v_m = sgn_m * V * e_{ax_m} (m = 0: v = 0).
+__device__ __forceinline__ int sim_axis(int m) { return (m - 1) >> 1; }
+__device__ __forceinline__ float sim_sign(int m) { return (m & 1) ? 1.0f : -1.0f; }
+
+__device__ __forceinline__ void cross3(const float a[3], const float b[3], float c[3]) {
+  c[0] = fma_(a[1], b[2], -mul_(a[2], b[1]));
+  c[1] = fma_(a[2], b[0], -mul_(a[0], b[2]));
+  c[2] = fma_(a[0], b[1], -mul_(a[1], b[0]));
+}
+__device__ __forceinline__ float dot3(const float a[3], const float b[3]) {
+  return fma_(a[0], b[0], fma_(a[1], b[1], mul_(a[2], b[2])));
+}
+
+// Per-point quantities shared by the 7 simulations.
+struct PointState {
+  float p[3];       // world position (= object frame: canonical object pose)
+  float n[3];       // unit normal grad/|grad|
+  float rg;         // 1/|grad|
+  float phi_hat;    // dilated SDF
+};
+
+__device__ __forceinline__ void point_state(const SdfSample& s, const float p[3], float r_dil, PointState& ps) {
+  float g2 = fma_(s.g[0], s.g[0], fma_(s.g[1], s.g[1], mul_(s.g[2], s.g[2])));
+  float rg = g2 > 0.0f ? rsqrtf(g2) : 0.0f;
+  ps.rg = rg;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    ps.p[k] = p[k];
+    ps.n[k] = mul_(s.g[k], rg);
+  }
+  ps.phi_hat = sub_(s.phi, r_dil);
+}
+
+// Constraint value on the plane through the query for simulation m:
+// phi_m = phi_hat - dt n . v_m.
+__device__ __forceinline__ float sim_phi(const PointState& ps, int m, float dtV) {
+  if (m == 0) return ps.phi_hat;
+  int ax = sim_axis(m);
+  return fma_(-sim_sign(m) * dtV, ps.n[ax], ps.phi_hat);
+}
+
+// Tangential unit vector and sin(angle(n, v_m)) for a moving simulation, written
+// without the cancellation of 1 - n_k^2: |e_k - n_k n| = sqrt(n_i^2 + n_j^2).
+__device__ __forceinline__ float sim_tangent(const PointState& ps, int m, float t[3]) {
+  int k = sim_axis(m);
+  int i = (k + 1) % 3, j = (k + 2) % 3;
+  float rho2 = fma_(ps.n[i], ps.n[i], mul_(ps.n[j], ps.n[j]));
+  if (!(rho2 > 0.0f)) {
+    t[0] = t[1] = t[2] = 0.0f;
+    return 0.0f;
+  }
+  float rr = rsqrtf(rho2);
+  float rho = mul_(rho2, rr);
+  float sg = sim_sign(m);
+  float c = -sg * ps.n[k] * rr;
+  t[k] = sg * rho;
+  t[i] = c * ps.n[i];
+  t[j] = c * ps.n[j];
+  return rho;
+}
+
+// Forward of one contact in simulation m (C > 0): the correction of Eq. (1) as
+// a generalised force f = -(lambda_n n + lambda_t t) with lever d = p - x_pred.
+__device__ __forceinline__ void contact_force(const PointState& ps, int m, float C, const ParamsDev& P,
+                                              const ObjDev& O, float f[3], float d[3]) {
+  d[0] = ps.p[0];
+  d[1] = ps.p[1];
+  d[2] = ps.p[2];
+  float dtV = P.dt * P.V;
+  if (m > 0) d[sim_axis(m)] -= sim_sign(m) * dtV;
+  float un[3];
+  cross3(d, ps.n, un);
+  float wn = fma_(O.inv_inertia, dot3(un, un), O.inv_mass);
+  float lam_n = C / wn;
+  f[0] = -lam_n * ps.n[0];
+  f[1] = -lam_n * ps.n[1];
+  f[2] = -lam_n * ps.n[2];
+  if (m > 0) {
+    float t[3];
+    float rho = sim_tangent(ps, m, t);
+    if (rho > 0.0f) {
+      float sigma = dtV * rho;
+      float ut[3];
+      cross3(d, t, ut);
+      float wt = fma_(O.inv_inertia, dot3(ut, ut), O.inv_mass);
+      float muC = P.mu * C;
+      float lam_t = (sigma <= muC ? sigma : muC) / wt;
+      f[0] -= lam_t * t[0];
+      f[1] -= lam_t * t[1];
+      f[2] -= lam_t * t[2];
+    }
+  }
+}
+
+// Adjoint of one simulation at one point.  Inputs: the wrench adjoint of the
+// simulation (Gl = dL/dW_lin, Ga = dL/dW_ang), the constraint value phi_m and
+// flag kappa.  Accumulates dL/dphi_hat, dL/dn and dL/dp (through the lever).
+// C = max(0, -phi_m) with the leaky rule: dC/dphi = -1 in contact, -alpha not.
+__device__ __forceinline__ void sim_adjoint(const PointState& ps, int m, float phi_m, bool kappa,
+                                            const float Gl[3], const float Ga[3], const ParamsDev& P,
+                                            const ObjDev& O, float extra_dC, float& d_phi_hat,
+                                            float dn[3], float dp[3]) {
+  const float dtV = P.dt * P.V;
+  float d[3] = {ps.p[0], ps.p[1], ps.p[2]};
+  if (m > 0) d[sim_axis(m)] -= sim_sign(m) * dtV;
+  float C = kappa ? -phi_m : 0.0f;
+  // gf = dL/df = Gl + Ga x d
+  float gad[3];
+  cross3(Ga, d, gad);
+  float gf[3] = {Gl[0] + gad[0], Gl[1] + gad[1], Gl[2] + gad[2]};
+  float un[3];
+  cross3(d, ps.n, un);
+  float wn = fma_(O.inv_inertia, dot3(un, un), O.inv_mass);
+  float rwn = __fdividef(1.0f, wn);
+  float dlam_n = -dot3(gf, ps.n);
+  float dC = dlam_n * rwn + extra_dC;
+  float t[3] = {0.0f, 0.0f, 0.0f};
+  float rho = 0.0f, sigma = 0.0f, rwt = 0.0f, dlam_t = 0.0f;
+  float ut[3] = {0.0f, 0.0f, 0.0f};
+  bool stat = false;
+  if (m > 0) {
+    rho = sim_tangent(ps, m, t);
+    if (rho > 0.0f) {
+      sigma = dtV * rho;
+      cross3(d, t, ut);
+      float wt = fma_(O.inv_inertia, dot3(ut, ut), O.inv_mass);
+      rwt = __fdividef(1.0f, wt);
+      dlam_t = -dot3(gf, t);
+      stat = sigma <= P.mu * C;
+      if (!stat) dC += P.mu * dlam_t * rwt;      // kinetic: lambda_t = mu C / w_t
+    }
+  }
+  if (C > 0.0f) {
+    // terms that carry lambda (zero when the point is not in contact)
+    float lam_n = C * rwn;
+    float lam_t = 0.0f;
+    if (rho > 0.0f) lam_t = (stat ? sigma : P.mu * C) * rwt;
+    float f[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) f[k] = -(lam_n * ps.n[k] + lam_t * t[k]);
+    // torque lever: d(d x f).Ga/dd = f x Ga
+    float fxg[3];
+    cross3(f, Ga, fxg);
+    float dd[3] = {fxg[0], fxg[1], fxg[2]};
+    // f = -lam_n n: dn += -lam_n gf
+    float dnl[3] = {-lam_n * gf[0], -lam_n * gf[1], -lam_n * gf[2]};
+    // lam_n = C / w_n, w_n = 1/m + |u_n|^2 / I, u_n = d x n
+    float dwn = -dlam_n * lam_n * rwn;
+    float dun[3] = {2.0f * O.inv_inertia * dwn * un[0], 2.0f * O.inv_inertia * dwn * un[1],
+                    2.0f * O.inv_inertia * dwn * un[2]};
+    float tmp[3];
+    cross3(ps.n, dun, tmp);   // d(d x n).dun/dd = n x dun
+    dd[0] += tmp[0]; dd[1] += tmp[1]; dd[2] += tmp[2];
+    cross3(dun, d, tmp);      // d(d x n).dun/dn = dun x d
+    dnl[0] += tmp[0]; dnl[1] += tmp[1]; dnl[2] += tmp[2];
+    if (rho > 0.0f) {
+      // f = -lam_t t: dt += -lam_t gf
+      float dtt[3] = {-lam_t * gf[0], -lam_t * gf[1], -lam_t * gf[2]};
+      float dsig = stat ? dlam_t * rwt : 0.0f;
+      float dwt = -dlam_t * lam_t * rwt;
+      float dut[3] = {2.0f * O.inv_inertia * dwt * ut[0], 2.0f * O.inv_inertia * dwt * ut[1],
+                      2.0f * O.inv_inertia * dwt * ut[2]};
+      cross3(t, dut, tmp);
+      dd[0] += tmp[0]; dd[1] += tmp[1]; dd[2] += tmp[2];
+      cross3(dut, d, tmp);
+      dtt[0] += tmp[0]; dtt[1] += tmp[1]; dtt[2] += tmp[2];
+      // t = s/sigma, sigma = |s|: ds = (dt - (t.dt) t)/sigma + dsig t
+      float tdt = dot3(t, dtt);
+      float rs = __fdividef(1.0f, sigma);
+      float ds[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) ds[k] = (dtt[k] - tdt * t[k]) * rs + dsig * t[k];
+      // s = c (e_k - n_k n), c = dt V sgn: dn += -c (n_k ds + (n.ds) e_k)
+      int ax = sim_axis(m);
+      float c = dtV * sim_sign(m);
+      float nds = dot3(ps.n, ds);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) dnl[k] -= c * ps.n[ax] * ds[k];
+      dnl[ax] -= c * nds;
+    }
+    dn[0] += dnl[0]; dn[1] += dnl[1]; dn[2] += dnl[2];
+    dp[0] += dd[0]; dp[1] += dd[1]; dp[2] += dd[2];
+  }
+  // C = max(0, -phi_m), leaky: dphi_m = -dC (contact) or -alpha dC
+  float dphi = kappa ? -dC : -P.alpha * dC;
+  d_phi_hat += dphi;
+  if (m > 0) dn[sim_axis(m)] -= sim_sign(m) * dtV * dphi;   // phi_m = phi_hat - dt V sgn n_k
+}
+
+// Adjoint of the SDF lookup and normalisation: given dL/dphi_hat, dL/dn and the
+// direct dL/dp, returns the total dL/dp.  n = g/|g|, g = grad phi(p), and the
+// Hessian of phi is the trilinear mixed part plus, outside the grid, the
+// curvature (I - eh eh^T)/e of the excess distance on the clamped axes.
+__device__ __forceinline__ void sdf_adjoint(const SdfSample& s, const PointState& ps, float d_phi_hat,
+                                            const float dn[3], float dp[3]) {
+  float ndn = dot3(ps.n, dn);
+  float dg[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) dg[k] = (dn[k] - ndn * ps.n[k]) * ps.rg;
+  dp[0] += d_phi_hat * s.g[0] + s.hxy * dg[1] + s.hxz * dg[2];
+  dp[1] += d_phi_hat * s.g[1] + s.hxy * dg[0] + s.hyz * dg[2];
+  dp[2] += d_phi_hat * s.g[2] + s.hxz * dg[0] + s.hyz * dg[1];
+  if (s.outside) {
+    // eh is zero on unclamped axes, so (I - eh eh^T) restricted to clamped axes
+    // is D_c - eh eh^T with D_c the clamped-axis mask (eh_k != 0 or clamped).
+    float re = __fdividef(1.0f, s.e);
+    float ehdg = dot3(s.eh, dg);
+    // clamped mask: an axis is clamped iff its trilinear slope was removed; the
+    // excess direction is nonzero exactly on clamped axes (u - u_c != 0).
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      float ck = (s.eh[k] != 0.0f) ? 1.0f : 0.0f;
+      dp[k] += (ck * dg[k] - s.eh[k] * ehdg) * re;
+    }
+  }
+}
+
+// Wrench adjoint per simulation and the loss, from the reduced wrenches.
+// xdot_m = v_m + W_lin inv_m / (N dt), thdot_m = W_ang inv_I / (N dt),
+// L_stable = (1/7) sum_m (|xdot_m| + |thdot_m|)  (Eq. 2).
+__device__ inline float stability_loss_and_adjoint(const float W[kSims][6], const float N[kSims],
+                                                   const ParamsDev& P, const ObjDev& O,
+                                                   float Gl[kSims][3], float Ga[kSims][3]) {
+  float L = 0.0f;
+  for (int m = 0; m < kSims; ++m) {
+    float Nc = N[m] > 1.0f ? N[m] : 1.0f;
+    float sl = O.inv_mass / (Nc * P.dt), sa = O.inv_inertia / (Nc * P.dt);
+    float v[3] = {0.0f, 0.0f, 0.0f};
+    if (m > 0) v[sim_axis(m)] = sim_sign(m) * P.V;
+    float xd[3], td[3];
+    for (int k = 0; k < 3; ++k) {
+      xd[k] = v[k] + W[m][k] * sl;
+      td[k] = W[m][3 + k] * sa;
+    }
+    float nx2 = xd[0] * xd[0] + xd[1] * xd[1] + xd[2] * xd[2];
+    float nt2 = td[0] * td[0] + td[1] * td[1] + td[2] * td[2];
+    float nx = sqrtf(nx2), nt = sqrtf(nt2);
+    L += nx + nt;
+    float ax = nx > 0.0f ? sl / (kSims * nx) : 0.0f;
+    float at = nt > 0.0f ? sa / (kSims * nt) : 0.0f;
+    for (int k = 0; k < 3; ++k) {
+      Gl[m][k] = xd[k] * ax;
+      Ga[m][k] = td[k] * at;
+    }
+  }
+  return L / kSims;
+}
+
+// Joint terms L_range (Eq. 3) and L_limit (Eq. 4) with their gradient into dth.
+__device__ inline float joint_losses(const HandDev& H, const float* th, const ParamsDev& P, float* dth) {
+  float s2 = 0.0f, lim = 0.0f;
+  for (int j = 0; j < H.J; ++j) {
+    float mid = 0.5f * (H.q_up[j] + H.q_low[j]);
+    float d = th[j] - mid;
+    s2 += d * d;
+    if (th[j] > H.q_up[j]) lim += th[j] - H.q_up[j];
+    if (th[j] < H.q_low[j]) lim += H.q_low[j] - th[j];
+  }
+  float rn = sqrtf(s2);
+  float inv = rn > 0.0f ? P.w_range / rn : 0.0f;
+  for (int j = 0; j < H.J; ++j) {
+    float mid = 0.5f * (H.q_up[j] + H.q_low[j]);
+    float g = (th[j] - mid) * inv;
+    if (th[j] > H.q_up[j]) g += P.w_limit;
+    if (th[j] < H.q_low[j]) g -= P.w_limit;
+    dth[j] = g;
+  }
+  return P.w_range * rn + P.w_limit * lim;
+}
+
+// Transpose of the left Jacobian of Exp applied to tau:
+// J_l(w)^T tau = tau - b (w x tau) + c (w x (w x tau)),
+// b = (1 - cos a)/a^2, c = (a - sin a)/a^3 (Taylor series below a = 0.5, where
+// a - sin a loses float32 digits).
+__device__ inline void exp_jacobian_T(const float w[3], const float tau[3], float out[3]) {
+  float a2 = w[0] * w[0] + w[1] * w[1] + w[2] * w[2];
+  float b, c;
+  if (a2 < 0.25f) {
+    b = 0.5f + a2 * (-1.0f / 24.0f + a2 * (1.0f / 720.0f + a2 * (-1.0f / 40320.0f)));
+    c = 1.0f / 6.0f + a2 * (-1.0f / 120.0f + a2 * (1.0f / 5040.0f + a2 * (-1.0f / 362880.0f)));
+  } else {
+    float a = sqrtf(a2);
+    float s, co;
+    sincosf(a, &s, &co);
+    float sh = sinf(0.5f * a);
+    b = 2.0f * sh * sh / a2;
+    c = (a - s) / (a2 * a);
+  }
+  float wt[3], wwt[3];
+  cross3(w, tau, wt);
+  cross3(w, wt, wwt);
+  for (int k = 0; k < 3; ++k) out[k] = tau[k] - b * wt[k] + c * wwt[k];
+}
+
+__device__ __forceinline__ float dilation_at(const ParamsDev& P, int k, int total_steps) {
+  if (P.schedule == 0) return P.r0;
+  int den = total_steps - 1 > 1 ? total_steps - 1 : 1;
+  float r = P.r0 * (1.0f - (float)k / (float)den);
+  return r > 0.0f ? r : 0.0f;
+}
+
+}  // namespace fg

@@ -1,0 +1,65 @@
+// Host-side internals shared by the translation units of libfastgraspd.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "fastgraspd.h"
+#include "fg_device.cuh"
+
+struct fg_hand {
+  fg::HandDev host;          // copy of the device descriptor (pts = device pointer)
+  fg::HandDev* dev;          // device copy of the descriptor
+  float4* pts;               // device [P]
+  int subtree_end[FG_MAX_LINKS];
+};
+
+struct fg_sdf {
+  fg::ObjDev host;           // grid = device pointer owned by this handle
+  float* grid;
+  size_t bytes;
+};
+
+struct fg_scene {
+  int n;
+  fg::ObjDev* dev;           // device [n]
+};
+
+namespace fg {
+
+void set_error(const std::string& msg);
+fg_status cuda_status(cudaError_t e, const char* what);
+ParamsDev params_from(const fg_params* p);
+int device_sm_count();
+
+// fused kernels (fg_fused.cu)
+enum FusedMode { kModeWrench = 0, kModeLossGrad = 1, kModeOptimize = 2 };
+struct FusedArgs {
+  const HandDev* hand;
+  const ObjDev* objs;
+  int n_obj;
+  const int* obj_of_cand;
+  float* q;
+  int B;
+  ParamsDev P;
+  float r_fixed;
+  int step0, total_steps, nsteps;
+  float* loss;
+  float* grad;
+  float* wrench;
+  int* ncontact;
+  uint32_t* bits;
+};
+cudaError_t launch_fused(int mode, const FusedArgs& a, const fg_hand* h, cudaStream_t st);
+
+// per-stage kernels (fg_plain.cu)
+size_t plain_workspace_bytes(const fg_hand* h, int B);
+cudaError_t launch_plain_step(const fg_hand* h, const fg_scene* sc, const int* obj_of_cand, float* q, int B,
+                              const ParamsDev& P, int step, int total_steps, int nsteps, float* loss,
+                              void* ws, cudaStream_t st);
+cudaError_t launch_fk_points(const fg_hand* h, const float* q, int B, float* pts, cudaStream_t st);
+cudaError_t launch_sdf_query(const ObjDev& o, const float* pts, int n, float r, float* phi, float* grad,
+                             cudaStream_t st);
+
+}  // namespace fg

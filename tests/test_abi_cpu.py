@@ -1,0 +1,94 @@
+"""The C-ABI library builds, loads and exports what include/fastgraspd.h declares
+(no GPU: no compute calls, only host-side entry points)."""
+
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for f in sorted(os.listdir(inc)):
+        if not f.endswith(".h"):
+            continue
+        txt = open(os.path.join(inc, f)).read()
+        txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+        txt = re.sub(r"//[^\n]*", "", txt)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*(fg_[A-Za-z0-9_]+)\s*\(", txt, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2306_08132_gb300.build import build_library
+    build_library()
+    from paper_2306_08132_gb300 import _lib
+    return _lib.load()
+
+
+def test_header_declares_the_hot_path_calls():
+    names = _declared_functions()
+    for n in ("fg_fk", "fg_sdf_query", "fg_contact_wrench", "fg_loss_and_grad", "fg_optimize_step",
+              "fg_hand_create", "fg_sdf_create", "fg_scene_create", "fg_last_error"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in sorted(_declared_functions()) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_binding_covers_every_declared_symbol():
+    from paper_2306_08132_gb300 import _lib
+    assert _declared_functions() <= set(_lib.SIGNATURES)
+
+
+def test_host_only_entry_points(lib):
+    a, b = C.c_int(), C.c_int()
+    assert lib.fg_version(C.byref(a), C.byref(b)) == 0 and a.value >= 1
+    assert lib.fg_status_string(3) == b"FG_ERR_BUDGET"
+    assert lib.fg_status_string(99) == b"FG_ERR_UNKNOWN"
+    buf = C.create_string_buffer(8)
+    assert lib.fg_last_error(buf, 8) == 0
+    assert lib.fg_last_error(None, 8) == 1
+
+
+def test_invalid_descriptors_are_rejected_before_any_device_work(lib):
+    """Validation runs on the host and returns FG_ERR_INVALID with a message."""
+    import numpy as np
+    from paper_2306_08132_gb300 import _lib
+    out = C.c_void_p()
+    assert lib.fg_hand_create(None, C.byref(out)) == 1
+    par = np.array([-1, 0, 0], dtype=np.int32)
+    bad_par = np.array([-1, 2, 0], dtype=np.int32)          # not topological
+    tf = np.zeros((3, 12), dtype=np.float32)
+    ax = np.array([[0, 0, 0], [1, 0, 0], [0, 2, 0]], dtype=np.float32)   # non-unit axis
+    lo = np.zeros(2, dtype=np.float32)
+    up = np.ones(2, dtype=np.float32)
+    pts = np.zeros((4, 3), dtype=np.float32)
+    lop = np.array([0, 1, 2, 1], dtype=np.int32)            # not sorted
+    P = lambda a, t: a.ctypes.data_as(C.POINTER(t))
+    d = _lib.HandDesc(3, 4, P(bad_par, C.c_int), P(tf, C.c_float), P(ax, C.c_float), P(lo, C.c_float),
+                      P(up, C.c_float), P(pts, C.c_float), P(lop, C.c_int))
+    assert lib.fg_hand_create(C.byref(d), C.byref(out)) == 1
+    assert b"topological" in _last(lib)
+    d.parent = P(par, C.c_int)
+    assert lib.fg_hand_create(C.byref(d), C.byref(out)) == 1
+    assert b"unit" in _last(lib)
+    org = (C.c_float * 3)(0, 0, 0)
+    assert lib.fg_sdf_create(None, 4, 4, 4, org, 0.1, 1.0, 1.0, C.byref(out)) == 1
+    g = np.zeros(8, dtype=np.float32)
+    assert lib.fg_sdf_create(g.ctypes.data_as(C.c_void_p), 1, 2, 2, org, 0.1, 1.0, 1.0, C.byref(out)) == 1
+    assert lib.fg_scene_create(None, 0, C.byref(out)) == 1
+
+
+def _last(lib):
+    buf = C.create_string_buffer(512)
+    lib.fg_last_error(buf, 512)
+    return buf.value
