@@ -196,6 +196,29 @@ fg_status fg_optimize_step_plain(const fg_hand* hand, const fg_scene* scene, con
                                  int total_steps, int nsteps, float* loss, void* workspace,
                                  size_t workspace_bytes, void* stream);
 
+/* ------------------------------------------------------------------ tuning */
+
+/* The fused kernels are compiled in several configurations: warps per
+ * candidate (points per warp = P / (32 * warps)) and the minimum number of
+ * resident CTAs per SM the register allocation is held to.  The selection is
+ * per device (the current one) and applies to fg_loss_and_grad and
+ * fg_optimize_step; it changes no result beyond float32 summation order. */
+fg_status fg_fused_config_count(int* n);
+fg_status fg_fused_config_info(int index, int* warps_per_candidate, int* min_ctas_per_sm);
+/* index in [0, count) selects a configuration; -1 restores the default. */
+fg_status fg_fused_config_select(int index);
+fg_status fg_fused_config_current(int* index);
+
+/* Autotuner: times every configuration of fg_optimize_step on this workload
+ * (q is copied to a scratch buffer, not modified), reps timed launches each
+ * after one warm-up, selects the fastest for the current device and returns its
+ * index in *best (nullable) and the mean times in host_times_ms[count]
+ * (nullable).  Synchronises `stream`; allocates its scratch with
+ * cudaMallocAsync on `stream`.  Errors: FG_ERR_INVALID, FG_ERR_CUDA, FG_ERR_OOM. */
+fg_status fg_autotune(const fg_hand* hand, const fg_scene* scene, const int* obj_of_cand, const float* q, int B,
+                      const fg_params* host_params, int step, int total_steps, int nsteps, int reps,
+                      float* host_times_ms, int* best, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

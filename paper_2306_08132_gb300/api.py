@@ -215,3 +215,42 @@ def optimize_step_plain(hand: Hand, scene: Scene, q: torch.Tensor, params: dict,
                                              _dptr(loss, "loss", shape=(B,)), C.c_void_p(aligned), avail,
                                              _stream()), "fg_optimize_step_plain")
     return loss
+
+
+def fused_configs() -> list[tuple[int, int]]:
+    """Compiled fused-kernel configurations: (warps per candidate, min CTAs per SM)."""
+    lib = _lib.load()
+    n = C.c_int()
+    check(lib.fg_fused_config_count(C.byref(n)), "fg_fused_config_count")
+    out = []
+    for i in range(n.value):
+        a, b = C.c_int(), C.c_int()
+        check(lib.fg_fused_config_info(i, C.byref(a), C.byref(b)), "fg_fused_config_info")
+        out.append((a.value, b.value))
+    return out
+
+
+def fused_config_select(index: int) -> None:
+    check(_lib.load().fg_fused_config_select(int(index)), "fg_fused_config_select")
+
+
+def fused_config_current() -> int:
+    i = C.c_int()
+    check(_lib.load().fg_fused_config_current(C.byref(i)), "fg_fused_config_current")
+    return i.value
+
+
+def autotune(hand: Hand, scene: Scene, q: torch.Tensor, params: dict, step: int = 0, total_steps: int = 1,
+             nsteps: int = 1, obj_of_cand: torch.Tensor | None = None, reps: int = 3):
+    """Time every fused configuration on this workload and select the fastest.
+    Returns (best index, list of mean milliseconds per configuration)."""
+    B = q.shape[0]
+    _dptr(q, "q", shape=(B, hand.D))
+    n = len(fused_configs())
+    times = (C.c_float * n)()
+    best = C.c_int()
+    prm = make_params(params)
+    check(_lib.load().fg_autotune(hand.handle, scene.handle, _oc(obj_of_cand, B), _dptr(q, "q"), B, C.byref(prm),
+                                  int(step), int(total_steps), int(nsteps), int(reps), times, C.byref(best),
+                                  _stream()), "fg_autotune")
+    return best.value, [float(t) for t in times]

@@ -330,6 +330,7 @@ fg_status fg_contact_wrench(const fg_hand* h, const fg_scene* sc, const int* oc,
   if (!std::isfinite(r)) return invalid("fg_contact_wrench: non-finite r_dil");
   FusedArgs a{};
   a.hand = h->dev;
+  a.hand_D = h->host.D;
   a.objs = sc->dev;
   a.n_obj = sc->n;
   a.obj_of_cand = oc;
@@ -353,6 +354,7 @@ fg_status fg_loss_and_grad(const fg_hand* h, const fg_scene* sc, const int* oc, 
   if (!std::isfinite(r)) return invalid("fg_loss_and_grad: non-finite r_dil");
   FusedArgs a{};
   a.hand = h->dev;
+  a.hand_D = h->host.D;
   a.objs = sc->dev;
   a.n_obj = sc->n;
   a.obj_of_cand = oc;
@@ -376,6 +378,7 @@ fg_status fg_optimize_step(const fg_hand* h, const fg_scene* sc, const int* oc, 
   if (!q) return invalid("fg_optimize_step: NULL q");
   FusedArgs a{};
   a.hand = h->dev;
+  a.hand_D = h->host.D;
   a.objs = sc->dev;
   a.n_obj = sc->n;
   a.obj_of_cand = oc;
@@ -409,6 +412,52 @@ fg_status fg_optimize_step_plain(const fg_hand* h, const fg_scene* sc, const int
   return cuda_status(launch_plain_step(h, sc, oc, q, B, params_from(p), step, total_steps, nsteps, loss, ws,
                                        (cudaStream_t)stream),
                      "fg_optimize_step_plain");
+}
+
+fg_status fg_fused_config_count(int* n) {
+  if (!n) return invalid("fg_fused_config_count: NULL");
+  *n = fused_config_count();
+  return FG_OK;
+}
+
+fg_status fg_fused_config_info(int index, int* nw, int* minb) {
+  if (index < 0 || index >= fused_config_count() || !nw || !minb) return invalid("fg_fused_config_info: bad index");
+  fused_config_info(index, nw, minb);
+  return FG_OK;
+}
+
+fg_status fg_fused_config_select(int index) {
+  if (index < -1 || index >= fused_config_count()) return invalid("fg_fused_config_select: bad index");
+  fused_config_select(index);
+  return FG_OK;
+}
+
+fg_status fg_fused_config_current(int* index) {
+  if (!index) return invalid("fg_fused_config_current: NULL");
+  *index = fused_config_current();
+  return FG_OK;
+}
+
+fg_status fg_autotune(const fg_hand* h, const fg_scene* sc, const int* oc, const float* q, int B, const fg_params* p,
+                      int step, int total_steps, int nsteps, int reps, float* host_times_ms, int* best,
+                      void* stream) {
+  fg_status st = check_common("fg_autotune", h, sc, B, p);
+  if (st != FG_OK) return st;
+  if (B < 1 || !q) return invalid("fg_autotune: need B >= 1 and q");
+  if (nsteps < 1 || reps < 1 || step < 0 || total_steps < 1) return invalid("fg_autotune: bad step arguments");
+  FusedArgs a{};
+  a.hand = h->dev;
+  a.hand_D = h->host.D;
+  a.objs = sc->dev;
+  a.n_obj = sc->n;
+  a.obj_of_cand = oc;
+  a.q = const_cast<float*>(q);
+  a.B = B;
+  a.P = params_from(p);
+  a.step0 = step;
+  a.total_steps = total_steps;
+  a.nsteps = nsteps;
+  return cuda_status(autotune_fused(a, reps, host_times_ms, best, (cudaStream_t)stream), "fg_autotune");
 }
 
 }  // extern "C"

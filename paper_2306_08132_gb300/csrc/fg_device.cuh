@@ -276,156 +276,262 @@ __device__ __forceinline__ void point_state(const SdfSample& s, const float p[3]
 // phi_m = phi_hat - dt n . v_m.
 __device__ __forceinline__ float sim_phi(const PointState& ps, int m, float dtV) {
   if (m == 0) return ps.phi_hat;
-  int ax = sim_axis(m);
-  return fma_(-sim_sign(m) * dtV, ps.n[ax], ps.phi_hat);
+  const int ax = sim_axis(m);
+  const float nk = ax == 0 ? ps.n[0] : (ax == 1 ? ps.n[1] : ps.n[2]);
+  return fma_(-sim_sign(m) * dtV, nk, ps.phi_hat);
 }
 
-// Tangential unit vector and sin(angle(n, v_m)) for a moving simulation, written
-// without the cancellation of 1 - n_k^2: |e_k - n_k n| = sqrt(n_i^2 + n_j^2).
-__device__ __forceinline__ float sim_tangent(const PointState& ps, int m, float t[3]) {
-  int k = sim_axis(m);
-  int i = (k + 1) % 3, j = (k + 2) % 3;
-  float rho2 = fma_(ps.n[i], ps.n[i], mul_(ps.n[j], ps.n[j]));
-  if (!(rho2 > 0.0f)) {
-    t[0] = t[1] = t[2] = 0.0f;
-    return 0.0f;
-  }
-  float rr = rsqrtf(rho2);
-  float rho = mul_(rho2, rr);
-  float sg = sim_sign(m);
-  float c = -sg * ps.n[k] * rr;
-  t[k] = sg * rho;
-  t[i] = c * ps.n[i];
-  t[j] = c * ps.n[j];
+// Unit direction of test velocity m (zero for m = 0), by selects so that a
+// runtime m indexes no local array.
+__device__ __forceinline__ void sim_dir(int m, float vd[3]) {
+  const int k = (m - 1) >> 1;
+  const float sg = sim_sign(m);
+  vd[0] = (m > 0 && k == 0) ? sg : 0.0f;
+  vd[1] = (m > 0 && k == 1) ? sg : 0.0f;
+  vd[2] = (m > 0 && k == 2) ? sg : 0.0f;
+}
+
+// Tangential unit vector t = (v - (v.n) n)/|v - (v.n) n| of a moving simulation
+// and rho = |e_k - n_k n| = sin(angle(n, v_m)).  rho^2 is the sum of the squares
+// of the two other components of n (no cancellation of 1 - n_k^2).  Returns 0
+// (and t = 0) when m = 0 or n is parallel to the velocity.
+__device__ __forceinline__ float sim_tangent(const float n[3], int m, float t[3]) {
+  t[0] = t[1] = t[2] = 0.0f;
+  if (m == 0) return 0.0f;
+  const int k = (m - 1) >> 1;
+  const float sg = sim_sign(m);
+  const bool k0 = k == 0, k1 = k == 1, k2 = k == 2;
+  const float nk = k0 ? n[0] : (k2 ? n[2] : n[1]);
+  const float ea = k0 ? n[1] : n[0];
+  const float eb = k2 ? n[1] : n[2];
+  const float rho2 = fma_(ea, ea, mul_(eb, eb));
+  if (!(rho2 > 0.0f)) return 0.0f;
+  const float rr = rsqrtf(rho2);
+  const float rho = mul_(rho2, rr);
+  const float cc = -sg * nk * rr;
+  t[0] = k0 ? sg * rho : cc * n[0];
+  t[1] = k1 ? sg * rho : cc * n[1];
+  t[2] = k2 ? sg * rho : cc * n[2];
   return rho;
 }
 
 // Forward of one contact in simulation m (C > 0): the correction of Eq. (1) as
 // a generalised force f = -(lambda_n n + lambda_t t) with lever d = p - x_pred.
+// Static friction when sigma <= mu C (sigma = dt V rho, the tangential
+// displacement), kinetic otherwise.
 __device__ __forceinline__ void contact_force(const PointState& ps, int m, float C, const ParamsDev& P,
                                               const ObjDev& O, float f[3], float d[3]) {
-  d[0] = ps.p[0];
-  d[1] = ps.p[1];
-  d[2] = ps.p[2];
-  float dtV = P.dt * P.V;
-  if (m > 0) d[sim_axis(m)] -= sim_sign(m) * dtV;
+  const float dtV = P.dt * P.V;
+  float vd[3];
+  sim_dir(m, vd);
+  d[0] = fma_(-dtV, vd[0], ps.p[0]);
+  d[1] = fma_(-dtV, vd[1], ps.p[1]);
+  d[2] = fma_(-dtV, vd[2], ps.p[2]);
   float un[3];
   cross3(d, ps.n, un);
-  float wn = fma_(O.inv_inertia, dot3(un, un), O.inv_mass);
-  float lam_n = C / wn;
+  const float wn = fma_(O.inv_inertia, dot3(un, un), O.inv_mass);
+  const float lam_n = C / wn;
   f[0] = -lam_n * ps.n[0];
   f[1] = -lam_n * ps.n[1];
   f[2] = -lam_n * ps.n[2];
-  if (m > 0) {
-    float t[3];
-    float rho = sim_tangent(ps, m, t);
-    if (rho > 0.0f) {
-      float sigma = dtV * rho;
-      float ut[3];
-      cross3(d, t, ut);
-      float wt = fma_(O.inv_inertia, dot3(ut, ut), O.inv_mass);
-      float muC = P.mu * C;
-      float lam_t = (sigma <= muC ? sigma : muC) / wt;
-      f[0] -= lam_t * t[0];
-      f[1] -= lam_t * t[1];
-      f[2] -= lam_t * t[2];
-    }
+  float t[3];
+  const float rho = sim_tangent(ps.n, m, t);
+  if (rho > 0.0f) {
+    const float sigma = mul_(dtV, rho);
+    float ut[3];
+    cross3(d, t, ut);
+    const float wt = fma_(O.inv_inertia, dot3(ut, ut), O.inv_mass);
+    const float muC = mul_(P.mu, C);
+    const float lam_t = (sigma <= muC ? sigma : muC) / wt;
+    f[0] -= lam_t * t[0];
+    f[1] -= lam_t * t[1];
+    f[2] -= lam_t * t[2];
   }
 }
 
-// Adjoint of one simulation at one point.  Inputs: the wrench adjoint of the
-// simulation (Gl = dL/dW_lin, Ga = dL/dW_ang), the constraint value phi_m and
-// flag kappa.  Accumulates dL/dphi_hat, dL/dn and dL/dp (through the lever).
-// C = max(0, -phi_m) with the leaky rule: dC/dphi = -1 in contact, -alpha not.
+// Adjoint of one simulation at one point (general path, any C).  Inputs: the
+// wrench adjoint of the simulation (Gl = dL/dW_lin, Ga = dL/dW_ang), the
+// constraint value phi_m and flag kappa.  Accumulates dL/dphi_hat, dL/dn and
+// dL/dp (through the lever).  C = max(0, -phi_m) with the leaky rule:
+// dC/dphi = -1 in contact, -alpha otherwise (Sec. III-C).
 __device__ __forceinline__ void sim_adjoint(const PointState& ps, int m, float phi_m, bool kappa,
                                             const float Gl[3], const float Ga[3], const ParamsDev& P,
-                                            const ObjDev& O, float extra_dC, float& d_phi_hat,
-                                            float dn[3], float dp[3]) {
+                                            const ObjDev& O, float extra_dC, float& d_phi_hat, float dn[3],
+                                            float dp[3]) {
   const float dtV = P.dt * P.V;
-  float d[3] = {ps.p[0], ps.p[1], ps.p[2]};
-  if (m > 0) d[sim_axis(m)] -= sim_sign(m) * dtV;
-  float C = kappa ? -phi_m : 0.0f;
+  float vd[3];
+  sim_dir(m, vd);
+  const float d[3] = {fma_(-dtV, vd[0], ps.p[0]), fma_(-dtV, vd[1], ps.p[1]), fma_(-dtV, vd[2], ps.p[2])};
+  const float C = kappa ? -phi_m : 0.0f;
   // gf = dL/df = Gl + Ga x d
   float gad[3];
   cross3(Ga, d, gad);
-  float gf[3] = {Gl[0] + gad[0], Gl[1] + gad[1], Gl[2] + gad[2]};
+  const float gf[3] = {Gl[0] + gad[0], Gl[1] + gad[1], Gl[2] + gad[2]};
   float un[3];
   cross3(d, ps.n, un);
-  float wn = fma_(O.inv_inertia, dot3(un, un), O.inv_mass);
-  float rwn = __fdividef(1.0f, wn);
-  float dlam_n = -dot3(gf, ps.n);
+  const float wn = fma_(O.inv_inertia, dot3(un, un), O.inv_mass);
+  const float rwn = __fdividef(1.0f, wn);
+  const float dlam_n = -dot3(gf, ps.n);
   float dC = dlam_n * rwn + extra_dC;
-  float t[3] = {0.0f, 0.0f, 0.0f};
-  float rho = 0.0f, sigma = 0.0f, rwt = 0.0f, dlam_t = 0.0f;
+  float t[3];
+  const float rho = sim_tangent(ps.n, m, t);
+  float sigma = 0.0f, rwt = 0.0f, dlam_t = 0.0f;
   float ut[3] = {0.0f, 0.0f, 0.0f};
   bool stat = false;
-  if (m > 0) {
-    rho = sim_tangent(ps, m, t);
-    if (rho > 0.0f) {
-      sigma = dtV * rho;
-      cross3(d, t, ut);
-      float wt = fma_(O.inv_inertia, dot3(ut, ut), O.inv_mass);
-      rwt = __fdividef(1.0f, wt);
-      dlam_t = -dot3(gf, t);
-      stat = sigma <= P.mu * C;
-      if (!stat) dC += P.mu * dlam_t * rwt;      // kinetic: lambda_t = mu C / w_t
-    }
+  if (rho > 0.0f) {
+    sigma = mul_(dtV, rho);
+    cross3(d, t, ut);
+    const float wt = fma_(O.inv_inertia, dot3(ut, ut), O.inv_mass);
+    rwt = __fdividef(1.0f, wt);
+    dlam_t = -dot3(gf, t);
+    stat = sigma <= mul_(P.mu, C);
+    if (!stat) dC += P.mu * dlam_t * rwt;      // kinetic: lambda_t = mu C / w_t
   }
   if (C > 0.0f) {
     // terms that carry lambda (zero when the point is not in contact)
-    float lam_n = C * rwn;
-    float lam_t = 0.0f;
-    if (rho > 0.0f) lam_t = (stat ? sigma : P.mu * C) * rwt;
+    const float lam_n = C * rwn;
+    const float lam_t = rho > 0.0f ? (stat ? sigma : P.mu * C) * rwt : 0.0f;
     float f[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) f[k] = -(lam_n * ps.n[k] + lam_t * t[k]);
-    // torque lever: d(d x f).Ga/dd = f x Ga
-    float fxg[3];
-    cross3(f, Ga, fxg);
-    float dd[3] = {fxg[0], fxg[1], fxg[2]};
-    // f = -lam_n n: dn += -lam_n gf
-    float dnl[3] = {-lam_n * gf[0], -lam_n * gf[1], -lam_n * gf[2]};
+    float dd[3];
+    cross3(f, Ga, dd);                               // d(d x f).Ga/dd = f x Ga
+    float dnl[3] = {-lam_n * gf[0], -lam_n * gf[1], -lam_n * gf[2]};   // f = -lam_n n
     // lam_n = C / w_n, w_n = 1/m + |u_n|^2 / I, u_n = d x n
-    float dwn = -dlam_n * lam_n * rwn;
-    float dun[3] = {2.0f * O.inv_inertia * dwn * un[0], 2.0f * O.inv_inertia * dwn * un[1],
-                    2.0f * O.inv_inertia * dwn * un[2]};
+    const float dwn = -dlam_n * lam_n * rwn;
+    const float sn = 2.0f * O.inv_inertia * dwn;
+    const float dun[3] = {sn * un[0], sn * un[1], sn * un[2]};
     float tmp[3];
-    cross3(ps.n, dun, tmp);   // d(d x n).dun/dd = n x dun
+    cross3(ps.n, dun, tmp);                          // d(d x n).dun/dd = n x dun
     dd[0] += tmp[0]; dd[1] += tmp[1]; dd[2] += tmp[2];
-    cross3(dun, d, tmp);      // d(d x n).dun/dn = dun x d
+    cross3(dun, d, tmp);                             // d(d x n).dun/dn = dun x d
     dnl[0] += tmp[0]; dnl[1] += tmp[1]; dnl[2] += tmp[2];
     if (rho > 0.0f) {
-      // f = -lam_t t: dt += -lam_t gf
-      float dtt[3] = {-lam_t * gf[0], -lam_t * gf[1], -lam_t * gf[2]};
-      float dsig = stat ? dlam_t * rwt : 0.0f;
-      float dwt = -dlam_t * lam_t * rwt;
-      float dut[3] = {2.0f * O.inv_inertia * dwt * ut[0], 2.0f * O.inv_inertia * dwt * ut[1],
-                      2.0f * O.inv_inertia * dwt * ut[2]};
+      float dtt[3] = {-lam_t * gf[0], -lam_t * gf[1], -lam_t * gf[2]};   // f = -lam_t t
+      const float dsig = stat ? dlam_t * rwt : 0.0f;
+      const float dwt = -dlam_t * lam_t * rwt;
+      const float st = 2.0f * O.inv_inertia * dwt;
+      const float dut[3] = {st * ut[0], st * ut[1], st * ut[2]};
       cross3(t, dut, tmp);
       dd[0] += tmp[0]; dd[1] += tmp[1]; dd[2] += tmp[2];
       cross3(dut, d, tmp);
       dtt[0] += tmp[0]; dtt[1] += tmp[1]; dtt[2] += tmp[2];
       // t = s/sigma, sigma = |s|: ds = (dt - (t.dt) t)/sigma + dsig t
-      float tdt = dot3(t, dtt);
-      float rs = __fdividef(1.0f, sigma);
+      const float tdt = dot3(t, dtt);
+      const float rs = __fdividef(1.0f, sigma);
       float ds[3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) ds[k] = (dtt[k] - tdt * t[k]) * rs + dsig * t[k];
-      // s = c (e_k - n_k n), c = dt V sgn: dn += -c (n_k ds + (n.ds) e_k)
-      int ax = sim_axis(m);
-      float c = dtV * sim_sign(m);
-      float nds = dot3(ps.n, ds);
+      // s = dt V (vd - (vd.n) n): dn += -dt V ((vd.n) ds + (n.ds) vd)
+      const float vn = dot3(vd, ps.n), nds = dot3(ps.n, ds);
 #pragma unroll
-      for (int k = 0; k < 3; ++k) dnl[k] -= c * ps.n[ax] * ds[k];
-      dnl[ax] -= c * nds;
+      for (int k = 0; k < 3; ++k) dnl[k] -= dtV * (vn * ds[k] + nds * vd[k]);
     }
     dn[0] += dnl[0]; dn[1] += dnl[1]; dn[2] += dnl[2];
     dp[0] += dd[0]; dp[1] += dd[1]; dp[2] += dd[2];
   }
   // C = max(0, -phi_m), leaky: dphi_m = -dC (contact) or -alpha dC
-  float dphi = kappa ? -dC : -P.alpha * dC;
+  const float dphi = kappa ? -dC : -P.alpha * dC;
   d_phi_hat += dphi;
-  if (m > 0) dn[sim_axis(m)] -= sim_sign(m) * dtV * dphi;   // phi_m = phi_hat - dt V sgn n_k
+  // phi_m = phi_hat - dt n . v_m
+#pragma unroll
+  for (int k = 0; k < 3; ++k) dn[k] -= dtV * vd[k] * dphi;
+}
+
+// Component k of a float4 (k is a compile-time constant after unrolling).
+__device__ __forceinline__ float f4c(const float4& v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
+
+// Adjoint of all 7 simulations at one point.  A simulation whose constraint is
+// active (phi_m < 0) takes the general path (sim_adjoint).  An inactive one has
+// C = 0, so only the leaky slope survives:
+//   dC = -(gf.n)/w_n - mu (gf.t)/w_t   (kinetic branch, sigma > mu C = 0),
+//   dphi_m = -alpha dC,
+// with gf = Gl_m + Ga_m x d_m, d_m = p - s c e_k, t = s tau_k.  Every term is
+// expanded around quantities shared by the simulations of the point:
+//   d x n   = U - s c E_k,      U = p x n,     E_k = e_k x n,  |E_k|^2 = n_i^2 + n_j^2
+//   d x tau = T_k - s c F_k,    T_k = p x tau_k, F_k = e_k x tau_k
+// so that each inactive simulation costs a few dot products.  G4 holds
+// (Gl_m, 0), (Ga_m, 0) for m = 0..6.
+__device__ __forceinline__ void point_sims_adjoint(const PointState& ps, const float4* __restrict__ G4,
+                                                   const ParamsDev& P, const ObjDev& O, float& dphi, float dn[3],
+                                                   float dp[3]) {
+  const float c = P.dt * P.V;
+  const float a = O.inv_mass, b = O.inv_inertia;
+  const float* n = ps.n;
+  float U[3];
+  cross3(ps.p, n, U);
+  const float Uu = dot3(U, U);
+  unsigned cmask = 0;
+  {  // m = 0: v = 0, d = p, no tangential displacement
+    const float phm = ps.phi_hat;
+    const float4 gl = G4[0], ga = G4[1];
+    if (phm < 0.0f) {
+      cmask |= 1u;
+    } else {
+      const float gfn = gl.x * n[0] + gl.y * n[1] + gl.z * n[2] + ga.x * U[0] + ga.y * U[1] + ga.z * U[2];
+      const float wn = a + b * Uu;
+      const float dC = P.w_pen - __fdividef(gfn, wn);
+      dphi -= P.alpha * dC;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int i = (k + 1) % 3, j = (k + 2) % 3;
+    const float ni = n[i], nj = n[j], nk = n[k];
+    const float rho2 = ni * ni + nj * nj;
+    const bool has_t = rho2 > 0.0f;
+    const float rr = has_t ? rsqrtf(rho2) : 0.0f;
+    float tau[3];
+    tau[k] = rho2 * rr;
+    tau[i] = -nk * ni * rr;
+    tau[j] = -nk * nj * rr;
+    float T[3];
+    cross3(ps.p, tau, T);
+    const float Tt = dot3(T, T);
+    const float UE = U[j] * ni - U[i] * nj;            // U . E_k
+    const float TF = T[j] * tau[i] - T[i] * tau[j];    // T_k . F_k
+    const float Fsq = tau[i] * tau[i] + tau[j] * tau[j];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int m = 1 + 2 * k + h;
+      const float s = h == 0 ? 1.0f : -1.0f;
+      const float phm = sim_phi(ps, m, c);
+      const float4 gl = G4[2 * m], ga = G4[2 * m + 1];
+      if (phm < 0.0f) {
+        cmask |= 1u << m;
+      } else {
+        const float sc = s * c;
+        const float un2 = Uu - 2.0f * sc * UE + c * c * rho2;
+        const float wn = a + b * un2;
+        const float gaE = f4c(ga, j) * ni - f4c(ga, i) * nj;
+        const float gfn = gl.x * n[0] + gl.y * n[1] + gl.z * n[2] + ga.x * U[0] + ga.y * U[1] + ga.z * U[2] -
+                          sc * gaE;
+        float dC = -__fdividef(gfn, wn);
+        if (has_t) {
+          const float vt2 = Tt - 2.0f * sc * TF + c * c * Fsq;
+          const float wt = a + b * vt2;
+          const float gaF = f4c(ga, j) * tau[i] - f4c(ga, i) * tau[j];
+          const float gft = gl.x * tau[0] + gl.y * tau[1] + gl.z * tau[2] + ga.x * T[0] + ga.y * T[1] +
+                            ga.z * T[2] - sc * gaF;
+          dC -= P.mu * s * __fdividef(gft, wt);
+        }
+        const float dph = -P.alpha * dC;
+        dphi += dph;
+        dn[k] -= sc * dph;
+      }
+    }
+  }
+  // simulations in which the point is in contact: general adjoint, one instance
+  if (cmask) {
+#pragma unroll 1
+    for (int m = 0; m < kSims; ++m) {
+      if ((cmask >> m) & 1u) {
+        const float4 gl = G4[2 * m], ga = G4[2 * m + 1];
+        const float Gl[3] = {gl.x, gl.y, gl.z}, Ga[3] = {ga.x, ga.y, ga.z};
+        sim_adjoint(ps, m, sim_phi(ps, m, c), true, Gl, Ga, P, O, m == 0 ? P.w_pen : 0.0f, dphi, dn, dp);
+      }
+    }
+  }
 }
 
 // Adjoint of the SDF lookup and normalisation: given dL/dphi_hat, dL/dn and the

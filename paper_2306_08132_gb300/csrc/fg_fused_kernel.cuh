@@ -1,0 +1,412 @@
+// Fused grasp-search step: one CTA of NW warps per candidate, persistent over
+// candidates and steps.  Per step:
+//
+//   FK       warp 0, one lane per link, level by level -> link frames (smem)
+//   sweep 1  point -> SDF -> 7 plane-linearised contacts; a warp that has a
+//            contact in simulation m reduces its forces into a per-warp slot
+//   loss     warp 0: wrenches -> L_stable (Eq. 2) and its adjoint per
+//            simulation, joint terms (Eqs. 3-4), one lane per simulation / joint
+//   sweep 2  recompute each point -> adjoint of the 7 simulations (leaky rule),
+//            of the normal and of the SDF -> dL/dp -> per-link (sum g, sum r x g)
+//   tree     warp 0: prefix scan over preorder links -> subtree sums -> dL/dq
+//   update   q <- q - lr dL/dq (smem), written back after the last step
+//
+// Nothing per point is written to global memory: the adjoint recomputes the
+// forward quantities of each point from the link frames.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "fg_internal.h"
+
+namespace fg {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+template <int NW>
+struct FusedSmem {
+  HandDev H;
+  ObjDev O;
+  float4 frame4[kMaxLinks][3];     // rows (R_r0, R_r1, R_r2, o_r) of each link frame
+  float4 G4[kSims][2];             // (dL/dW_lin, 0), (dL/dW_ang, 0) per simulation
+  float q[64];
+  float grad[64];
+  float wred[NW][kSims][8];        // per warp: W (6), N, pen
+  float lacc[NW][kMaxLinks][6];    // per warp, per link: sum g, sum (p - t) x g
+  float Wtot[kSims][8];
+  float loss;
+  int bad_object;
+};
+
+// Point range of warp w: contiguous, 32-aligned chunks.
+__device__ __forceinline__ void warp_range(int P, int NW, int w, int& b, int& e) {
+  int chunk = ((P + 32 * NW - 1) / (32 * NW)) * 32;
+  b = w * chunk;
+  e = min(P, b + chunk);
+}
+
+__device__ __forceinline__ void store_frame(const Frame& F, float4* f4) {
+  f4[0] = make_float4(F.R[0], F.R[1], F.R[2], F.o[0]);
+  f4[1] = make_float4(F.R[3], F.R[4], F.R[5], F.o[1]);
+  f4[2] = make_float4(F.R[6], F.R[7], F.R[8], F.o[2]);
+}
+
+__device__ __forceinline__ void load_frame(const float4* f4, Frame& F) {
+  const float4 a = f4[0], b = f4[1], c = f4[2];
+  F.R[0] = a.x; F.R[1] = a.y; F.R[2] = a.z; F.o[0] = a.w;
+  F.R[3] = b.x; F.R[4] = b.y; F.R[5] = b.z; F.o[1] = b.w;
+  F.R[6] = c.x; F.R[7] = c.y; F.R[8] = c.z; F.o[2] = c.w;
+}
+
+// Link frames by depth level: lane l computes link l once its parent is done.
+__device__ __forceinline__ void fk_warp(const HandDev& H, const float* q, float4 (*frame4)[3], int lane) {
+  for (int d = 0; d <= H.max_depth; ++d) {
+    if (lane < H.L && H.depth[lane] == d) {
+      Frame F;
+      if (lane == 0) {
+        root_frame(q, F);
+      } else {
+        Frame par;
+        load_frame(frame4[H.parent[lane]], par);
+        link_frame(H, lane, par, q[6 + lane - 1], F);
+      }
+      store_frame(F, frame4[lane]);
+    }
+    __syncwarp();
+  }
+}
+
+__device__ __forceinline__ void world_point(const float4* f4, const float4& sp, float p[3]) {
+  const float4 a = f4[0], b = f4[1], c = f4[2];
+  p[0] = fma_(a.x, sp.x, fma_(a.y, sp.y, fma_(a.z, sp.z, a.w)));
+  p[1] = fma_(b.x, sp.x, fma_(b.y, sp.y, fma_(b.z, sp.z, b.w)));
+  p[2] = fma_(c.x, sp.x, fma_(c.y, sp.y, fma_(c.z, sp.z, c.w)));
+}
+
+template <int MODE, int NW, int MINB>
+__global__ void __launch_bounds__(NW * 32, MINB) fused_step_kernel(FusedArgs a) {
+  __shared__ FusedSmem<NW> S;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) S.H = *a.hand;
+  __syncthreads();
+  const HandDev& H = S.H;
+  const int D = H.D, P = H.P, L = H.L;
+  const ParamsDev& Pm = a.P;
+  const float dtV = Pm.dt * Pm.V;
+  int pb, pe;
+  warp_range(P, NW, warp, pb, pe);
+  const int nwords = (P + 31) >> 5;
+
+  for (int c = blockIdx.x; c < a.B; c += gridDim.x) {
+    __syncthreads();
+    if (tid < D) S.q[tid] = a.q[(size_t)c * D + tid];
+    if (tid == 0) {
+      const int oi = a.obj_of_cand ? a.obj_of_cand[c] : 0;
+      S.bad_object = oi < 0 || oi >= a.n_obj;
+      if (!S.bad_object) S.O = a.objs[oi];
+    }
+    __syncthreads();
+    if (S.bad_object) {
+      // an object index outside the scene: NaN outputs, q left unchanged
+      const float nan = __int_as_float(0x7fc00000);
+      if (MODE == kModeWrench) {
+        for (int idx = tid; idx < kSims * 6; idx += NW * 32) a.wrench[(size_t)c * kSims * 6 + idx] = nan;
+        if (tid < kSims) a.ncontact[(size_t)c * kSims + tid] = -1;
+      } else if (MODE == kModeLossGrad) {
+        if (tid == 0) a.loss[c] = nan;
+        if (a.grad && tid < D) a.grad[(size_t)c * D + tid] = nan;
+      } else if (a.loss && tid == 0) {
+        a.loss[c] = nan;
+      }
+      continue;
+    }
+    const int nsteps = MODE == kModeOptimize ? a.nsteps : 1;
+    for (int s = 0; s < nsteps; ++s) {
+      const float r = MODE == kModeOptimize ? dilation_at(Pm, a.step0 + s, a.total_steps) : a.r_fixed;
+      __syncthreads();
+      if (warp == 0) fk_warp(H, S.q, S.frame4, lane);
+      for (int idx = tid; idx < NW * kSims * 8; idx += NW * 32) (&S.wred[0][0][0])[idx] = 0.0f;
+      __syncthreads();
+      const ObjDev O = S.O;
+
+      // ---------------------------------------------------------------- sweep 1
+      for (int base = pb; base < pe; base += 32) {
+        const int i = base + lane;
+        const bool valid = i < pe;
+        const float4 sp = __ldg(H.pts + (valid ? i : base));
+        float p[3];
+        world_point(S.frame4[(int)sp.w], sp, p);
+        SdfSample smp;
+        sdf_lookup<false>(O, p, smp);
+        PointState ps;
+        point_state(smp, p, r, ps);
+#pragma unroll 1
+        for (int m = 0; m < kSims; ++m) {
+          const float phm = sim_phi(ps, m, dtV);
+          const bool kap = valid && phm < 0.0f;
+          const unsigned bal = __ballot_sync(kFull, kap);
+          if (MODE == kModeWrench && lane == 0 && a.bits)
+            a.bits[((size_t)c * kSims + m) * nwords + (base >> 5)] = bal;
+          if (bal) {
+            float v[7] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+            if (kap) {
+              float f[3], d[3], tq[3];
+              contact_force(ps, m, -phm, Pm, O, f, d);
+              cross3(d, f, tq);
+              v[0] = f[0]; v[1] = f[1]; v[2] = f[2];
+              v[3] = tq[0]; v[4] = tq[1]; v[5] = tq[2];
+              v[6] = -phm;
+            }
+#pragma unroll
+            for (int k = 0; k < 7; ++k) v[k] = warp_sum(v[k]);
+            if (lane == 0) {
+#pragma unroll
+              for (int k = 0; k < 6; ++k) S.wred[warp][m][k] += v[k];
+              S.wred[warp][m][6] += (float)__popc(bal);
+              if (m == 0) S.wred[warp][0][7] += v[6];
+            }
+          }
+        }
+      }
+      __syncthreads();
+
+      // ------------------------------------------------------------ reduction
+      if (warp == 0) {
+        for (int idx = lane; idx < kSims * 8; idx += 32) {
+          const int m = idx >> 3, k = idx & 7;
+          float v = 0.0f;
+#pragma unroll
+          for (int w = 0; w < NW; ++w) v += S.wred[w][m][k];
+          S.Wtot[m][k] = v;
+        }
+        __syncwarp();
+        if (MODE != kModeWrench) {
+          // loss and wrench adjoint: lane m handles simulation m, lane j joint j
+          float Lpart = 0.0f;
+          if (lane < kSims) {
+            const int m = lane;
+            const float Nc = fmaxf(S.Wtot[m][6], 1.0f);
+            const float sl = O.inv_mass / (Nc * Pm.dt), sa = O.inv_inertia / (Nc * Pm.dt);
+            float v[3] = {0.0f, 0.0f, 0.0f};
+            if (m > 0) v[sim_axis(m)] = sim_sign(m) * Pm.V;
+            float xd[3], td[3];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+              xd[k] = v[k] + S.Wtot[m][k] * sl;
+              td[k] = S.Wtot[m][3 + k] * sa;
+            }
+            const float nx = sqrtf(xd[0] * xd[0] + xd[1] * xd[1] + xd[2] * xd[2]);
+            const float nt = sqrtf(td[0] * td[0] + td[1] * td[1] + td[2] * td[2]);
+            Lpart = nx + nt;
+            const float ax = nx > 0.0f ? sl / (kSims * nx) : 0.0f;
+            const float at = nt > 0.0f ? sa / (kSims * nt) : 0.0f;
+            S.G4[m][0] = make_float4(xd[0] * ax, xd[1] * ax, xd[2] * ax, 0.0f);
+            S.G4[m][1] = make_float4(td[0] * at, td[1] * at, td[2] * at, 0.0f);
+          }
+          float dj = 0.0f, d2 = 0.0f, lim = 0.0f, th = 0.0f;
+          if (lane < H.J) {
+            th = S.q[6 + lane];
+            dj = th - 0.5f * (H.q_up[lane] + H.q_low[lane]);
+            d2 = dj * dj;
+            if (th > H.q_up[lane]) lim += th - H.q_up[lane];
+            if (th < H.q_low[lane]) lim += H.q_low[lane] - th;
+          }
+          const float Ls = warp_sum(Lpart) / kSims;
+          const float rn = sqrtf(warp_sum(d2));
+          const float lims = warp_sum(lim);
+          if (lane < H.J) {
+            float g = rn > 0.0f ? Pm.w_range * dj / rn : 0.0f;
+            if (th > H.q_up[lane]) g += Pm.w_limit;
+            if (th < H.q_low[lane]) g -= Pm.w_limit;
+            S.grad[6 + lane] = g;
+          }
+          if (lane == 0) S.loss = Ls + Pm.w_range * rn + Pm.w_limit * lims + Pm.w_pen * S.Wtot[0][7];
+        }
+      }
+      for (int idx = tid; idx < NW * kMaxLinks * 6; idx += NW * 32) (&S.lacc[0][0][0])[idx] = 0.0f;
+      __syncthreads();
+      if (MODE == kModeWrench) {
+        for (int idx = tid; idx < kSims * 6; idx += NW * 32) {
+          const int m = idx / 6, k = idx % 6;
+          a.wrench[((size_t)c * kSims + m) * 6 + k] = S.Wtot[m][k];
+        }
+        if (tid < kSims) a.ncontact[(size_t)c * kSims + tid] = (int)S.Wtot[tid][6];
+        continue;
+      }
+
+      // ---------------------------------------------------------------- sweep 2
+      {
+        const float t0[3] = {S.q[0], S.q[1], S.q[2]};
+        int cur = -1;
+        float acc[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        for (int base = pb; base < pe; base += 32) {
+          const int i = base + lane;
+          const bool valid = i < pe;
+          const float4 sp = __ldg(H.pts + (valid ? i : base));
+          const int link = (int)sp.w;
+          float p[3];
+          world_point(S.frame4[link], sp, p);
+          SdfSample smp;
+          sdf_lookup<true>(O, p, smp);
+          PointState ps;
+          point_state(smp, p, r, ps);
+          float dphi = 0.0f, dn[3] = {0.0f, 0.0f, 0.0f}, dp[3] = {0.0f, 0.0f, 0.0f};
+          point_sims_adjoint(ps, &S.G4[0][0], Pm, O, dphi, dn, dp);
+          sdf_adjoint(smp, ps, dphi, dn, dp);
+          float v[6];
+          if (valid) {
+            const float rel[3] = {p[0] - t0[0], p[1] - t0[1], p[2] - t0[2]};
+            float tq[3];
+            cross3(rel, dp, tq);
+            v[0] = dp[0]; v[1] = dp[1]; v[2] = dp[2];
+            v[3] = tq[0]; v[4] = tq[1]; v[5] = tq[2];
+          } else {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) v[k] = 0.0f;
+          }
+          const int l0 = __shfl_sync(kFull, link, 0);
+          const bool uniform = __all_sync(kFull, !valid || link == l0);
+          if (uniform && l0 == cur) {
+#pragma unroll
+            for (int k = 0; k < 6; ++k) acc[k] += v[k];
+          } else {
+            if (cur >= 0) {
+#pragma unroll
+              for (int k = 0; k < 6; ++k) {
+                const float sum = warp_sum(acc[k]);
+                if (lane == 0) S.lacc[warp][cur][k] += sum;
+              }
+            }
+            if (uniform) {
+              cur = l0;
+#pragma unroll
+              for (int k = 0; k < 6; ++k) acc[k] = v[k];
+            } else {
+              // the 32 points straddle links: reduce each link present separately
+              cur = -1;
+              unsigned remaining = __ballot_sync(kFull, valid);
+              while (remaining) {
+                const int leader = __ffs(remaining) - 1;
+                const int l = __shfl_sync(kFull, link, leader);
+                const bool mine = valid && link == l;
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                  const float sum = warp_sum(mine ? v[k] : 0.0f);
+                  if (lane == 0) S.lacc[warp][l][k] += sum;
+                }
+                remaining &= ~__ballot_sync(kFull, mine);
+              }
+#pragma unroll
+              for (int k = 0; k < 6; ++k) acc[k] = 0.0f;
+            }
+          }
+        }
+        if (cur >= 0) {
+#pragma unroll
+          for (int k = 0; k < 6; ++k) {
+            const float sum = warp_sum(acc[k]);
+            if (lane == 0) S.lacc[warp][cur][k] += sum;
+          }
+        }
+      }
+      __syncthreads();
+
+      // ------------------------------------------------------------------ tree
+      if (warp == 0) {
+        // per-link sums over warps, inclusive prefix over preorder links
+        float pre[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          float x = 0.0f;
+          if (lane < L) {
+#pragma unroll
+            for (int w = 0; w < NW; ++w) x += S.lacc[w][lane][k];
+          }
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const float y = __shfl_up_sync(kFull, x, o);
+            if (lane >= o) x += y;
+          }
+          pre[k] = x;
+        }
+        // subtree(lane) = [lane, end): sum = pre[end - 1] - pre[lane - 1]
+        const int end = lane < L ? H.subtree_end[lane] : lane + 1;
+        float sub[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+          const float hi = __shfl_sync(kFull, pre[k], (end - 1) & 31);
+          const float lo = __shfl_sync(kFull, pre[k], (lane + 31) & 31);
+          sub[k] = hi - (lane > 0 ? lo : 0.0f);
+        }
+        if (lane >= 1 && lane < L) {
+          Frame F;
+          load_frame(S.frame4[lane], F);
+          float aw[3];
+          matvec3(F.R, H.axis[lane], aw);
+          const float rel[3] = {F.o[0] - S.q[0], F.o[1] - S.q[1], F.o[2] - S.q[2]};
+          float rg[3];
+          cross3(rel, sub, rg);
+          const float tau[3] = {sub[3] - rg[0], sub[4] - rg[1], sub[5] - rg[2]};
+          S.grad[6 + lane - 1] += aw[0] * tau[0] + aw[1] * tau[1] + aw[2] * tau[2];
+        }
+        if (lane == 0) {
+          S.grad[0] = sub[0];
+          S.grad[1] = sub[1];
+          S.grad[2] = sub[2];
+          const float w[3] = {S.q[3], S.q[4], S.q[5]};
+          const float tau[3] = {sub[3], sub[4], sub[5]};
+          float gw[3];
+          exp_jacobian_T(w, tau, gw);
+          S.grad[3] = gw[0];
+          S.grad[4] = gw[1];
+          S.grad[5] = gw[2];
+        }
+      }
+      __syncthreads();
+      if (MODE == kModeLossGrad) {
+        if (tid < D && a.grad) a.grad[(size_t)c * D + tid] = S.grad[tid];
+        if (tid == 0) a.loss[c] = S.loss;
+      } else {  // optimize
+        if (tid < D) S.q[tid] -= Pm.lr * S.grad[tid];
+        if (tid == 0 && a.loss && s == nsteps - 1) a.loss[c] = S.loss;
+      }
+    }
+    if (MODE == kModeOptimize) {
+      __syncthreads();
+      if (tid < D) a.q[(size_t)c * D + tid] = S.q[tid];
+    }
+  }
+}
+
+// Launch of one compiled configuration: a persistent grid of (SMs x resident
+// CTAs) blocks, capped at B.
+template <int MODE, int NW, int MINB>
+cudaError_t launch_fused_cfg(const FusedArgs& a, cudaStream_t st) {
+  static int blocks_per_sm[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int& bps = blocks_per_sm[dev & 63];
+  if (bps <= 0) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fused_step_kernel<MODE, NW, MINB>, NW * 32, 0);
+    if (e != cudaSuccess) return e;
+    if (bps < 1) bps = 1;
+  }
+  long long grid = (long long)device_sm_count() * bps;
+  if (grid > a.B) grid = a.B;
+  if (grid < 1) return cudaSuccess;
+  fused_step_kernel<MODE, NW, MINB><<<(int)grid, NW * 32, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+// Compiled configurations of the loss/gradient and optimisation kernels:
+// warps per candidate and the minimum resident CTAs per SM the register
+// allocation is held to.  The autotuner times them on a workload.
+#define FG_FUSED_CONFIGS(X) X(4, 4) X(4, 5) X(4, 6) X(4, 8) X(8, 2) X(8, 3) X(2, 8) X(2, 12)
+
+}  // namespace fg

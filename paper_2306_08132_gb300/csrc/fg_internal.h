@@ -50,8 +50,16 @@ struct FusedArgs {
   float* wrench;
   int* ncontact;
   uint32_t* bits;
+  int hand_D;
 };
+typedef cudaError_t (*FusedLaunchFn)(const FusedArgs&, cudaStream_t);
+extern const FusedLaunchFn kOptimizeLaunch[];
 cudaError_t launch_fused(int mode, const FusedArgs& a, const fg_hand* h, cudaStream_t st);
+int fused_config_count();
+void fused_config_info(int i, int* nw, int* minb);
+int fused_config_current();
+void fused_config_select(int i);
+cudaError_t autotune_fused(const FusedArgs& base, int reps, float* times_ms, int* best, cudaStream_t st);
 
 // per-stage kernels (fg_plain.cu)
 size_t plain_workspace_bytes(const fg_hand* h, int B);

@@ -293,3 +293,29 @@ def test_full_size_batched_sampled_parity(fg):
     _compare_loss_grad(loss.cpu().numpy()[sample], grad.cpu().numpy()[sample], sub, clean)
     step = ((q1 - q).cpu().numpy()[sample]).astype(np.float64) / -w.params["lr"]
     _compare_loss_grad(loss.cpu().numpy()[sample], step, sub, clean)
+
+
+def test_every_fused_configuration_matches_oracle(fg, tiny):
+    """Each compiled (warps per candidate, register budget) configuration gives the
+    oracle's loss and gradient; the autotuner selects one of them."""
+    w, r = tiny.w, 0.004
+    ref = O.batch_loss_and_grad(tiny.S, w.q0, w.obj_of_cand, r)
+    clean = tiny.clean(w.q0, r)
+    q = torch.tensor(w.q0, device=_dev())
+    cfgs = fg.fused_configs()
+    assert len(cfgs) >= 4
+    try:
+        for i in range(len(cfgs)):
+            fg.fused_config_select(i)
+            loss, grad = fg.loss_and_grad(tiny.hand, tiny.scene, q, w.params, r, obj_of_cand=tiny.oc)
+            _compare_loss_grad(loss.cpu().numpy(), grad.cpu().numpy(), ref, clean)
+            q1 = q.clone()
+            fg.optimize_step(tiny.hand, tiny.scene, q1, w.params, 0, w.steps, 1, obj_of_cand=tiny.oc)
+            step = (q1 - q).cpu().numpy().astype(np.float64) / -w.params["lr"]
+            _compare_loss_grad(loss.cpu().numpy(), step, ref, clean)
+        best, times = fg.autotune(tiny.hand, tiny.scene, q, w.params, 0, w.steps, 1, obj_of_cand=tiny.oc, reps=2)
+        assert 0 <= best < len(cfgs) and fg.fused_config_current() == best
+        assert all(t > 0 for t in times)
+        assert torch.equal(q, torch.tensor(w.q0, device=_dev()))     # the autotuner leaves q alone
+    finally:
+        fg.fused_config_select(-1)
