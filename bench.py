@@ -180,6 +180,7 @@ def main():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--profile-kernel", action="store_true",
                     help="set up the workload, run a few fused launches and exit (for ncu)")
+    ap.add_argument("--config", type=int, default=None, help="fused configuration index (default: autotune)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -217,6 +218,8 @@ def main():
         fg.optimize_step(hand, scene, q, w.params, 0, K, S_in, obj_of_cand=oc, loss=loss)
 
     if args.profile_kernel:
+        if args.config is not None:
+            fg.fused_config_select(args.config)
         for _ in range(5):
             fused_step()
         torch.cuda.synchronize()
@@ -275,6 +278,9 @@ def main():
     # the project's autotuner picks the fused-kernel configuration on this workload
     best_cfg, cfg_ms = fg.autotune(hand, scene, q0, w.params, 0, K, S_in, obj_of_cand=oc, reps=3)
     cfgs = fg.fused_configs()
+    if args.config is not None:
+        best_cfg = args.config
+        fg.fused_config_select(best_cfg)
     fused_graph = graphed(fused_step)
     prewarm(fused_graph)
     sampler = ClockSampler(local)

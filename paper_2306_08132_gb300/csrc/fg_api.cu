@@ -3,6 +3,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <string>
@@ -168,29 +169,58 @@ fg_status fg_hand_create(const fg_hand_desc* d, fg_hand** out) {
     if (!std::isfinite(x) || !std::isfinite(y) || !std::isfinite(z)) return invalid("fg_hand_create: non-finite point");
     pts[i] = make_float4(x, y, z, (float)l);
   }
+  // bounding sphere (link frame) of every chunk of 32 consecutive points; a chunk
+  // that spans two links is never culled (link -1)
+  const int nchunks = (P + 31) / 32;
+  H.nchunks = nchunks;
+  std::vector<float4> spheres(nchunks);
+  std::vector<int> clink(nchunks);
+  for (int j = 0; j < nchunks; ++j) {
+    const int b = 32 * j, e = std::min(P, b + 32);
+    int l = d->link_of_point[b];
+    for (int i = b; i < e; ++i)
+      if (d->link_of_point[i] != l) l = -1;
+    double c[3] = {0.0, 0.0, 0.0};
+    for (int i = b; i < e; ++i)
+      for (int k = 0; k < 3; ++k) c[k] += d->pts_local[3 * i + k];
+    for (int k = 0; k < 3; ++k) c[k] /= (e - b);
+    const float cf[3] = {(float)c[0], (float)c[1], (float)c[2]};
+    double rad = 0.0;
+    for (int i = b; i < e; ++i) {
+      double r2 = 0.0;
+      for (int k = 0; k < 3; ++k) {
+        const double dk = (double)d->pts_local[3 * i + k] - (double)cf[k];
+        r2 += dk * dk;
+      }
+      rad = std::max(rad, std::sqrt(r2));
+    }
+    spheres[j] = make_float4(cf[0], cf[1], cf[2], (float)(rad * (1.0 + 1e-6) + 1e-7));
+    clink[j] = l;
+  }
   fg_hand* h = new (std::nothrow) fg_hand;
   if (!h) return FG_ERR_OOM;
   std::memset(h, 0, sizeof(*h));
-  cudaError_t e = cudaMalloc(&h->pts, sizeof(float4) * P);
-  if (e != cudaSuccess) {
-    delete h;
-    return cuda_status(e, "fg_hand_create: cudaMalloc");
-  }
-  e = cudaMalloc(&h->dev, sizeof(HandDev));
-  if (e != cudaSuccess) {
+  auto fail = [&](cudaError_t e, const char* what) {
     cudaFree(h->pts);
-    delete h;
-    return cuda_status(e, "fg_hand_create: cudaMalloc");
-  }
-  H.pts = h->pts;
-  e = cudaMemcpy(h->pts, pts.data(), sizeof(float4) * P, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) e = cudaMemcpy(h->dev, &H, sizeof(HandDev), cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) {
-    cudaFree(h->pts);
+    cudaFree(h->chunk_sphere);
+    cudaFree(h->chunk_link);
     cudaFree(h->dev);
     delete h;
-    return cuda_status(e, "fg_hand_create: cudaMemcpy");
-  }
+    return cuda_status(e, what);
+  };
+  cudaError_t e = cudaMalloc(&h->pts, sizeof(float4) * P);
+  if (e == cudaSuccess) e = cudaMalloc(&h->chunk_sphere, sizeof(float4) * nchunks);
+  if (e == cudaSuccess) e = cudaMalloc(&h->chunk_link, sizeof(int) * nchunks);
+  if (e == cudaSuccess) e = cudaMalloc(&h->dev, sizeof(HandDev));
+  if (e != cudaSuccess) return fail(e, "fg_hand_create: cudaMalloc");
+  H.pts = h->pts;
+  H.chunk_sphere = h->chunk_sphere;
+  H.chunk_link = h->chunk_link;
+  e = cudaMemcpy(h->pts, pts.data(), sizeof(float4) * P, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->chunk_sphere, spheres.data(), sizeof(float4) * nchunks, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->chunk_link, clink.data(), sizeof(int) * nchunks, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(h->dev, &H, sizeof(HandDev), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return fail(e, "fg_hand_create: cudaMemcpy");
   h->host = H;
   for (int l = 0; l < L; ++l) h->subtree_end[l] = H.subtree_end[l];
   *out = h;
@@ -200,6 +230,8 @@ fg_status fg_hand_create(const fg_hand_desc* d, fg_hand** out) {
 fg_status fg_hand_destroy(fg_hand* h) {
   if (!h) return FG_OK;
   cudaFree(h->pts);
+  cudaFree(h->chunk_sphere);
+  cudaFree(h->chunk_link);
   cudaFree(h->dev);
   delete h;
   return FG_OK;
@@ -252,12 +284,26 @@ fg_status fg_sdf_create(const float* grid, int nx, int ny, int nz, const float* 
   o.inv_h = 1.0f / pitch;
   o.inv_mass = 1.0f / mass;
   o.inv_inertia = 1.0f / inertia;
+  int levels = 0;
+  const size_t pf = min_pyramid_floats(nx, ny, nz, &levels);
+  s->pyr = nullptr;
+  e = cudaMalloc(&s->pyr, sizeof(float) * pf);
+  if (e == cudaSuccess) e = build_min_pyramid(s->grid, nx, ny, nz, s->pyr, levels, o.pyr_off);
+  if (e != cudaSuccess) {
+    cudaFree(s->pyr);
+    cudaFree(s->grid);
+    delete s;
+    return cuda_status(e, "fg_sdf_create: min-pyramid");
+  }
+  o.pyr = s->pyr;
+  o.pyr_levels = levels;
   *out = s;
   return FG_OK;
 }
 
 fg_status fg_sdf_destroy(fg_sdf* s) {
   if (!s) return FG_OK;
+  cudaFree(s->pyr);
   cudaFree(s->grid);
   delete s;
   return FG_OK;

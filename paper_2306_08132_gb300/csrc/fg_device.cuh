@@ -30,16 +30,26 @@ struct HandDev {
   float q_low[kMaxLinks];        // per joint j = l - 1
   float q_up[kMaxLinks];
   int subtree_end[kMaxLinks];    // links are in depth-first preorder: subtree(l) = [l, subtree_end[l])
+  int nchunks;                   // ceil(P / 32) chunks of 32 consecutive points
   const float4* pts;             // [P] (x, y, z, link index as float)
+  const float4* chunk_sphere;    // [nchunks] bounding sphere in the link frame (centre, radius)
+  const int* chunk_link;         // [nchunks] link of the chunk, -1 when it spans two links
 };
+
+// Chunks a fused CTA can cull in shared memory (hands up to 8,192 points).
+constexpr int kMaxCullChunks = 256;
+
+constexpr int kMaxPyrLevels = 12;
 
 struct ObjDev {
   const float* grid;             // [nz][ny][nx]
-  int nx, ny, nz, pad0;
+  int nx, ny, nz;
+  int pyr_levels;                // levels 1..pyr_levels of the min-pyramid
   float ox, oy, oz;              // origin
   float inv_h, h;                // 1/pitch, pitch
   float inv_mass, inv_inertia;
-  float pad1;
+  const float* pyr;              // min-pyramid, level k at pyr + pyr_off[k - 1]
+  int pyr_off[kMaxPyrLevels];
 };
 
 struct ParamsDev {
@@ -235,6 +245,35 @@ __device__ __forceinline__ void sdf_lookup(const ObjDev& O, const float p[3], Sd
     s.e = mul_(O.h, dn);
   }
   s.phi = add_(val, s.e);
+}
+
+// Lower bound of the interpolated SDF over every point whose index coordinates
+// lie in the box [lo, hi] (any values; clamped to the grid, which also covers
+// points outside it since the excess distance is non-negative).  Uses the finest
+// pyramid level at which the box spans at most 3 blocks per axis.
+__device__ inline float region_min(const ObjDev& O, const float lo[3], const float hi[3]) {
+  const int n[3] = {O.nx, O.ny, O.nz};
+  int c0[3], c1[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float cap = (float)(n[k] - 2);
+    const float a = fminf(fmaxf(lo[k], 0.0f), cap), b = fminf(fmaxf(hi[k], 0.0f), cap);
+    c0[k] = (int)floorf(a);
+    c1[k] = (int)floorf(b);
+  }
+  int lev = 1;
+  for (; lev < O.pyr_levels; ++lev) {
+    if ((c1[0] >> lev) - (c0[0] >> lev) <= 2 && (c1[1] >> lev) - (c0[1] >> lev) <= 2 &&
+        (c1[2] >> lev) - (c0[2] >> lev) <= 2)
+      break;
+  }
+  const int bx = ((n[0] - 1) + (1 << lev) - 1) >> lev, by = ((n[1] - 1) + (1 << lev) - 1) >> lev;
+  const float* L = O.pyr + O.pyr_off[lev - 1];
+  float m = 3.0e38f;
+  for (int z = c0[2] >> lev; z <= (c1[2] >> lev); ++z)
+    for (int y = c0[1] >> lev; y <= (c1[1] >> lev); ++y)
+      for (int x = c0[0] >> lev; x <= (c1[0] >> lev); ++x) m = fminf(m, __ldg(L + ((size_t)z * by + y) * bx + x));
+  return m;
 }
 
 // ------------------------------------------------------------------ contact sims
@@ -463,24 +502,19 @@ __device__ __forceinline__ void point_sims_adjoint(const PointState& ps, const f
   const float Uu = dot3(U, U);
   unsigned cmask = 0;
   {  // m = 0: v = 0, d = p, no tangential displacement
-    const float phm = ps.phi_hat;
+    const bool kap = ps.phi_hat < 0.0f;
+    cmask |= kap ? 1u : 0u;
     const float4 gl = G4[0], ga = G4[1];
-    if (phm < 0.0f) {
-      cmask |= 1u;
-    } else {
-      const float gfn = gl.x * n[0] + gl.y * n[1] + gl.z * n[2] + ga.x * U[0] + ga.y * U[1] + ga.z * U[2];
-      const float wn = a + b * Uu;
-      const float dC = P.w_pen - __fdividef(gfn, wn);
-      dphi -= P.alpha * dC;
-    }
+    const float gfn = gl.x * n[0] + gl.y * n[1] + gl.z * n[2] + ga.x * U[0] + ga.y * U[1] + ga.z * U[2];
+    const float dC = P.w_pen - __fdividef(gfn, a + b * Uu);
+    dphi -= kap ? 0.0f : P.alpha * dC;
   }
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const int i = (k + 1) % 3, j = (k + 2) % 3;
     const float ni = n[i], nj = n[j], nk = n[k];
     const float rho2 = ni * ni + nj * nj;
-    const bool has_t = rho2 > 0.0f;
-    const float rr = has_t ? rsqrtf(rho2) : 0.0f;
+    const float rr = rho2 > 0.0f ? rsqrtf(rho2) : 0.0f;     // tau = 0 when n is parallel to e_k
     float tau[3];
     tau[k] = rho2 * rr;
     tau[i] = -nk * ni * rr;
@@ -491,34 +525,27 @@ __device__ __forceinline__ void point_sims_adjoint(const PointState& ps, const f
     const float UE = U[j] * ni - U[i] * nj;            // U . E_k
     const float TF = T[j] * tau[i] - T[i] * tau[j];    // T_k . F_k
     const float Fsq = tau[i] * tau[i] + tau[j] * tau[j];
+    const float wn0 = a + b * (Uu + c * c * rho2), wn1 = 2.0f * b * c * UE;
+    const float wt0 = a + b * (Tt + c * c * Fsq), wt1 = 2.0f * b * c * TF;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int m = 1 + 2 * k + h;
       const float s = h == 0 ? 1.0f : -1.0f;
-      const float phm = sim_phi(ps, m, c);
+      const float sc = s * c;
+      const bool kap = sim_phi(ps, m, c) < 0.0f;
+      cmask |= kap ? (1u << m) : 0u;
       const float4 gl = G4[2 * m], ga = G4[2 * m + 1];
-      if (phm < 0.0f) {
-        cmask |= 1u << m;
-      } else {
-        const float sc = s * c;
-        const float un2 = Uu - 2.0f * sc * UE + c * c * rho2;
-        const float wn = a + b * un2;
-        const float gaE = f4c(ga, j) * ni - f4c(ga, i) * nj;
-        const float gfn = gl.x * n[0] + gl.y * n[1] + gl.z * n[2] + ga.x * U[0] + ga.y * U[1] + ga.z * U[2] -
-                          sc * gaE;
-        float dC = -__fdividef(gfn, wn);
-        if (has_t) {
-          const float vt2 = Tt - 2.0f * sc * TF + c * c * Fsq;
-          const float wt = a + b * vt2;
-          const float gaF = f4c(ga, j) * tau[i] - f4c(ga, i) * tau[j];
-          const float gft = gl.x * tau[0] + gl.y * tau[1] + gl.z * tau[2] + ga.x * T[0] + ga.y * T[1] +
-                            ga.z * T[2] - sc * gaF;
-          dC -= P.mu * s * __fdividef(gft, wt);
-        }
-        const float dph = -P.alpha * dC;
-        dphi += dph;
-        dn[k] -= sc * dph;
-      }
+      const float gaE = f4c(ga, j) * ni - f4c(ga, i) * nj;
+      const float gfn = gl.x * n[0] + gl.y * n[1] + gl.z * n[2] + ga.x * U[0] + ga.y * U[1] + ga.z * U[2] -
+                        sc * gaE;
+      const float gaF = f4c(ga, j) * tau[i] - f4c(ga, i) * tau[j];
+      const float gft = gl.x * tau[0] + gl.y * tau[1] + gl.z * tau[2] + ga.x * T[0] + ga.y * T[1] + ga.z * T[2] -
+                        sc * gaF;
+      // dC = -(gf.n)/w_n - mu (gf.t)/w_t with w_n = wn0 - s wn1, w_t = wt0 - s wt1
+      const float dC = -__fdividef(gfn, wn0 - s * wn1) - P.mu * s * __fdividef(gft, wt0 - s * wt1);
+      const float dph = kap ? 0.0f : -P.alpha * dC;
+      dphi += dph;
+      dn[k] -= sc * dph;
     }
   }
   // simulations in which the point is in contact: general adjoint, one instance

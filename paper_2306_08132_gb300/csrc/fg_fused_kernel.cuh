@@ -42,6 +42,9 @@ struct FusedSmem {
   float Wtot[kSims][8];
   float loss;
   int bad_object;
+  int n_active;
+  unsigned active_bits[kMaxCullChunks / 32];
+  unsigned short active_list[kMaxCullChunks];
 };
 
 // Point range of warp w: contiguous, 32-aligned chunks.
@@ -135,10 +138,67 @@ __global__ void __launch_bounds__(NW * 32, MINB) fused_step_kernel(FusedArgs a) 
       __syncthreads();
       const ObjDev O = S.O;
 
+      // --------------------------------------------------------- chunk culling
+      // A chunk of 32 points (one link) can only hold a contact if some point has
+      // phi_m = phi_hat - dt V n_k < 0, i.e. phi(p) < r + dt V.  Every point lies in
+      // the chunk's bounding sphere (centre c, radius R), and the interpolated
+      // field over that sphere is bounded below by the min-pyramid over its box,
+      // so a chunk with  min - r - dt V (1 + 1e-5) - slack > 0  has no contact in
+      // any simulation; the slack covers float32 rounding of positions and values.
+      // Its contact flags are all zero and its forces are not computed.
+      const bool cull = H.nchunks <= kMaxCullChunks;
+      if (cull) {
+        for (int j0 = warp * 32; j0 < H.nchunks; j0 += NW * 32) {
+          const int j = j0 + lane;
+          bool active = false;
+          if (j < H.nchunks) {
+            active = true;
+            const int l = H.chunk_link[j];
+            if (l >= 0) {
+              const float4 cs = __ldg(H.chunk_sphere + j);
+              float cw[3];
+              world_point(S.frame4[l], cs, cw);
+              const float slack = 1e-6f + 1e-5f * (fabsf(cw[0]) + fabsf(cw[1]) + fabsf(cw[2]));
+              const float R = (cs.w + slack) * O.inv_h;
+              const float org[3] = {O.ox, O.oy, O.oz};
+              float lo[3], hi[3];
+#pragma unroll
+              for (int k = 0; k < 3; ++k) {
+                const float u = (cw[k] - org[k]) * O.inv_h;
+                lo[k] = u - R - 1e-3f;
+                hi[k] = u + R + 1e-3f;
+              }
+              const float mn = region_min(O, lo, hi);
+              active = !(mn - r - dtV * (1.0f + 1e-5f) - (1e-6f + 1e-5f * fabsf(mn)) > 0.0f);
+            }
+            if (MODE == kModeWrench && !active && a.bits) {
+#pragma unroll 1
+              for (int m = 0; m < kSims; ++m) a.bits[((size_t)c * kSims + m) * nwords + j] = 0u;
+            }
+          }
+          const unsigned word = __ballot_sync(kFull, active);
+          if (lane == 0) S.active_bits[j0 >> 5] = word;
+        }
+        __syncthreads();
+        if (warp == 0) {
+          int count = 0;
+          for (int wi = 0; wi < (H.nchunks + 31) >> 5; ++wi) {
+            const unsigned bits = S.active_bits[wi];
+            if ((bits >> lane) & 1u)
+              S.active_list[count + __popc(bits & ((1u << lane) - 1u))] = (unsigned short)(wi * 32 + lane);
+            count += __popc(bits);
+          }
+          if (lane == 0) S.n_active = count;
+        }
+        __syncthreads();
+      }
+
       // ---------------------------------------------------------------- sweep 1
-      for (int base = pb; base < pe; base += 32) {
+      const int n_work = cull ? S.n_active : H.nchunks;
+      for (int idx = warp; idx < n_work; idx += NW) {
+        const int base = 32 * (cull ? (int)S.active_list[idx] : idx);
         const int i = base + lane;
-        const bool valid = i < pe;
+        const bool valid = i < P;
         const float4 sp = __ldg(H.pts + (valid ? i : base));
         float p[3];
         world_point(S.frame4[(int)sp.w], sp, p);

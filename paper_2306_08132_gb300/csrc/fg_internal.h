@@ -9,15 +9,18 @@
 #include "fg_device.cuh"
 
 struct fg_hand {
-  fg::HandDev host;          // copy of the device descriptor (pts = device pointer)
+  fg::HandDev host;          // copy of the device descriptor (pointers are device pointers)
   fg::HandDev* dev;          // device copy of the descriptor
   float4* pts;               // device [P]
+  float4* chunk_sphere;      // device [nchunks]
+  int* chunk_link;           // device [nchunks]
   int subtree_end[FG_MAX_LINKS];
 };
 
 struct fg_sdf {
-  fg::ObjDev host;           // grid = device pointer owned by this handle
+  fg::ObjDev host;           // grid and pyramid: device pointers owned by this handle
   float* grid;
+  float* pyr;
   size_t bytes;
 };
 
@@ -32,6 +35,8 @@ void set_error(const std::string& msg);
 fg_status cuda_status(cudaError_t e, const char* what);
 ParamsDev params_from(const fg_params* p);
 int device_sm_count();
+size_t min_pyramid_floats(int nx, int ny, int nz, int* levels);
+cudaError_t build_min_pyramid(const float* grid, int nx, int ny, int nz, float* pyr, int levels, int* offsets);
 
 // fused kernels (fg_fused.cu)
 enum FusedMode { kModeWrench = 0, kModeLossGrad = 1, kModeOptimize = 2 };

@@ -15,7 +15,8 @@ so the configuration vector is q = (t[3], w[3], theta[J]) with D = 6 + J.
 Geometry (metres): capsule links of radius 9 mm with flexion lengths 45/30/25 mm,
 10 mm abduction knuckles, and a 9 x 9 x 2.5 cm box palm.  Surface points are a
 deterministic Fibonacci sampling of each capsule (area-uniform) and a stratified
-golden-ratio lattice on the box faces.
+golden-ratio lattice on the box faces, listed per link in Morton order so that
+consecutive points are neighbours on the surface.
 
 Each link is first placed by its REST world frame (rotation R_l, origin o_l).  The
 fixed parent->child transforms are then derived as T_fix = T_rest(parent)^-1 T_rest(l),
@@ -107,6 +108,18 @@ def box_points(half, n: int) -> np.ndarray:
     return np.array(pts, dtype=np.float64)
 
 
+def _morton_order(pts: np.ndarray) -> np.ndarray:
+    """Order of points along a Morton (Z-order) curve of their 10-bit quantised
+    coordinates, so that consecutive points are spatially close."""
+    lo, hi = pts.min(axis=0), pts.max(axis=0)
+    q = np.floor((pts - lo) / np.maximum(hi - lo, 1e-12) * 1023.0).astype(np.int64)
+    code = np.zeros(len(pts), dtype=np.int64)
+    for bit in range(10):
+        for axis in range(3):
+            code |= ((q[:, axis] >> bit) & 1) << (3 * bit + axis)
+    return np.argsort(code, kind="stable")
+
+
 def _layout(kind: int):
     """Return link specs: (name, parent_index, R_rest, o_rest, axis_local, shape, limits)."""
     eye = np.eye(3)
@@ -187,6 +200,7 @@ def make_hand(kind: int, points_per_link: int) -> dict:
             pts = box_points(shape[1], points_per_link)
         else:
             pts = capsule_points(shape[1], CAPSULE_RADIUS, points_per_link)
+        pts = pts[_morton_order(pts)]          # spatially coherent runs of 32 points
         local.append(pts)
         link_of_point.extend([l] * len(pts))
         link_start.append(link_start[-1] + len(pts))
