@@ -355,7 +355,9 @@ def main():
                            "l2": "flushed between timed steps (256 MiB write)", "parallelism": "dp%d" % world,
                            "fused_config": {"warps_per_candidate": cfgs[best_cfg][0],
                                             "min_ctas_per_sm": cfgs[best_cfg][1],
-                                            "autotune_ms": {"%dw/%d" % c: round(t, 4) for c, t in zip(cfgs, cfg_ms)}}},
+                                            "points_per_thread": cfgs[best_cfg][2],
+                                            "autotune_ms": {"%dw/%d/%dp" % c: round(t, 4)
+                                                            for c, t in zip(cfgs, cfg_ms)}}},
                 "plain": plain, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
                 "gpu_launches": args.steps * 1, "clocks": clocks, "wall_s_timed_region": wall,
                 "per_step_ms": {"min": float(np.min(ms)), "median": float(np.median(ms)), "max": float(np.max(ms))}}

@@ -199,12 +199,14 @@ fg_status fg_optimize_step_plain(const fg_hand* hand, const fg_scene* scene, con
 /* ------------------------------------------------------------------ tuning */
 
 /* The fused kernels are compiled in several configurations: warps per
- * candidate (points per warp = P / (32 * warps)) and the minimum number of
- * resident CTAs per SM the register allocation is held to.  The selection is
+ * candidate (points per warp = P / warps), the minimum number of resident CTAs
+ * per SM the register allocation is held to, and the points each thread carries
+ * per iteration of the adjoint sweep (independent dependency chains).  The selection is
  * per device (the current one) and applies to fg_loss_and_grad and
  * fg_optimize_step; it changes no result beyond float32 summation order. */
 fg_status fg_fused_config_count(int* n);
-fg_status fg_fused_config_info(int index, int* warps_per_candidate, int* min_ctas_per_sm);
+fg_status fg_fused_config_info(int index, int* warps_per_candidate, int* min_ctas_per_sm,
+                               int* points_per_thread);
 /* index in [0, count) selects a configuration; -1 restores the default. */
 fg_status fg_fused_config_select(int index);
 fg_status fg_fused_config_current(int* index);

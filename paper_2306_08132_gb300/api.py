@@ -217,16 +217,17 @@ def optimize_step_plain(hand: Hand, scene: Scene, q: torch.Tensor, params: dict,
     return loss
 
 
-def fused_configs() -> list[tuple[int, int]]:
-    """Compiled fused-kernel configurations: (warps per candidate, min CTAs per SM)."""
+def fused_configs() -> list[tuple[int, int, int]]:
+    """Compiled fused-kernel configurations: (warps per candidate, min CTAs per SM,
+    points per thread in the adjoint sweep)."""
     lib = _lib.load()
     n = C.c_int()
     check(lib.fg_fused_config_count(C.byref(n)), "fg_fused_config_count")
     out = []
     for i in range(n.value):
-        a, b = C.c_int(), C.c_int()
-        check(lib.fg_fused_config_info(i, C.byref(a), C.byref(b)), "fg_fused_config_info")
-        out.append((a.value, b.value))
+        a, b, c = C.c_int(), C.c_int(), C.c_int()
+        check(lib.fg_fused_config_info(i, C.byref(a), C.byref(b), C.byref(c)), "fg_fused_config_info")
+        out.append((a.value, b.value, c.value))
     return out
 
 

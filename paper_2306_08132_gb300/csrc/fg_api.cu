@@ -284,6 +284,9 @@ fg_status fg_sdf_create(const float* grid, int nx, int ny, int nz, const float* 
   o.inv_h = 1.0f / pitch;
   o.inv_mass = 1.0f / mass;
   o.inv_inertia = 1.0f / inertia;
+  o.uo[0] = -origin[0] * o.inv_h;
+  o.uo[1] = -origin[1] * o.inv_h;
+  o.uo[2] = -origin[2] * o.inv_h;
   int levels = 0;
   const size_t pf = min_pyramid_floats(nx, ny, nz, &levels);
   s->pyr = nullptr;
@@ -466,9 +469,10 @@ fg_status fg_fused_config_count(int* n) {
   return FG_OK;
 }
 
-fg_status fg_fused_config_info(int index, int* nw, int* minb) {
-  if (index < 0 || index >= fused_config_count() || !nw || !minb) return invalid("fg_fused_config_info: bad index");
-  fused_config_info(index, nw, minb);
+fg_status fg_fused_config_info(int index, int* nw, int* minb, int* ppt) {
+  if (index < 0 || index >= fused_config_count() || !nw || !minb || !ppt)
+    return invalid("fg_fused_config_info: bad index or NULL");
+  fused_config_info(index, nw, minb, ppt);
   return FG_OK;
 }
 

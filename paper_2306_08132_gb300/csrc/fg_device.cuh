@@ -48,6 +48,7 @@ struct ObjDev {
   float ox, oy, oz;              // origin
   float inv_h, h;                // 1/pitch, pitch
   float inv_mass, inv_inertia;
+  float uo[3];                   // -origin / pitch: index coordinate u = p / pitch + uo
   const float* pyr;              // min-pyramid, level k at pyr + pyr_off[k - 1]
   int pyr_off[kMaxPyrLevels];
 };
@@ -183,19 +184,17 @@ struct SdfSample {
 template <bool kHess>
 __device__ __forceinline__ void sdf_lookup(const ObjDev& O, const float p[3], SdfSample& s) {
   const float n_max[3] = {(float)(O.nx - 1), (float)(O.ny - 1), (float)(O.nz - 1)};
-  const float org[3] = {O.ox, O.oy, O.oz};
   float u[3], uc[3], du[3], f[3];
   int i0[3];
   bool clamped[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    u[k] = mul_(sub_(p[k], org[k]), O.inv_h);
-    bool lo = u[k] < 0.0f, hi = u[k] > n_max[k];
-    clamped[k] = lo || hi;
-    uc[k] = lo ? 0.0f : (hi ? n_max[k] : u[k]);
-    du[k] = sub_(u[k], uc[k]);
-    int ii = (int)floorf(uc[k]);
-    int cap = (int)n_max[k] - 1;
+    u[k] = fma_(p[k], O.inv_h, O.uo[k]);
+    uc[k] = fminf(fmaxf(u[k], 0.0f), n_max[k]);     // NaN -> 0
+    clamped[k] = uc[k] != u[k];
+    du[k] = sub_(u[k], uc[k]);                       // 0 unless clamped
+    const int ii = (int)floorf(uc[k]);
+    const int cap = (int)n_max[k] - 1;
     i0[k] = ii < cap ? ii : cap;
     f[k] = sub_(uc[k], (float)i0[k]);
   }
@@ -234,9 +233,9 @@ __device__ __forceinline__ void sdf_lookup(const ObjDev& O, const float p[3], Sd
   s.e = 0.0f;
   s.eh[0] = s.eh[1] = s.eh[2] = 0.0f;
   if (s.outside) {
-    float dn2 = fma_(du[0], du[0], fma_(du[1], du[1], mul_(du[2], du[2])));
-    float dn = sqrtf(dn2);
-    float r = __fdiv_rn(1.0f, dn);
+    const float dn2 = fma_(du[0], du[0], fma_(du[1], du[1], mul_(du[2], du[2])));
+    const float r = rsqrtf(dn2);                     // dn2 > 0 outside the grid
+    const float dn = mul_(dn2, r);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       s.eh[k] = mul_(du[k], r);
@@ -269,10 +268,29 @@ __device__ inline float region_min(const ObjDev& O, const float lo[3], const flo
   }
   const int bx = ((n[0] - 1) + (1 << lev) - 1) >> lev, by = ((n[1] - 1) + (1 << lev) - 1) >> lev;
   const float* L = O.pyr + O.pyr_off[lev - 1];
+  int b0[3], b1[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    b0[k] = c0[k] >> lev;
+    b1[k] = c1[k] >> lev;   // b1 - b0 <= 2 except at the coarsest level of a huge grid
+  }
+  // 27 independent loads; a block index past b1 repeats b1 (same minimum)
   float m = 3.0e38f;
-  for (int z = c0[2] >> lev; z <= (c1[2] >> lev); ++z)
-    for (int y = c0[1] >> lev; y <= (c1[1] >> lev); ++y)
-      for (int x = c0[0] >> lev; x <= (c1[0] >> lev); ++x) m = fminf(m, __ldg(L + ((size_t)z * by + y) * bx + x));
+#pragma unroll
+  for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 3; ++dx) {
+        const int x = min(b0[0] + dx, b1[0]), y = min(b0[1] + dy, b1[1]), z = min(b0[2] + dz, b1[2]);
+        m = fminf(m, __ldg(L + ((size_t)z * by + y) * bx + x));
+      }
+  // a grid larger than 2^kMaxPyrLevels cells per axis can leave more than 3 blocks
+  if (b1[0] - b0[0] > 2 || b1[1] - b0[1] > 2 || b1[2] - b0[2] > 2) {
+    for (int z = b0[2]; z <= b1[2]; ++z)
+      for (int y = b0[1]; y <= b1[1]; ++y)
+        for (int x = b0[0]; x <= b1[0]; ++x) m = fminf(m, __ldg(L + ((size_t)z * by + y) * bx + x));
+  }
   return m;
 }
 
@@ -491,11 +509,22 @@ __device__ __forceinline__ float f4c(const float4& v, int k) { return k == 0 ? v
 //   d x tau = T_k - s c F_k,    T_k = p x tau_k, F_k = e_k x tau_k
 // so that each inactive simulation costs a few dot products.  G4 holds
 // (Gl_m, 0), (Ga_m, 0) for m = 0..6.
-__device__ __forceinline__ void point_sims_adjoint(const PointState& ps, const float4* __restrict__ G4,
-                                                   const ParamsDev& P, const ObjDev& O, float& dphi, float dn[3],
-                                                   float dp[3]) {
+// Constants of the simulation adjoint for one candidate step, kept in shared
+// memory: K[0] = (1/m, 1/I, c = dt V, c^2), K[1] = (2 c / I, mu, alpha, alpha c),
+// K[2] = (w_pen, 0, 0, 0).
+__device__ __forceinline__ void sim_constants(const ParamsDev& P, const ObjDev& O, float4 K[3]) {
   const float c = P.dt * P.V;
-  const float a = O.inv_mass, b = O.inv_inertia;
+  K[0] = make_float4(O.inv_mass, O.inv_inertia, c, c * c);
+  K[1] = make_float4(2.0f * c * O.inv_inertia, P.mu, P.alpha, P.alpha * c);
+  K[2] = make_float4(P.w_pen, 0.0f, 0.0f, 0.0f);
+}
+
+__device__ __forceinline__ void point_sims_adjoint(const PointState& ps, const float4* __restrict__ G4,
+                                                   const float4* __restrict__ Kp, const ParamsDev& P,
+                                                   const ObjDev& O, float& dphi, float dn[3], float dp[3]) {
+  const float4 K0 = Kp[0], K1 = Kp[1];
+  const float a = K0.x, b = K0.y, c = K0.z, cc = K0.w;
+  const float tbc = K1.x, mu = K1.y, alpha = K1.z, alphac = K1.w;
   const float* n = ps.n;
   float U[3];
   cross3(ps.p, n, U);
@@ -506,8 +535,8 @@ __device__ __forceinline__ void point_sims_adjoint(const PointState& ps, const f
     cmask |= kap ? 1u : 0u;
     const float4 gl = G4[0], ga = G4[1];
     const float gfn = gl.x * n[0] + gl.y * n[1] + gl.z * n[2] + ga.x * U[0] + ga.y * U[1] + ga.z * U[2];
-    const float dC = P.w_pen - __fdividef(gfn, a + b * Uu);
-    dphi -= kap ? 0.0f : P.alpha * dC;
+    const float q = gfn * __fdividef(1.0f, a + b * Uu) - Kp[2].x;
+    dphi = fmaf(alpha, kap ? 0.0f : q, dphi);
   }
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
@@ -517,35 +546,41 @@ __device__ __forceinline__ void point_sims_adjoint(const PointState& ps, const f
     const float rr = rho2 > 0.0f ? rsqrtf(rho2) : 0.0f;     // tau = 0 when n is parallel to e_k
     float tau[3];
     tau[k] = rho2 * rr;
-    tau[i] = -nk * ni * rr;
-    tau[j] = -nk * nj * rr;
+    const float nkr = -nk * rr;
+    tau[i] = nkr * ni;
+    tau[j] = nkr * nj;
     float T[3];
     cross3(ps.p, tau, T);
-    const float Tt = dot3(T, T);
     const float UE = U[j] * ni - U[i] * nj;            // U . E_k
     const float TF = T[j] * tau[i] - T[i] * tau[j];    // T_k . F_k
     const float Fsq = tau[i] * tau[i] + tau[j] * tau[j];
-    const float wn0 = a + b * (Uu + c * c * rho2), wn1 = 2.0f * b * c * UE;
-    const float wt0 = a + b * (Tt + c * c * Fsq), wt1 = 2.0f * b * c * TF;
+    const float wn0 = a + b * fmaf(cc, rho2, Uu), wn1 = tbc * UE;
+    const float wt0 = a + b * fmaf(cc, Fsq, dot3(T, T)), wt1 = tbc * TF;
+    // per-axis parts of the dot products shared by the two signs
+    float gdn[2], gdt[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int m = 1 + 2 * k + h;
-      const float s = h == 0 ? 1.0f : -1.0f;
-      const float sc = s * c;
+      const float4 gl = G4[2 * m], ga = G4[2 * m + 1];
+      const float sc = h == 0 ? c : -c;
+      const float gaE = f4c(ga, j) * ni - f4c(ga, i) * nj;
+      const float gaF = f4c(ga, j) * tau[i] - f4c(ga, i) * tau[j];
+      gdn[h] = fmaf(-sc, gaE, gl.x * n[0] + gl.y * n[1] + gl.z * n[2] + ga.x * U[0] + ga.y * U[1] + ga.z * U[2]);
+      gdt[h] = fmaf(-sc, gaF, gl.x * tau[0] + gl.y * tau[1] + gl.z * tau[2] + ga.x * T[0] + ga.y * T[1] +
+                                  ga.z * T[2]);
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int m = 1 + 2 * k + h;
       const bool kap = sim_phi(ps, m, c) < 0.0f;
       cmask |= kap ? (1u << m) : 0u;
-      const float4 gl = G4[2 * m], ga = G4[2 * m + 1];
-      const float gaE = f4c(ga, j) * ni - f4c(ga, i) * nj;
-      const float gfn = gl.x * n[0] + gl.y * n[1] + gl.z * n[2] + ga.x * U[0] + ga.y * U[1] + ga.z * U[2] -
-                        sc * gaE;
-      const float gaF = f4c(ga, j) * tau[i] - f4c(ga, i) * tau[j];
-      const float gft = gl.x * tau[0] + gl.y * tau[1] + gl.z * tau[2] + ga.x * T[0] + ga.y * T[1] + ga.z * T[2] -
-                        sc * gaF;
-      // dC = -(gf.n)/w_n - mu (gf.t)/w_t with w_n = wn0 - s wn1, w_t = wt0 - s wt1
-      const float dC = -__fdividef(gfn, wn0 - s * wn1) - P.mu * s * __fdividef(gft, wt0 - s * wt1);
-      const float dph = kap ? 0.0f : -P.alpha * dC;
-      dphi += dph;
-      dn[k] -= sc * dph;
+      // dph = -alpha dC,  dC = -(gf.n)/w_n - mu s (gf.tau)/w_t,  w = w0 - s w1
+      const float rwn = __fdividef(1.0f, h == 0 ? wn0 - wn1 : wn0 + wn1);
+      const float rwt = __fdividef(1.0f, h == 0 ? wt0 - wt1 : wt0 + wt1);
+      const float q = fmaf(h == 0 ? mu : -mu, gdt[h] * rwt, gdn[h] * rwn);
+      const float qa = kap ? 0.0f : q;
+      dphi = fmaf(alpha, qa, dphi);
+      dn[k] = fmaf(h == 0 ? -alphac : alphac, qa, dn[k]);
     }
   }
   // simulations in which the point is in contact: general adjoint, one instance

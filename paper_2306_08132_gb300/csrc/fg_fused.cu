@@ -6,14 +6,16 @@
 
 namespace fg {
 
-#define FG_CFG_NW(nw, mb) nw,
-#define FG_CFG_MB(nw, mb) mb,
-#define FG_CFG_LOSSGRAD(nw, mb) &launch_fused_cfg<kModeLossGrad, nw, mb>,
+#define FG_CFG_NW(nw, mb, ppt) nw,
+#define FG_CFG_MB(nw, mb, ppt) mb,
+#define FG_CFG_PPT(nw, mb, ppt) ppt,
+#define FG_CFG_LOSSGRAD(nw, mb, ppt) &launch_fused_cfg<kModeLossGrad, nw, mb, ppt>,
 static const int kCfgNW[] = {FG_FUSED_CONFIGS(FG_CFG_NW)};
 static const int kCfgMinB[] = {FG_FUSED_CONFIGS(FG_CFG_MB)};
+static const int kCfgPPT[] = {FG_FUSED_CONFIGS(FG_CFG_PPT)};
 static const FusedLaunchFn kLossGradLaunch[] = {FG_FUSED_CONFIGS(FG_CFG_LOSSGRAD)};
 constexpr int kNumCfg = sizeof(kCfgNW) / sizeof(kCfgNW[0]);
-constexpr int kDefaultCfg = 1;   // 4 warps per candidate, >= 5 CTAs per SM
+constexpr int kDefaultCfg = 3;   // 4 warps per candidate, >= 8 CTAs per SM, 1 point per thread
 
 static int g_selected[64] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1,
                              -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1,
@@ -21,9 +23,10 @@ static int g_selected[64] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1,
                              -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
 
 int fused_config_count() { return kNumCfg; }
-void fused_config_info(int i, int* nw, int* minb) {
+void fused_config_info(int i, int* nw, int* minb, int* ppt) {
   *nw = kCfgNW[i];
   *minb = kCfgMinB[i];
+  *ppt = kCfgPPT[i];
 }
 static int& selected_slot() {
   int dev = 0;
@@ -41,7 +44,7 @@ cudaError_t launch_fused(int mode, const FusedArgs& a, const fg_hand* h, cudaStr
   if (a.B <= 0) return cudaSuccess;
   const int cfg = fused_config_current();
   switch (mode) {
-    case kModeWrench: return launch_fused_cfg<kModeWrench, 4, 6>(a, st);
+    case kModeWrench: return launch_fused_cfg<kModeWrench, 4, 6, 1>(a, st);
     case kModeLossGrad: return kLossGradLaunch[cfg](a, st);
     default: return kOptimizeLaunch[cfg](a, st);
   }

@@ -35,6 +35,7 @@ struct FusedSmem {
   ObjDev O;
   float4 frame4[kMaxLinks][3];     // rows (R_r0, R_r1, R_r2, o_r) of each link frame
   float4 G4[kSims][2];             // (dL/dW_lin, 0), (dL/dW_ang, 0) per simulation
+  float4 K[3];                     // constants of the simulation adjoint
   float q[64];
   float grad[64];
   float wred[NW][kSims][8];        // per warp: W (6), N, pen
@@ -92,7 +93,79 @@ __device__ __forceinline__ void world_point(const float4* f4, const float4& sp, 
   p[2] = fma_(c.x, sp.x, fma_(c.y, sp.y, fma_(c.z, sp.z, c.w)));
 }
 
-template <int MODE, int NW, int MINB>
+// Adjoint of one hand point (index i, link frames in smem): dL/dp through the 7
+// simulations, the normal and the SDF lookup.  v = (g, (p - t0) x g).
+__device__ __forceinline__ void point_adjoint(const HandDev& H, const float4 (*frame4)[3],
+                                              const float4* __restrict__ G4, const float4* __restrict__ K,
+                                              const ObjDev& O,
+                                              const ParamsDev& Pm, float r, const float t0[3], int i, bool valid,
+                                              float v[6], int& link) {
+  const float4 sp = __ldg(H.pts + i);
+  link = (int)sp.w;
+  float p[3];
+  world_point(frame4[link], sp, p);
+  SdfSample smp;
+  sdf_lookup<true>(O, p, smp);
+  PointState ps;
+  point_state(smp, p, r, ps);
+  float dphi = 0.0f, dn[3] = {0.0f, 0.0f, 0.0f}, dp[3] = {0.0f, 0.0f, 0.0f};
+  point_sims_adjoint(ps, G4, K, Pm, O, dphi, dn, dp);
+  sdf_adjoint(smp, ps, dphi, dn, dp);
+  if (valid) {
+    const float rel[3] = {p[0] - t0[0], p[1] - t0[1], p[2] - t0[2]};
+    float tq[3];
+    cross3(rel, dp, tq);
+    v[0] = dp[0]; v[1] = dp[1]; v[2] = dp[2];
+    v[3] = tq[0]; v[4] = tq[1]; v[5] = tq[2];
+  } else {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) v[k] = 0.0f;
+  }
+}
+
+// Adds 32 points' (g, r x g) to the warp's per-link sums.  Runs of points of one
+// link accumulate in registers (acc, for link cur) and are reduced when the link
+// changes; a group of 32 that straddles links is reduced link by link.
+__device__ __forceinline__ void link_accumulate(float (*lacc)[6], int lane, int link, bool valid, const float v[6],
+                                                int& cur, float acc[6]) {
+  const int l0 = __shfl_sync(kFull, link, 0);
+  const bool uniform = __all_sync(kFull, !valid || link == l0);
+  if (uniform && l0 == cur) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) acc[k] += v[k];
+    return;
+  }
+  if (cur >= 0) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const float sum = warp_sum(acc[k]);
+      if (lane == 0) lacc[cur][k] += sum;
+    }
+  }
+  if (uniform) {
+    cur = l0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) acc[k] = v[k];
+    return;
+  }
+  cur = -1;
+  unsigned remaining = __ballot_sync(kFull, valid);
+  while (remaining) {
+    const int leader = __ffs(remaining) - 1;
+    const int l = __shfl_sync(kFull, link, leader);
+    const bool mine = valid && link == l;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+      const float sum = warp_sum(mine ? v[k] : 0.0f);
+      if (lane == 0) lacc[l][k] += sum;
+    }
+    remaining &= ~__ballot_sync(kFull, mine);
+  }
+#pragma unroll
+  for (int k = 0; k < 6; ++k) acc[k] = 0.0f;
+}
+
+template <int MODE, int NW, int MINB, int PPT>
 __global__ void __launch_bounds__(NW * 32, MINB) fused_step_kernel(FusedArgs a) {
   __shared__ FusedSmem<NW> S;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -112,7 +185,10 @@ __global__ void __launch_bounds__(NW * 32, MINB) fused_step_kernel(FusedArgs a) 
     if (tid == 0) {
       const int oi = a.obj_of_cand ? a.obj_of_cand[c] : 0;
       S.bad_object = oi < 0 || oi >= a.n_obj;
-      if (!S.bad_object) S.O = a.objs[oi];
+      if (!S.bad_object) {
+        S.O = a.objs[oi];
+        sim_constants(a.P, S.O, S.K);
+      }
     }
     __syncthreads();
     if (S.bad_object) {
@@ -136,7 +212,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) fused_step_kernel(FusedArgs a) 
       if (warp == 0) fk_warp(H, S.q, S.frame4, lane);
       for (int idx = tid; idx < NW * kSims * 8; idx += NW * 32) (&S.wred[0][0][0])[idx] = 0.0f;
       __syncthreads();
-      const ObjDev O = S.O;
+      const ObjDev& O = S.O;
 
       // --------------------------------------------------------- chunk culling
       // A chunk of 32 points (one link) can only hold a contact if some point has
@@ -305,67 +381,20 @@ __global__ void __launch_bounds__(NW * 32, MINB) fused_step_kernel(FusedArgs a) 
         const float t0[3] = {S.q[0], S.q[1], S.q[2]};
         int cur = -1;
         float acc[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-        for (int base = pb; base < pe; base += 32) {
-          const int i = base + lane;
-          const bool valid = i < pe;
-          const float4 sp = __ldg(H.pts + (valid ? i : base));
-          const int link = (int)sp.w;
-          float p[3];
-          world_point(S.frame4[link], sp, p);
-          SdfSample smp;
-          sdf_lookup<true>(O, p, smp);
-          PointState ps;
-          point_state(smp, p, r, ps);
-          float dphi = 0.0f, dn[3] = {0.0f, 0.0f, 0.0f}, dp[3] = {0.0f, 0.0f, 0.0f};
-          point_sims_adjoint(ps, &S.G4[0][0], Pm, O, dphi, dn, dp);
-          sdf_adjoint(smp, ps, dphi, dn, dp);
-          float v[6];
-          if (valid) {
-            const float rel[3] = {p[0] - t0[0], p[1] - t0[1], p[2] - t0[2]};
-            float tq[3];
-            cross3(rel, dp, tq);
-            v[0] = dp[0]; v[1] = dp[1]; v[2] = dp[2];
-            v[3] = tq[0]; v[4] = tq[1]; v[5] = tq[2];
-          } else {
+        for (int base = pb; base < pe; base += 32 * PPT) {
+          float v[PPT][6];
+          int link[PPT];
+          bool valid[PPT];
 #pragma unroll
-            for (int k = 0; k < 6; ++k) v[k] = 0.0f;
+          for (int u = 0; u < PPT; ++u) {
+            const int bb = base + 32 * u;
+            const int i = bb + lane;
+            valid[u] = i < pe;
+            point_adjoint(H, S.frame4, &S.G4[0][0], S.K, O, Pm, r, t0, valid[u] ? i : base, valid[u], v[u], link[u]);
           }
-          const int l0 = __shfl_sync(kFull, link, 0);
-          const bool uniform = __all_sync(kFull, !valid || link == l0);
-          if (uniform && l0 == cur) {
 #pragma unroll
-            for (int k = 0; k < 6; ++k) acc[k] += v[k];
-          } else {
-            if (cur >= 0) {
-#pragma unroll
-              for (int k = 0; k < 6; ++k) {
-                const float sum = warp_sum(acc[k]);
-                if (lane == 0) S.lacc[warp][cur][k] += sum;
-              }
-            }
-            if (uniform) {
-              cur = l0;
-#pragma unroll
-              for (int k = 0; k < 6; ++k) acc[k] = v[k];
-            } else {
-              // the 32 points straddle links: reduce each link present separately
-              cur = -1;
-              unsigned remaining = __ballot_sync(kFull, valid);
-              while (remaining) {
-                const int leader = __ffs(remaining) - 1;
-                const int l = __shfl_sync(kFull, link, leader);
-                const bool mine = valid && link == l;
-#pragma unroll
-                for (int k = 0; k < 6; ++k) {
-                  const float sum = warp_sum(mine ? v[k] : 0.0f);
-                  if (lane == 0) S.lacc[warp][l][k] += sum;
-                }
-                remaining &= ~__ballot_sync(kFull, mine);
-              }
-#pragma unroll
-              for (int k = 0; k < 6; ++k) acc[k] = 0.0f;
-            }
-          }
+          for (int u = 0; u < PPT; ++u)
+            if (base + 32 * u < pe) link_accumulate(S.lacc[warp], lane, link[u], valid[u], v[u], cur, acc);
         }
         if (cur >= 0) {
 #pragma unroll
@@ -446,27 +475,29 @@ __global__ void __launch_bounds__(NW * 32, MINB) fused_step_kernel(FusedArgs a) 
 
 // Launch of one compiled configuration: a persistent grid of (SMs x resident
 // CTAs) blocks, capped at B.
-template <int MODE, int NW, int MINB>
+template <int MODE, int NW, int MINB, int PPT>
 cudaError_t launch_fused_cfg(const FusedArgs& a, cudaStream_t st) {
   static int blocks_per_sm[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
   int& bps = blocks_per_sm[dev & 63];
   if (bps <= 0) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fused_step_kernel<MODE, NW, MINB>, NW * 32, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fused_step_kernel<MODE, NW, MINB, PPT>, NW * 32, 0);
     if (e != cudaSuccess) return e;
     if (bps < 1) bps = 1;
   }
   long long grid = (long long)device_sm_count() * bps;
   if (grid > a.B) grid = a.B;
   if (grid < 1) return cudaSuccess;
-  fused_step_kernel<MODE, NW, MINB><<<(int)grid, NW * 32, 0, st>>>(a);
+  fused_step_kernel<MODE, NW, MINB, PPT><<<(int)grid, NW * 32, 0, st>>>(a);
   return cudaGetLastError();
 }
 
 // Compiled configurations of the loss/gradient and optimisation kernels:
-// warps per candidate and the minimum resident CTAs per SM the register
-// allocation is held to.  The autotuner times them on a workload.
-#define FG_FUSED_CONFIGS(X) X(4, 4) X(4, 5) X(4, 6) X(4, 8) X(8, 2) X(8, 3) X(2, 8) X(2, 12)
+// warps per candidate, the minimum resident CTAs per SM the register
+// allocation is held to, and points per thread in the adjoint sweep.  The autotuner times them on a workload.
+// (warps per candidate, min CTAs per SM, points per thread per adjoint iteration)
+#define FG_FUSED_CONFIGS(X) \
+  X(4, 4, 1) X(4, 5, 1) X(4, 6, 1) X(4, 8, 1) X(8, 3, 1) X(2, 8, 1) X(4, 4, 2) X(4, 5, 2) X(2, 8, 2)
 
 }  // namespace fg

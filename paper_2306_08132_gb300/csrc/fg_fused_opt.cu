@@ -4,7 +4,7 @@
 
 namespace fg {
 
-#define FG_CFG_OPT(nw, mb) &launch_fused_cfg<kModeOptimize, nw, mb>,
+#define FG_CFG_OPT(nw, mb, ppt) &launch_fused_cfg<kModeOptimize, nw, mb, ppt>,
 extern const FusedLaunchFn kOptimizeLaunch[] = {FG_FUSED_CONFIGS(FG_CFG_OPT)};
 
 }  // namespace fg

@@ -61,7 +61,7 @@ typedef cudaError_t (*FusedLaunchFn)(const FusedArgs&, cudaStream_t);
 extern const FusedLaunchFn kOptimizeLaunch[];
 cudaError_t launch_fused(int mode, const FusedArgs& a, const fg_hand* h, cudaStream_t st);
 int fused_config_count();
-void fused_config_info(int i, int* nw, int* minb);
+void fused_config_info(int i, int* nw, int* minb, int* ppt);
 int fused_config_current();
 void fused_config_select(int i);
 cudaError_t autotune_fused(const FusedArgs& base, int reps, float* times_ms, int* best, cudaStream_t st);
