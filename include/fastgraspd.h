@@ -196,6 +196,32 @@ fg_status fg_optimize_step_plain(const fg_hand* hand, const fg_scene* scene, con
                                  int total_steps, int nsteps, float* loss, void* workspace,
                                  size_t workspace_bytes, void* stream);
 
+/* ------------------------------------------------------------ no allocation */
+
+/* Bytes of the scratch array built into the library for
+ * fg_optimize_step_plain_noalloc (held on every GPU that loads the library). */
+#define FG_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* The paper has no counterpart to this entry point; it exists for callers that
+ * cannot allocate device memory while running (a real-time planning loop that
+ * must not block or fail on an allocation mid-cycle, or a host whose device
+ * memory belongs to another runtime's allocator).  It runs the same step as
+ * fg_optimize_step_plain with the per-stage scratch in a fixed array of
+ * FG_NOALLOC_SCRATCH_BYTES inside the library, and calls no allocator.
+ * Arguments as fg_optimize_step_plain, without the workspace.
+ *  - FG_ERR_INVALID (with a message) when the step needs more scratch than the
+ *    array holds (fg_plain_workspace_size(hand, B) > FG_NOALLOC_SCRATCH_BYTES;
+ *    about 490,000 candidate points).
+ *  - The first call on a device looks up the array's device address (once per
+ *    device, with that device current); make that first call before any stream
+ *    capture.
+ *  - All calls share the one array and its contents persist between calls
+ *    (each call writes all the scratch it reads).  Calls whose work overlaps on
+ *    the GPU, e.g. on two unordered streams, race on it: order them. */
+fg_status fg_optimize_step_plain_noalloc(const fg_hand* hand, const fg_scene* scene, const int* obj_of_cand,
+                                         float* q, int B, const fg_params* host_params, int step,
+                                         int total_steps, int nsteps, float* loss, void* stream);
+
 /* ------------------------------------------------------------------ tuning */
 
 /* The fused kernels are compiled in several configurations: warps per

@@ -67,6 +67,7 @@ SIGNATURES = {
     "fg_optimize_step": [_vp, _vp, _vp, _vp, _i, C.POINTER(Params), _i, _i, _i, _vp, _vp],
     "fg_plain_workspace_size": [_vp, _i, C.POINTER(C.c_size_t)],
     "fg_optimize_step_plain": [_vp, _vp, _vp, _vp, _i, C.POINTER(Params), _i, _i, _i, _vp, _vp, C.c_size_t, _vp],
+    "fg_optimize_step_plain_noalloc": [_vp, _vp, _vp, _vp, _i, C.POINTER(Params), _i, _i, _i, _vp, _vp],
     "fg_fused_config_count": [C.POINTER(_i)],
     "fg_fused_config_info": [_i, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i)],
     "fg_fused_config_select": [_i],

@@ -255,3 +255,20 @@ def autotune(hand: Hand, scene: Scene, q: torch.Tensor, params: dict, step: int 
                                   int(step), int(total_steps), int(nsteps), int(reps), times, C.byref(best),
                                   _stream()), "fg_autotune")
     return best.value, [float(t) for t in times]
+
+
+def optimize_step_plain_noalloc(hand: Hand, scene: Scene, q: torch.Tensor, params: dict, step: int,
+                                total_steps: int, nsteps: int = 1, obj_of_cand: torch.Tensor | None = None,
+                                loss: torch.Tensor | None = None):
+    """The per-stage step with its scratch in the library's built-in array instead
+    of a workspace (for callers that cannot allocate device memory while running;
+    B * P is limited by FG_NOALLOC_SCRATCH_BYTES).  Calls that overlap on the GPU
+    share that array and must be ordered."""
+    B = q.shape[0]
+    _dptr(q, "q", shape=(B, hand.D))
+    prm = make_params(params)
+    check(_lib.load().fg_optimize_step_plain_noalloc(hand.handle, scene.handle, _oc(obj_of_cand, B), _dptr(q, "q"),
+                                                     B, C.byref(prm), int(step), int(total_steps), int(nsteps),
+                                                     _dptr(loss, "loss", shape=(B,)) if loss is not None else None,
+                                                     _stream()), "fg_optimize_step_plain_noalloc")
+    return loss
