@@ -99,8 +99,8 @@ def load_traffic(kernel_tag: str):
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
-    from paper_2306_08132_gb300.build import source_hash
-    cur = source_hash()
+    from paper_2306_08132_gb300.build import source_hash, FUSED_SOURCES
+    cur = source_hash(FUSED_SOURCES)
     for line in open(path):
         parts = line.split()
         if len(parts) >= 3 and parts[0] == kernel_tag and parts[1] == cur:

@@ -40,11 +40,19 @@ def _inputs() -> list[str]:
     return files + [os.path.abspath(__file__)]
 
 
-def source_hash() -> str:
-    """Short hash of every source and header the library is built from."""
+# Sources that define the fused kernel (its profile stays valid while they are unchanged).
+FUSED_SOURCES = ("fg_device.cuh", "fg_fused_kernel.cuh", "fg_fused.cu", "fg_fused_opt.cu", "fg_internal.h",
+                 "fastgraspd.h")
+
+
+def source_hash(names=None) -> str:
+    """Short hash of the sources and headers the library is built from (or of the
+    named files only)."""
     import hashlib
     h = hashlib.sha256()
     for f in sorted(_inputs()):
+        if names is not None and os.path.basename(f) not in names:
+            continue
         if f.endswith((".cu", ".cuh", ".h")):
             h.update(os.path.basename(f).encode())
             with open(f, "rb") as fh:

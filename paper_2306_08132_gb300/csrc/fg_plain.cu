@@ -258,29 +258,46 @@ __global__ void contact_adj_kernel(const HandDev* __restrict__ Hp, const ObjDev*
 }
 
 // 7: per-link sums of g and (p - t) x g, one CTA (256 threads) per candidate.
+// Points are sorted by link, so a warp's 32 points usually share one link: those
+// are reduced with shuffles and added once; mixed warps add point by point.
 __global__ void link_reduce_kernel(const HandDev* __restrict__ Hp, int B, const float* __restrict__ q,
                                    const float* __restrict__ pts, const float* __restrict__ dpo,
                                    float* __restrict__ lsum) {
   __shared__ float acc[kMaxLinks][6];
   const HandDev& H = *Hp;
   const int b = blockIdx.x;
+  const int lane = threadIdx.x & 31;
   for (int k = threadIdx.x; k < kMaxLinks * 6; k += blockDim.x) (&acc[0][0])[k] = 0.0f;
   __syncthreads();
   size_t BP = (size_t)B * H.P;
   const float t0[3] = {q[(size_t)b * H.D], q[(size_t)b * H.D + 1], q[(size_t)b * H.D + 2]};
-  for (int i = threadIdx.x; i < H.P; i += blockDim.x) {
-    size_t idx = (size_t)b * H.P + i;
-    int l = (int)__ldg(H.pts + i).w;
-    float g[3] = {dpo[idx], dpo[BP + idx], dpo[2 * BP + idx]};
-    float rel[3] = {pts[idx] - t0[0], pts[BP + idx] - t0[1], pts[2 * BP + idx] - t0[2]};
-    float tq[3];
-    cross3(rel, g, tq);
-    atomicAdd(&acc[l][0], g[0]);
-    atomicAdd(&acc[l][1], g[1]);
-    atomicAdd(&acc[l][2], g[2]);
-    atomicAdd(&acc[l][3], tq[0]);
-    atomicAdd(&acc[l][4], tq[1]);
-    atomicAdd(&acc[l][5], tq[2]);
+  for (int base = threadIdx.x - lane; base < H.P; base += blockDim.x) {
+    const int i = base + lane;
+    const bool valid = i < H.P;
+    float v[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+    int l = 0;
+    if (valid) {
+      const size_t idx = (size_t)b * H.P + i;
+      l = (int)__ldg(H.pts + i).w;
+      const float g[3] = {dpo[idx], dpo[BP + idx], dpo[2 * BP + idx]};
+      const float rel[3] = {pts[idx] - t0[0], pts[BP + idx] - t0[1], pts[2 * BP + idx] - t0[2]};
+      float tq[3];
+      cross3(rel, g, tq);
+      v[0] = g[0]; v[1] = g[1]; v[2] = g[2];
+      v[3] = tq[0]; v[4] = tq[1]; v[5] = tq[2];
+    }
+    const int l0 = __shfl_sync(0xffffffffu, l, 0);
+    if (__all_sync(0xffffffffu, !valid || l == l0)) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) {
+        float x = v[k];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) atomicAdd(&acc[l0][k], x);
+      }
+    } else if (valid) {
+#pragma unroll
+      for (int k = 0; k < 6; ++k) atomicAdd(&acc[l][k], v[k]);
+    }
   }
   __syncthreads();
   for (int k = threadIdx.x; k < H.L * 6; k += blockDim.x) lsum[(size_t)b * H.L * 6 + k] = (&acc[0][0])[k];
