@@ -196,6 +196,65 @@ fg_status fg_optimize_step_plain(const fg_hand* hand, const fg_scene* scene, con
                                  int total_steps, int nsteps, float* loss, void* workspace,
                                  size_t workspace_bytes, void* stream);
 
+/* ------------------------------------------------------------ request queue */
+
+/* A request queue runs many grasp searches at once with continuous batching
+ * (the paper's problem of Sec. III for a stream of objects, hands and candidate
+ * counts).  It owns a scheduler thread and a CUDA stream on the device current
+ * at creation.  A submitted request waits until a slot is free and its device
+ * footprint fits the HBM budget: q and loss (B (D + 1) 4 bytes) plus the
+ * object's grid and min-pyramid, counted once per object while any admitted
+ * request uses it.  Each round launches one fused kernel over the candidates of
+ * all admitted requests, up to steps_per_launch optimisation steps each;
+ * finished requests are copied to host memory and free their slot and bytes,
+ * and waiting requests join at the next round.  A request's result is the same
+ * alone and in any mix (candidates are independent).  The hand and object
+ * handles of a request must stay alive until its result is collected. */
+
+#define FG_QUEUE_MAX_SLOTS 64
+
+typedef struct {
+  int max_slots;          /* requests on the GPU at once, <= FG_QUEUE_MAX_SLOTS (0: 32)       */
+  int max_requests;       /* submitted and not yet collected (0: 4096)                         */
+  int steps_per_launch;   /* optimisation steps per request per round (0: 10)                  */
+  int timeout_ms;         /* bound on the wait for one round (0: 60000); past it the round's
+                             requests fail with FG_ERR_TIMEOUT and the queue takes no more work */
+} fg_queue_opts;
+
+typedef struct {
+  const fg_hand* hand;
+  const fg_sdf* sdf;
+  int B;                  /* candidates, >= 1                                   */
+  int steps;              /* gradient-descent steps, >= 1 (schedule over steps) */
+  const float* host_q0;   /* [B][D] initial candidates, copied at submit        */
+  fg_params params;
+} fg_request;
+
+typedef struct {
+  int pending, active, finished, failed;
+  size_t bytes_in_use, budget;
+  uint64_t rounds, candidate_steps;
+} fg_queue_stat;
+
+/* Errors: FG_ERR_INVALID, FG_ERR_OOM, FG_ERR_CUDA. */
+fg_status fg_queue_create(size_t hbm_budget_bytes, const fg_queue_opts* opts, fg_queue** out);
+/* Non-blocking.  FG_ERR_BUDGET if the request alone exceeds the budget (it could
+ * never be admitted); FG_ERR_BUSY if max_requests are outstanding; FG_ERR_INVALID
+ * for a malformed request. */
+fg_status fg_queue_submit(fg_queue* queue, const fg_request* host_req, uint64_t* id);
+/* Non-blocking: *done = 1 once the request finished (or failed). */
+fg_status fg_queue_poll(fg_queue* queue, uint64_t id, int* done);
+/* Blocks up to timeout_ms; FG_ERR_TIMEOUT if the request has not finished. */
+fg_status fg_queue_wait(fg_queue* queue, uint64_t id, int timeout_ms);
+/* Copies the final q [B][D] and the loss of the last step [B] (either nullable)
+ * and the latency from submit to completion, then forgets the request.
+ * FG_ERR_BUSY if not finished; the request's error if it failed. */
+fg_status fg_queue_result(fg_queue* queue, uint64_t id, float* host_q, float* host_loss, double* latency_s);
+fg_status fg_queue_stats(fg_queue* queue, fg_queue_stat* out);
+/* Waiting requests are dropped, the round in flight completes, then the
+ * queue's resources are freed. */
+fg_status fg_queue_destroy(fg_queue* queue);
+
 /* ------------------------------------------------------------ no allocation */
 
 /* Bytes of the scratch array built into the library for

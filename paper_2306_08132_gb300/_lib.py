@@ -40,7 +40,18 @@ class Params(C.Structure):
 
 class QueueOpts(C.Structure):
     _fields_ = [("max_slots", C.c_int), ("max_requests", C.c_int), ("steps_per_launch", C.c_int),
-                ("poll_limit", C.c_int)]
+                ("timeout_ms", C.c_int)]
+
+
+class Request(C.Structure):
+    _fields_ = [("hand", C.c_void_p), ("sdf", C.c_void_p), ("B", C.c_int), ("steps", C.c_int),
+                ("host_q0", C.POINTER(C.c_float)), ("params", Params)]
+
+
+class QueueStat(C.Structure):
+    _fields_ = [("pending", C.c_int), ("active", C.c_int), ("finished", C.c_int), ("failed", C.c_int),
+                ("bytes_in_use", C.c_size_t), ("budget", C.c_size_t), ("rounds", C.c_uint64),
+                ("candidate_steps", C.c_uint64)]
 
 
 _vp = C.c_void_p
@@ -68,6 +79,13 @@ SIGNATURES = {
     "fg_plain_workspace_size": [_vp, _i, C.POINTER(C.c_size_t)],
     "fg_optimize_step_plain": [_vp, _vp, _vp, _vp, _i, C.POINTER(Params), _i, _i, _i, _vp, _vp, C.c_size_t, _vp],
     "fg_optimize_step_plain_noalloc": [_vp, _vp, _vp, _vp, _i, C.POINTER(Params), _i, _i, _i, _vp, _vp],
+    "fg_queue_create": [C.c_size_t, C.POINTER(QueueOpts), C.POINTER(_vp)],
+    "fg_queue_submit": [_vp, C.POINTER(Request), C.POINTER(C.c_uint64)],
+    "fg_queue_poll": [_vp, C.c_uint64, C.POINTER(_i)],
+    "fg_queue_wait": [_vp, C.c_uint64, _i],
+    "fg_queue_result": [_vp, C.c_uint64, C.POINTER(_f), C.POINTER(_f), C.POINTER(C.c_double)],
+    "fg_queue_stats": [_vp, C.POINTER(QueueStat)],
+    "fg_queue_destroy": [_vp],
     "fg_fused_config_count": [C.POINTER(_i)],
     "fg_fused_config_info": [_i, C.POINTER(_i), C.POINTER(_i), C.POINTER(_i)],
     "fg_fused_config_select": [_i],

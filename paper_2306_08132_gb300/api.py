@@ -272,3 +272,60 @@ def optimize_step_plain_noalloc(hand: Hand, scene: Scene, q: torch.Tensor, param
                                                      _dptr(loss, "loss", shape=(B,)) if loss is not None else None,
                                                      _stream()), "fg_optimize_step_plain_noalloc")
     return loss
+
+
+class Queue:
+    """fg_queue: continuous-batching request queue on the current device."""
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int = 0, max_requests: int = 0,
+                 steps_per_launch: int = 0, timeout_ms: int = 0):
+        lib = _lib.load()
+        opts = _lib.QueueOpts(max_slots, max_requests, steps_per_launch, timeout_ms)
+        h = C.c_void_p()
+        check(lib.fg_queue_create(int(hbm_budget_bytes), C.byref(opts), C.byref(h)), "fg_queue_create")
+        self.handle = h
+        self._shapes = {}
+
+    def submit(self, hand: Hand, sdf: Sdf, q0: np.ndarray, steps: int, params: dict) -> int:
+        q0 = np.ascontiguousarray(q0, dtype=np.float32)
+        if q0.ndim != 2 or q0.shape[1] != hand.D:
+            raise ValueError("q0 must be [B, %d]" % hand.D)
+        req = _lib.Request(hand.handle.value, sdf.handle.value, q0.shape[0], int(steps),
+                           q0.ctypes.data_as(C.POINTER(C.c_float)), make_params(params))
+        rid = C.c_uint64()
+        check(_lib.load().fg_queue_submit(self.handle, C.byref(req), C.byref(rid)), "fg_queue_submit")
+        self._shapes[rid.value] = q0.shape
+        return rid.value
+
+    def poll(self, rid: int) -> bool:
+        done = C.c_int()
+        check(_lib.load().fg_queue_poll(self.handle, rid, C.byref(done)), "fg_queue_poll")
+        return bool(done.value)
+
+    def wait(self, rid: int, timeout_ms: int) -> None:
+        check(_lib.load().fg_queue_wait(self.handle, rid, int(timeout_ms)), "fg_queue_wait")
+
+    def result(self, rid: int):
+        """(q [B, D], loss [B], latency seconds); forgets the request."""
+        B, D = self._shapes[rid]
+        q = np.empty((B, D), dtype=np.float32)
+        loss = np.empty(B, dtype=np.float32)
+        lat = C.c_double()
+        check(_lib.load().fg_queue_result(self.handle, rid, q.ctypes.data_as(C.POINTER(C.c_float)),
+                                          loss.ctypes.data_as(C.POINTER(C.c_float)), C.byref(lat)),
+              "fg_queue_result")
+        del self._shapes[rid]
+        return q, loss, lat.value
+
+    def stats(self) -> dict:
+        st = _lib.QueueStat()
+        check(_lib.load().fg_queue_stats(self.handle, C.byref(st)), "fg_queue_stats")
+        return {k: getattr(st, k) for k, _ in st._fields_}
+
+    def close(self) -> None:
+        if getattr(self, "handle", None) is not None and _lib._lib is not None:
+            _lib._lib.fg_queue_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        self.close()

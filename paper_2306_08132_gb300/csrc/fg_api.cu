@@ -300,6 +300,7 @@ fg_status fg_sdf_create(const float* grid, int nx, int ny, int nz, const float* 
   }
   o.pyr = s->pyr;
   o.pyr_levels = levels;
+  s->pyr_bytes = sizeof(float) * pf;
   *out = s;
   return FG_OK;
 }

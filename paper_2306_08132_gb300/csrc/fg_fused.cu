@@ -50,6 +50,12 @@ cudaError_t launch_fused(int mode, const FusedArgs& a, const fg_hand* h, cudaStr
   }
 }
 
+// One round of a request queue: every active request's candidates in one launch.
+cudaError_t launch_queue_round(const FusedArgs& a, cudaStream_t st) {
+  if (a.B <= 0) return cudaSuccess;
+  return launch_fused_cfg<kModeQueue, 4, 6, 1>(a, st);
+}
+
 cudaError_t autotune_fused(const FusedArgs& base, int reps, float* times_ms, int* best, cudaStream_t st) {
   const size_t qbytes = sizeof(float) * (size_t)base.B * 64;
   (void)qbytes;

@@ -46,6 +46,13 @@ struct FusedSmem {
   int n_active;
   unsigned active_bits[kMaxCullChunks / 32];
   unsigned short active_list[kMaxCullChunks];
+  // source of the current candidate (the call's arguments, or a queue slot)
+  ParamsDev Pm;
+  const HandDev* src_hand;
+  const HandDev* hand_loaded;
+  float* qout;
+  float* lout;
+  int cl, step0, total, nsteps;
 };
 
 // Point range of warp w: contiguous, 32-aligned chunks.
@@ -168,28 +175,60 @@ __device__ __forceinline__ void link_accumulate(float (*lacc)[6], int lane, int 
 template <int MODE, int NW, int MINB, int PPT>
 __global__ void __launch_bounds__(NW * 32, MINB) fused_step_kernel(FusedArgs a) {
   __shared__ FusedSmem<NW> S;
+  constexpr bool kOpt = MODE == kModeOptimize || MODE == kModeQueue;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  if (tid == 0) S.H = *a.hand;
-  __syncthreads();
+  if (tid == 0) S.hand_loaded = nullptr;
   const HandDev& H = S.H;
-  const int D = H.D, P = H.P, L = H.L;
-  const ParamsDev& Pm = a.P;
-  const float dtV = Pm.dt * Pm.V;
-  int pb, pe;
-  warp_range(P, NW, warp, pb, pe);
-  const int nwords = (P + 31) >> 5;
+  const ParamsDev& Pm = S.Pm;
 
   for (int c = blockIdx.x; c < a.B; c += gridDim.x) {
     __syncthreads();
-    if (tid < D) S.q[tid] = a.q[(size_t)c * D + tid];
     if (tid == 0) {
-      const int oi = a.obj_of_cand ? a.obj_of_cand[c] : 0;
-      S.bad_object = oi < 0 || oi >= a.n_obj;
-      if (!S.bad_object) {
-        S.O = a.objs[oi];
-        sim_constants(a.P, S.O, S.K);
+      if (MODE == kModeQueue) {
+        // candidate c of the round belongs to the slot whose range holds it
+        int sl = 0;
+        while (sl + 1 < a.nslots && a.slots[sl + 1].cand_start <= c) ++sl;
+        const QueueSlotDev& Q = a.slots[sl];
+        S.src_hand = Q.hand;
+        S.O = Q.obj;
+        S.Pm = Q.P;
+        S.cl = c - Q.cand_start;
+        S.qout = Q.q;
+        S.lout = Q.loss;
+        S.step0 = Q.step0;
+        S.total = Q.total_steps;
+        S.nsteps = Q.nsteps;
+        S.bad_object = 0;
+      } else {
+        S.src_hand = a.hand;
+        S.Pm = a.P;
+        S.cl = c;
+        S.qout = a.q;
+        S.lout = a.loss;
+        S.step0 = a.step0;
+        S.total = a.total_steps;
+        S.nsteps = MODE == kModeOptimize ? a.nsteps : 1;
+        const int oi = a.obj_of_cand ? a.obj_of_cand[c] : 0;
+        S.bad_object = oi < 0 || oi >= a.n_obj;
+        if (!S.bad_object) S.O = a.objs[oi];
       }
     }
+    __syncthreads();
+    if (S.src_hand != S.hand_loaded) {          // uniform: every thread reads the same words
+      const int* src = reinterpret_cast<const int*>(S.src_hand);
+      int* dst = reinterpret_cast<int*>(&S.H);
+      for (int k = tid; k < (int)(sizeof(HandDev) / sizeof(int)); k += NW * 32) dst[k] = src[k];
+      __syncthreads();
+      if (tid == 0) S.hand_loaded = S.src_hand;
+    }
+    const int D = H.D, P = H.P, L = H.L;
+    const float dtV = Pm.dt * Pm.V;
+    int pb, pe;
+    warp_range(P, NW, warp, pb, pe);
+    const int nwords = (P + 31) >> 5;
+    const int cl = S.cl;
+    if (tid < D) S.q[tid] = S.qout[(size_t)cl * D + tid];
+    if (tid == 0 && !S.bad_object) sim_constants(Pm, S.O, S.K);
     __syncthreads();
     if (S.bad_object) {
       // an object index outside the scene: NaN outputs, q left unchanged
@@ -205,9 +244,9 @@ __global__ void __launch_bounds__(NW * 32, MINB) fused_step_kernel(FusedArgs a) 
       }
       continue;
     }
-    const int nsteps = MODE == kModeOptimize ? a.nsteps : 1;
+    const int nsteps = S.nsteps;
     for (int s = 0; s < nsteps; ++s) {
-      const float r = MODE == kModeOptimize ? dilation_at(Pm, a.step0 + s, a.total_steps) : a.r_fixed;
+      const float r = kOpt ? dilation_at(Pm, S.step0 + s, S.total) : a.r_fixed;
       __syncthreads();
       if (warp == 0) fk_warp(H, S.q, S.frame4, lane);
       for (int idx = tid; idx < NW * kSims * 8; idx += NW * 32) (&S.wred[0][0][0])[idx] = 0.0f;
@@ -463,12 +502,12 @@ __global__ void __launch_bounds__(NW * 32, MINB) fused_step_kernel(FusedArgs a) 
         if (tid == 0) a.loss[c] = S.loss;
       } else {  // optimize
         if (tid < D) S.q[tid] -= Pm.lr * S.grad[tid];
-        if (tid == 0 && a.loss && s == nsteps - 1) a.loss[c] = S.loss;
+        if (tid == 0 && S.lout && s == nsteps - 1) S.lout[cl] = S.loss;
       }
     }
-    if (MODE == kModeOptimize) {
+    if (kOpt) {
       __syncthreads();
-      if (tid < D) a.q[(size_t)c * D + tid] = S.q[tid];
+      if (tid < D) S.qout[(size_t)cl * D + tid] = S.q[tid];
     }
   }
 }

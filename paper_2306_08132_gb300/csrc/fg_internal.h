@@ -21,7 +21,8 @@ struct fg_sdf {
   fg::ObjDev host;           // grid and pyramid: device pointers owned by this handle
   float* grid;
   float* pyr;
-  size_t bytes;
+  size_t bytes;              // grid bytes
+  size_t pyr_bytes;          // min-pyramid bytes
 };
 
 struct fg_scene {
@@ -39,7 +40,18 @@ size_t min_pyramid_floats(int nx, int ny, int nz, int* levels);
 cudaError_t build_min_pyramid(const float* grid, int nx, int ny, int nz, float* pyr, int levels, int* offsets);
 
 // fused kernels (fg_fused.cu)
-enum FusedMode { kModeWrench = 0, kModeLossGrad = 1, kModeOptimize = 2 };
+enum FusedMode { kModeWrench = 0, kModeLossGrad = 1, kModeOptimize = 2, kModeQueue = 3 };
+
+// One active request of a queue round: candidates [cand_start, cand_start + B)
+// of the round's launch step this request's q from step0 for nsteps steps.
+struct QueueSlotDev {
+  const HandDev* hand;
+  float* q;
+  float* loss;
+  ObjDev obj;
+  ParamsDev P;
+  int cand_start, B, step0, total_steps, nsteps;
+};
 struct FusedArgs {
   const HandDev* hand;
   const ObjDev* objs;
@@ -56,6 +68,8 @@ struct FusedArgs {
   int* ncontact;
   uint32_t* bits;
   int hand_D;
+  const QueueSlotDev* slots;   // queue mode: slot table (device), sorted by cand_start
+  int nslots;
 };
 typedef cudaError_t (*FusedLaunchFn)(const FusedArgs&, cudaStream_t);
 extern const FusedLaunchFn kOptimizeLaunch[];
@@ -65,6 +79,7 @@ void fused_config_info(int i, int* nw, int* minb, int* ppt);
 int fused_config_current();
 void fused_config_select(int i);
 cudaError_t autotune_fused(const FusedArgs& base, int reps, float* times_ms, int* best, cudaStream_t st);
+cudaError_t launch_queue_round(const FusedArgs& a, cudaStream_t st);
 
 // per-stage kernels (fg_plain.cu)
 size_t plain_workspace_bytes(const fg_hand* h, int B);
