@@ -138,6 +138,44 @@ def oracle_rate(w, budget_s: float, r: float, max_cands: int | None = None):
     return done / dt, done, dt, torch.get_num_threads()
 
 
+def run_serving(fg, n_requests: int, rate_hz: float, device, budget_bytes: int, steps_per_launch: int = 10):
+    """Replays a Poisson stream of grasp-search requests into a request queue in
+    real time and returns latency percentiles and throughput."""
+    import synth
+    from synth.workloads import build_request
+    specs = synth.serving_stream(n_requests=n_requests, rate_hz=rate_hz)
+    cache = {}
+    built = []
+    for sp in specs:
+        hand_d, obj, q0, params, steps = build_request(sp, device=device, hand_cache=cache)
+        key = sp["hand_kind"]
+        if ("h", key) not in cache:
+            cache[("h", key)] = fg.Hand.from_synth(hand_d)
+        built.append((cache[("h", key)], fg.Sdf.from_synth(obj), q0, params, steps, sp["arrival_s"]))
+    queue = fg.Queue(budget_bytes, steps_per_launch=steps_per_launch)
+    ids, lat = [], []
+    cand_steps = sum(b[2].shape[0] * b[4] for b in built)
+    t0 = time.perf_counter()
+    try:
+        for hand, sdf, q0, params, steps, t_arr in built:
+            while time.perf_counter() - t0 < t_arr:
+                time.sleep(0.0005)
+            ids.append(queue.submit(hand, sdf, q0, steps, params))
+        for rid in ids:
+            queue.wait(rid, 600000)
+            lat.append(queue.result(rid)[2])
+        makespan = time.perf_counter() - t0
+        st = queue.stats()
+    finally:
+        queue.close()
+    lat = np.array(lat)
+    return {"requests": n_requests, "arrival_rate_hz": rate_hz, "p50_s": float(np.percentile(lat, 50)),
+            "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()), "makespan_s": makespan,
+            "candidate_steps_per_s": cand_steps / makespan, "rounds": st["rounds"],
+            "steps_per_launch": steps_per_launch,
+            "note": "offered load exceeds capacity at this arrival rate; latency includes queueing"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -181,6 +219,8 @@ def main():
     ap.add_argument("--profile-kernel", action="store_true",
                     help="set up the workload, run a few fused launches and exit (for ncu)")
     ap.add_argument("--config", type=int, default=None, help="fused configuration index (default: autotune)")
+    ap.add_argument("--serving", type=int, default=40, help="requests in the serving (p50/p99) run; 0 skips it")
+    ap.add_argument("--serving-rate", type=float, default=200.0)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -341,6 +381,11 @@ def main():
                 "traffic": load_traffic("fused_step"), "kernel_ms": kern_ms,
                 "flops_per_launch": flops, "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
 
+    serving = None
+    if args.serving > 0:
+        free, _ = torch.cuda.mem_get_info()
+        serving = run_serving(fg, args.serving, args.serving_rate, dev, int(0.5 * free))
+
     if rank == 0:
         r0 = O.dilation_radius(O.Params.from_dict(w.params), 0, K)
         rate, n, dt, cores = oracle_rate(w, args.cpu_budget, r0)
@@ -359,6 +404,8 @@ def main():
                                             "autotune_ms": {"%dw/%d/%dp" % c: round(t, 4)
                                                             for c, t in zip(cfgs, cfg_ms)}}},
                 "plain": plain, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
+                "latency": None if serving is None else {"p50_s": serving["p50_s"], "p99_s": serving["p99_s"]},
+                "serving": serving,
                 "gpu_launches": args.steps * 1, "clocks": clocks, "wall_s_timed_region": wall,
                 "per_step_ms": {"min": float(np.min(ms)), "median": float(np.median(ms)), "max": float(np.max(ms))}}
         print(json.dumps(line))

@@ -171,7 +171,8 @@ fg_status fg_contact_wrench(const fg_hand* hand, const fg_scene* scene, const in
 
 /* Loss and gradient (Eqs. 2-4, Sec. III-C leaky rule) at dilation r_dil,
  * forward and adjoint fused in one kernel (the adjoint recomputes the forward
- * per point; nothing per point is stored).  loss: [B]; grad: [B][D] nullable. */
+ * per point; nothing per point is stored).  loss: [B]; grad: [B][D] nullable
+ * (NULL: the loss alone, without the adjoint sweep). */
 fg_status fg_loss_and_grad(const fg_hand* hand, const fg_scene* scene, const int* obj_of_cand,
                            const float* q, int B, const fg_params* host_params, float r_dil,
                            float* loss, float* grad, void* stream);

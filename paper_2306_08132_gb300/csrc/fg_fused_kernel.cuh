@@ -406,6 +406,10 @@ __global__ void __launch_bounds__(NW * 32, MINB) fused_step_kernel(FusedArgs a) 
       }
       for (int idx = tid; idx < NW * kMaxLinks * 6; idx += NW * 32) (&S.lacc[0][0][0])[idx] = 0.0f;
       __syncthreads();
+      if (MODE == kModeLossGrad && a.grad == nullptr) {    // loss only: no adjoint
+        if (tid == 0) a.loss[c] = S.loss;
+        continue;
+      }
       if (MODE == kModeWrench) {
         for (int idx = tid; idx < kSims * 6; idx += NW * 32) {
           const int m = idx / 6, k = idx % 6;
