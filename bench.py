@@ -108,16 +108,30 @@ def load_traffic(kernel_tag: str):
     return None
 
 
-def build_workload(device, rank):
+def build_workload(device, rank, n_obj=8, per_obj=1024, grid_n=128):
+    """The benchmark workload for one rank.  Weak scaling: every rank holds the same
+    objects and its own share of the global candidate set (rank 0 the recipe's
+    candidates, rank k > 0 candidates drawn from seed base + 100 + k), so ranks
+    never exchange data."""
     import synth
-    w = synth.batched_superquadric_workload(device=device)
+    w = synth.batched_superquadric_workload(n_obj=n_obj, per_obj=per_obj, grid_n=grid_n, device=device)
     if rank:
-        # weak scaling: every rank gets its own candidates (same shape, other seed)
         rng = np.random.default_rng(synth.workloads.SEED_BASE + 100 + rank)
         from synth.candidates import sample_candidates
-        q = [sample_candidates(rng, w.hand, 1024, o["bound_radius"] + 0.06) for o in w.objects]
+        q = [sample_candidates(rng, w.hand, per_obj, o["bound_radius"] + 0.06) for o in w.objects]
         w.q0 = np.concatenate(q)
     return w
+
+
+def max_over_ranks(value: float, world: int, device="cpu") -> float:
+    """The slowest rank's time (the whole job is done when the last rank is)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def oracle_rate(w, budget_s: float, r: float, max_cands: int | None = None):
@@ -329,11 +343,7 @@ def main():
     ms = timed(fused_graph, args.steps, args.warmup)
     wall = time.perf_counter() - t_wall
     clocks = sampler.stop()
-    ms_step = float(np.mean(ms))
-    if world > 1:
-        t = torch.tensor([ms_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(float(np.mean(ms)), world, dev)
     cand_steps = w.B * S_in * world
     value = cand_steps / (ms_step / 1000.0)
 
@@ -357,11 +367,7 @@ def main():
         hloss.copy_(loss, non_blocking=True)
 
     ems = timed(e2e_step, max(3, args.steps // 2), 3)
-    e2e_ms = float(np.mean(ems))
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(float(np.mean(ems)), world, dev)
     e2e = {"value": cand_steps / (e2e_ms / 1000.0), "unit": "candidate-steps/s",
            "h2d_bytes_per_step": int(hq0.numel() * 4), "d2h_bytes_per_step": int(hq.numel() * 4 + hloss.numel() * 4)}
 
