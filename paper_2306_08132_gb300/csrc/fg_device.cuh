@@ -181,58 +181,79 @@ struct SdfSample {
   bool outside;
 };
 
-template <bool kHess>
-__device__ __forceinline__ void sdf_lookup(const ObjDev& O, const float p[3], SdfSample& s) {
-  const float n_max[3] = {(float)(O.nx - 1), (float)(O.ny - 1), (float)(O.nz - 1)};
-  float u[3], uc[3], du[3], f[3];
-  int i0[3];
+// The lookup in three parts, so that a sweep can issue the next point's corner
+// loads before it computes the current point: sdf_index (cell and fractions),
+// sdf_gather (the 8 corner values), sdf_finish (value, gradient, curvature).
+struct SdfIndex {
+  float f[3], du[3];
   bool clamped[3];
+  const float* cell;   // corner (i0, j0, k0)
+};
+
+__device__ __forceinline__ void sdf_index(const ObjDev& O, const float p[3], SdfIndex& ix) {
+  const float n_max[3] = {(float)(O.nx - 1), (float)(O.ny - 1), (float)(O.nz - 1)};
+  int i0[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    u[k] = fma_(p[k], O.inv_h, O.uo[k]);
-    uc[k] = fminf(fmaxf(u[k], 0.0f), n_max[k]);     // NaN -> 0
-    clamped[k] = uc[k] != u[k];
-    du[k] = sub_(u[k], uc[k]);                       // 0 unless clamped
-    const int ii = (int)floorf(uc[k]);
+    const float u = fma_(p[k], O.inv_h, O.uo[k]);
+    const float uc = fminf(fmaxf(u, 0.0f), n_max[k]);     // NaN -> 0
+    ix.clamped[k] = uc != u;
+    ix.du[k] = sub_(u, uc);                               // 0 unless clamped
+    const int ii = (int)floorf(uc);
     const int cap = (int)n_max[k] - 1;
     i0[k] = ii < cap ? ii : cap;
-    f[k] = sub_(uc[k], (float)i0[k]);
+    ix.f[k] = sub_(uc, (float)i0[k]);
   }
-  const int sx = 1, sy = O.nx, sz = O.nx * O.ny;
-  const float* G = O.grid + ((size_t)i0[2] * O.ny + i0[1]) * O.nx + i0[0];
-  float c000 = __ldg(G), c100 = __ldg(G + sx);
-  float c010 = __ldg(G + sy), c110 = __ldg(G + sy + sx);
-  float c001 = __ldg(G + sz), c101 = __ldg(G + sz + sx);
-  float c011 = __ldg(G + sz + sy), c111 = __ldg(G + sz + sy + sx);
+  ix.cell = O.grid + ((size_t)i0[2] * O.ny + i0[1]) * O.nx + i0[0];
+}
+
+__device__ __forceinline__ void sdf_gather(const ObjDev& O, const float* G, float c[8]) {
+  const int sy = O.nx, sz = O.nx * O.ny;
+  c[0] = __ldg(G);
+  c[1] = __ldg(G + 1);
+  c[2] = __ldg(G + sy);
+  c[3] = __ldg(G + sy + 1);
+  c[4] = __ldg(G + sz);
+  c[5] = __ldg(G + sz + 1);
+  c[6] = __ldg(G + sz + sy);
+  c[7] = __ldg(G + sz + sy + 1);
+}
+
+// c = (c000, c100, c010, c110, c001, c101, c011, c111)
+template <bool kHess>
+__device__ __forceinline__ void sdf_finish(const ObjDev& O, const SdfIndex& ix, const float c[8], SdfSample& s) {
+  const float* f = ix.f;
   // trilinear in differences: x first, then y, then z
-  float dx00 = sub_(c100, c000), dx10 = sub_(c110, c010), dx01 = sub_(c101, c001), dx11 = sub_(c111, c011);
-  float x00 = fma_(f[0], dx00, c000), x10 = fma_(f[0], dx10, c010);
-  float x01 = fma_(f[0], dx01, c001), x11 = fma_(f[0], dx11, c011);
-  float dy0 = sub_(x10, x00), dy1 = sub_(x11, x01);
-  float y0 = fma_(f[1], dy0, x00), y1 = fma_(f[1], dy1, x01);
-  float dz = sub_(y1, y0);
-  float val = fma_(f[2], dz, y0);
-  float ey0 = sub_(dx10, dx00), ey1 = sub_(dx11, dx01);
-  float a0 = fma_(f[1], ey0, dx00), a1 = fma_(f[1], ey1, dx01);
-  float dax = sub_(a1, a0);
-  float gx = fma_(f[2], dax, a0);             // d/dfx
-  float ddy = sub_(dy1, dy0);
-  float gy = fma_(f[2], ddy, dy0);            // d/dfy
-  float gz = dz;                              // d/dfz
-  s.g[0] = clamped[0] ? 0.0f : mul_(gx, O.inv_h);
-  s.g[1] = clamped[1] ? 0.0f : mul_(gy, O.inv_h);
-  s.g[2] = clamped[2] ? 0.0f : mul_(gz, O.inv_h);
+  const float dx00 = sub_(c[1], c[0]), dx10 = sub_(c[3], c[2]), dx01 = sub_(c[5], c[4]), dx11 = sub_(c[7], c[6]);
+  const float x00 = fma_(f[0], dx00, c[0]), x10 = fma_(f[0], dx10, c[2]);
+  const float x01 = fma_(f[0], dx01, c[4]), x11 = fma_(f[0], dx11, c[6]);
+  const float dy0 = sub_(x10, x00), dy1 = sub_(x11, x01);
+  const float y0 = fma_(f[1], dy0, x00), y1 = fma_(f[1], dy1, x01);
+  const float dz = sub_(y1, y0);
+  const float val = fma_(f[2], dz, y0);
+  const float ey0 = sub_(dx10, dx00), ey1 = sub_(dx11, dx01);
+  const float a0 = fma_(f[1], ey0, dx00), a1 = fma_(f[1], ey1, dx01);
+  const float dax = sub_(a1, a0);
+  const float gx = fma_(f[2], dax, a0);             // d/dfx
+  const float ddy = sub_(dy1, dy0);
+  const float gy = fma_(f[2], ddy, dy0);            // d/dfy
+  const float gz = dz;                              // d/dfz
+  const bool* cl = ix.clamped;
+  s.g[0] = cl[0] ? 0.0f : mul_(gx, O.inv_h);
+  s.g[1] = cl[1] ? 0.0f : mul_(gy, O.inv_h);
+  s.g[2] = cl[2] ? 0.0f : mul_(gz, O.inv_h);
   if (kHess) {
-    float ih2 = mul_(O.inv_h, O.inv_h);
-    float hxy = fma_(f[2], sub_(ey1, ey0), ey0);
-    s.hxy = (clamped[0] || clamped[1]) ? 0.0f : mul_(hxy, ih2);
-    s.hxz = (clamped[0] || clamped[2]) ? 0.0f : mul_(dax, ih2);
-    s.hyz = (clamped[1] || clamped[2]) ? 0.0f : mul_(ddy, ih2);
+    const float ih2 = mul_(O.inv_h, O.inv_h);
+    const float hxy = fma_(f[2], sub_(ey1, ey0), ey0);
+    s.hxy = (cl[0] || cl[1]) ? 0.0f : mul_(hxy, ih2);
+    s.hxz = (cl[0] || cl[2]) ? 0.0f : mul_(dax, ih2);
+    s.hyz = (cl[1] || cl[2]) ? 0.0f : mul_(ddy, ih2);
   }
-  s.outside = clamped[0] || clamped[1] || clamped[2];
+  s.outside = cl[0] || cl[1] || cl[2];
   s.e = 0.0f;
   s.eh[0] = s.eh[1] = s.eh[2] = 0.0f;
   if (s.outside) {
+    const float* du = ix.du;
     const float dn2 = fma_(du[0], du[0], fma_(du[1], du[1], mul_(du[2], du[2])));
     const float r = rsqrtf(dn2);                     // dn2 > 0 outside the grid
     const float dn = mul_(dn2, r);
@@ -244,6 +265,15 @@ __device__ __forceinline__ void sdf_lookup(const ObjDev& O, const float p[3], Sd
     s.e = mul_(O.h, dn);
   }
   s.phi = add_(val, s.e);
+}
+
+template <bool kHess>
+__device__ __forceinline__ void sdf_lookup(const ObjDev& O, const float p[3], SdfSample& s) {
+  SdfIndex ix;
+  sdf_index(O, p, ix);
+  float c[8];
+  sdf_gather(O, ix.cell, c);
+  sdf_finish<kHess>(O, ix, c, s);
 }
 
 // Lower bound of the interpolated SDF over every point whose index coordinates
@@ -583,15 +613,16 @@ __device__ __forceinline__ void point_sims_adjoint(const PointState& ps, const f
       dn[k] = fmaf(h == 0 ? -alphac : alphac, qa, dn[k]);
     }
   }
-  // simulations in which the point is in contact: general adjoint, one instance
-  if (cmask) {
-#pragma unroll 1
-    for (int m = 0; m < kSims; ++m) {
-      if ((cmask >> m) & 1u) {
-        const float4 gl = G4[2 * m], ga = G4[2 * m + 1];
-        const float Gl[3] = {gl.x, gl.y, gl.z}, Ga[3] = {ga.x, ga.y, ga.z};
-        sim_adjoint(ps, m, sim_phi(ps, m, c), true, Gl, Ga, P, O, m == 0 ? P.w_pen : 0.0f, dphi, dn, dp);
-      }
+  // simulations in which some lane of the warp is in contact: general adjoint,
+  // one instance, visiting only those simulations
+  unsigned wmask = __reduce_or_sync(0xffffffffu, cmask);
+  while (wmask) {
+    const int m = __ffs(wmask) - 1;
+    wmask &= wmask - 1u;
+    if ((cmask >> m) & 1u) {
+      const float4 gl = G4[2 * m], ga = G4[2 * m + 1];
+      const float Gl[3] = {gl.x, gl.y, gl.z}, Ga[3] = {ga.x, ga.y, ga.z};
+      sim_adjoint(ps, m, sim_phi(ps, m, c), true, Gl, Ga, P, O, m == 0 ? P.w_pen : 0.0f, dphi, dn, dp);
     }
   }
 }

@@ -15,7 +15,7 @@ static const int kCfgMinB[] = {FG_FUSED_CONFIGS(FG_CFG_MB)};
 static const int kCfgPPT[] = {FG_FUSED_CONFIGS(FG_CFG_PPT)};
 static const FusedLaunchFn kLossGradLaunch[] = {FG_FUSED_CONFIGS(FG_CFG_LOSSGRAD)};
 constexpr int kNumCfg = sizeof(kCfgNW) / sizeof(kCfgNW[0]);
-constexpr int kDefaultCfg = 3;   // 4 warps per candidate, >= 8 CTAs per SM, 1 point per thread
+constexpr int kDefaultCfg = 2;   // 4 warps per candidate, >= 6 CTAs per SM, 1 point per thread
 
 static int g_selected[64] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1,
                              -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1,

@@ -309,45 +309,57 @@ __global__ void __launch_bounds__(NW * 32, MINB) fused_step_kernel(FusedArgs a) 
       }
 
       // ---------------------------------------------------------------- sweep 1
-      const int n_work = cull ? S.n_active : H.nchunks;
-      for (int idx = warp; idx < n_work; idx += NW) {
-        const int base = 32 * (cull ? (int)S.active_list[idx] : idx);
-        const int i = base + lane;
-        const bool valid = i < P;
-        const float4 sp = __ldg(H.pts + (valid ? i : base));
-        float p[3];
-        world_point(S.frame4[(int)sp.w], sp, p);
-        SdfSample smp;
-        sdf_lookup<false>(O, p, smp);
-        PointState ps;
-        point_state(smp, p, r, ps);
-#pragma unroll 1
+      {
+        // per-thread wrench sums (registers), contact counts from ballots (warp-uniform)
+        float W[kSims][6], cnt[kSims], pen = 0.0f;
+#pragma unroll
         for (int m = 0; m < kSims; ++m) {
-          const float phm = sim_phi(ps, m, dtV);
-          const bool kap = valid && phm < 0.0f;
-          const unsigned bal = __ballot_sync(kFull, kap);
-          if (MODE == kModeWrench && lane == 0 && a.bits)
-            a.bits[((size_t)c * kSims + m) * nwords + (base >> 5)] = bal;
-          if (bal) {
-            float v[7] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+          cnt[m] = 0.0f;
+#pragma unroll
+          for (int k = 0; k < 6; ++k) W[m][k] = 0.0f;
+        }
+        const int n_work = cull ? S.n_active : H.nchunks;
+        for (int idx = warp; idx < n_work; idx += NW) {
+          const int base = 32 * (cull ? (int)S.active_list[idx] : idx);
+          const int i = base + lane;
+          const bool valid = i < P;
+          const float4 sp = __ldg(H.pts + (valid ? i : base));
+          float p[3];
+          world_point(S.frame4[(int)sp.w], sp, p);
+          SdfSample smp;
+          sdf_lookup<false>(O, p, smp);
+          PointState ps;
+          point_state(smp, p, r, ps);
+#pragma unroll
+          for (int m = 0; m < kSims; ++m) {
+            const float phm = sim_phi(ps, m, dtV);
+            const bool kap = valid && phm < 0.0f;
+            const unsigned bal = __ballot_sync(kFull, kap);
+            cnt[m] += (float)__popc(bal);
+            if (MODE == kModeWrench && lane == 0 && a.bits)
+              a.bits[((size_t)c * kSims + m) * nwords + (base >> 5)] = bal;
             if (kap) {
               float f[3], d[3], tq[3];
               contact_force(ps, m, -phm, Pm, O, f, d);
               cross3(d, f, tq);
-              v[0] = f[0]; v[1] = f[1]; v[2] = f[2];
-              v[3] = tq[0]; v[4] = tq[1]; v[5] = tq[2];
-              v[6] = -phm;
-            }
-#pragma unroll
-            for (int k = 0; k < 7; ++k) v[k] = warp_sum(v[k]);
-            if (lane == 0) {
-#pragma unroll
-              for (int k = 0; k < 6; ++k) S.wred[warp][m][k] += v[k];
-              S.wred[warp][m][6] += (float)__popc(bal);
-              if (m == 0) S.wred[warp][0][7] += v[6];
+              W[m][0] += f[0]; W[m][1] += f[1]; W[m][2] += f[2];
+              W[m][3] += tq[0]; W[m][4] += tq[1]; W[m][5] += tq[2];
+              if (m == 0) pen -= phm;
             }
           }
         }
+        // one reduction per warp and step
+#pragma unroll
+        for (int m = 0; m < kSims; ++m) {
+#pragma unroll
+          for (int k = 0; k < 6; ++k) {
+            const float v = warp_sum(W[m][k]);
+            if (lane == 0) S.wred[warp][m][k] = v;
+          }
+          if (lane == 0) S.wred[warp][m][6] = cnt[m];
+        }
+        pen = warp_sum(pen);
+        if (lane == 0) S.wred[warp][0][7] = pen;
       }
       __syncthreads();
 
@@ -540,7 +552,6 @@ cudaError_t launch_fused_cfg(const FusedArgs& a, cudaStream_t st) {
 // warps per candidate, the minimum resident CTAs per SM the register
 // allocation is held to, and points per thread in the adjoint sweep.  The autotuner times them on a workload.
 // (warps per candidate, min CTAs per SM, points per thread per adjoint iteration)
-#define FG_FUSED_CONFIGS(X) \
-  X(4, 4, 1) X(4, 5, 1) X(4, 6, 1) X(4, 8, 1) X(8, 3, 1) X(2, 8, 1) X(4, 4, 2) X(4, 5, 2) X(2, 8, 2)
+#define FG_FUSED_CONFIGS(X) X(4, 4, 1) X(4, 5, 1) X(4, 6, 1) X(4, 8, 1) X(8, 3, 1) X(2, 8, 1)
 
 }  // namespace fg
