@@ -197,6 +197,20 @@ fg_status fg_hand_create(const fg_hand_desc* d, fg_hand** out) {
     spheres[j] = make_float4(cf[0], cf[1], cf[2], (float)(rad * (1.0 + 1e-6) + 1e-7));
     clink[j] = l;
   }
+  // adjoint work units: each link's points in runs of at most kUnitPoints
+  std::vector<int4> units;
+  {
+    int i = 0;
+    for (int l = 0; l < L; ++l) {
+      H.unit_begin[l] = (int)units.size();
+      int e = i;
+      while (e < P && d->link_of_point[e] == l) ++e;
+      for (int b = i; b < e; b += kUnitPoints) units.push_back(make_int4(b, std::min(kUnitPoints, e - b), l, 0));
+      i = e;
+    }
+    H.unit_begin[L] = (int)units.size();
+    H.nunits = (int)units.size();
+  }
   fg_hand* h = new (std::nothrow) fg_hand;
   if (!h) return FG_ERR_OOM;
   std::memset(h, 0, sizeof(*h));
@@ -204,6 +218,7 @@ fg_status fg_hand_create(const fg_hand_desc* d, fg_hand** out) {
     cudaFree(h->pts);
     cudaFree(h->chunk_sphere);
     cudaFree(h->chunk_link);
+    cudaFree(h->units);
     cudaFree(h->dev);
     delete h;
     return cuda_status(e, what);
@@ -211,14 +226,18 @@ fg_status fg_hand_create(const fg_hand_desc* d, fg_hand** out) {
   cudaError_t e = cudaMalloc(&h->pts, sizeof(float4) * P);
   if (e == cudaSuccess) e = cudaMalloc(&h->chunk_sphere, sizeof(float4) * nchunks);
   if (e == cudaSuccess) e = cudaMalloc(&h->chunk_link, sizeof(int) * nchunks);
+  if (e == cudaSuccess) e = cudaMalloc(&h->units, sizeof(int4) * std::max<size_t>(units.size(), 1));
   if (e == cudaSuccess) e = cudaMalloc(&h->dev, sizeof(HandDev));
   if (e != cudaSuccess) return fail(e, "fg_hand_create: cudaMalloc");
   H.pts = h->pts;
   H.chunk_sphere = h->chunk_sphere;
   H.chunk_link = h->chunk_link;
+  H.units = h->units;
   e = cudaMemcpy(h->pts, pts.data(), sizeof(float4) * P, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(h->chunk_sphere, spheres.data(), sizeof(float4) * nchunks, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(h->chunk_link, clink.data(), sizeof(int) * nchunks, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !units.empty())
+    e = cudaMemcpy(h->units, units.data(), sizeof(int4) * units.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy(h->dev, &H, sizeof(HandDev), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return fail(e, "fg_hand_create: cudaMemcpy");
   h->host = H;
@@ -232,6 +251,7 @@ fg_status fg_hand_destroy(fg_hand* h) {
   cudaFree(h->pts);
   cudaFree(h->chunk_sphere);
   cudaFree(h->chunk_link);
+  cudaFree(h->units);
   cudaFree(h->dev);
   delete h;
   return FG_OK;

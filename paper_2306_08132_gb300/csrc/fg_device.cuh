@@ -13,6 +13,7 @@
 #include <stdint.h>
 
 #include "fastgraspd.h"
+#include "fg_vec.cuh"
 
 namespace fg {
 
@@ -34,7 +35,13 @@ struct HandDev {
   const float4* pts;             // [P] (x, y, z, link index as float)
   const float4* chunk_sphere;    // [nchunks] bounding sphere in the link frame (centre, radius)
   const int* chunk_link;         // [nchunks] link of the chunk, -1 when it spans two links
+  // work units of the adjoint sweep: runs of at most kUnitPoints points of one link
+  int nunits;
+  int unit_begin[kMaxLinks + 1]; // units of link l: [unit_begin[l], unit_begin[l + 1])
+  const int4* units;             // [nunits] (first point, point count, link, 0)
 };
+
+constexpr int kUnitPoints = 64;
 
 // Chunks a fused CTA can cull in shared memory (hands up to 8,192 points).
 constexpr int kMaxCullChunks = 256;
@@ -169,17 +176,20 @@ __device__ __forceinline__ void transform_point(const float* R, const float* o, 
 
 // ------------------------------------------------------------------------- SDF
 
-// Result of one grid lookup.  g is the gradient of the undilated SDF; Hxy, Hxz,
-// Hyz the mixed second derivatives of the trilinear part (zero on clamped axes);
-// when the point lies outside the grid, eh = (u - u_c)/|u - u_c| and e the excess.
-struct SdfSample {
-  float phi;
-  float g[3];
-  float hxy, hxz, hyz;
-  float eh[3];
-  float e;
-  bool outside;
+// Result of one grid lookup (V = float: one point; float2: two points).  g is
+// the gradient of the undilated SDF; hxy, hxz, hyz the mixed second derivatives
+// of the trilinear part (zero on clamped axes); when the point lies outside the
+// grid, eh = (u - u_c)/|u - u_c| and e the excess distance.
+template <class V>
+struct SdfSampleT {
+  V phi;
+  V g[3];
+  V hxy, hxz, hyz;
+  V eh[3];
+  V e;
+  mask_t<V> outside;
 };
+using SdfSample = SdfSampleT<float>;
 
 // The lookup in three parts, so that a sweep can issue the next point's corner
 // loads before it computes the current point: sdf_index (cell and fractions),
@@ -219,52 +229,79 @@ __device__ __forceinline__ void sdf_gather(const ObjDev& O, const float* G, floa
   c[7] = __ldg(G + sz + sy + 1);
 }
 
-// c = (c000, c100, c010, c110, c001, c101, c011, c111)
-template <bool kHess>
-__device__ __forceinline__ void sdf_finish(const ObjDev& O, const SdfIndex& ix, const float c[8], SdfSample& s) {
-  const float* f = ix.f;
+__device__ __forceinline__ float rsqrt_or_zero(float x) { return x > 0.0f ? rsqrtf(x) : 0.0f; }
+__device__ __forceinline__ float rcp_or_zero(float x) { return x > 0.0f ? __fdividef(1.0f, x) : 0.0f; }
+__device__ __forceinline__ float rcp_fast(float x) { return __fdividef(1.0f, x); }
+
+// Value, gradient and (kHess) mixed second derivatives from the fractions f, the
+// excess du = u - u_c, the clamp flags and the corners
+// c = (c000, c100, c010, c110, c001, c101, c011, c111).
+template <bool kHess, class V>
+__device__ __forceinline__ void sdf_finish_v(const ObjDev& O, const V f[3], const V du[3], const mask_t<V> cl[3],
+                                             const V c[8], SdfSampleT<V>& s) {
   // trilinear in differences: x first, then y, then z
-  const float dx00 = sub_(c[1], c[0]), dx10 = sub_(c[3], c[2]), dx01 = sub_(c[5], c[4]), dx11 = sub_(c[7], c[6]);
-  const float x00 = fma_(f[0], dx00, c[0]), x10 = fma_(f[0], dx10, c[2]);
-  const float x01 = fma_(f[0], dx01, c[4]), x11 = fma_(f[0], dx11, c[6]);
-  const float dy0 = sub_(x10, x00), dy1 = sub_(x11, x01);
-  const float y0 = fma_(f[1], dy0, x00), y1 = fma_(f[1], dy1, x01);
-  const float dz = sub_(y1, y0);
-  const float val = fma_(f[2], dz, y0);
-  const float ey0 = sub_(dx10, dx00), ey1 = sub_(dx11, dx01);
-  const float a0 = fma_(f[1], ey0, dx00), a1 = fma_(f[1], ey1, dx01);
-  const float dax = sub_(a1, a0);
-  const float gx = fma_(f[2], dax, a0);             // d/dfx
-  const float ddy = sub_(dy1, dy0);
-  const float gy = fma_(f[2], ddy, dy0);            // d/dfy
-  const float gz = dz;                              // d/dfz
-  const bool* cl = ix.clamped;
-  s.g[0] = cl[0] ? 0.0f : mul_(gx, O.inv_h);
-  s.g[1] = cl[1] ? 0.0f : mul_(gy, O.inv_h);
-  s.g[2] = cl[2] ? 0.0f : mul_(gz, O.inv_h);
+  const V dx00 = vsub(c[1], c[0]), dx10 = vsub(c[3], c[2]), dx01 = vsub(c[5], c[4]), dx11 = vsub(c[7], c[6]);
+  const V x00 = vfma(f[0], dx00, c[0]), x10 = vfma(f[0], dx10, c[2]);
+  const V x01 = vfma(f[0], dx01, c[4]), x11 = vfma(f[0], dx11, c[6]);
+  const V dy0 = vsub(x10, x00), dy1 = vsub(x11, x01);
+  const V y0 = vfma(f[1], dy0, x00), y1 = vfma(f[1], dy1, x01);
+  const V dz = vsub(y1, y0);
+  const V val = vfma(f[2], dz, y0);
+  const V ey0 = vsub(dx10, dx00), ey1 = vsub(dx11, dx01);
+  const V a0 = vfma(f[1], ey0, dx00), a1 = vfma(f[1], ey1, dx01);
+  const V dax = vsub(a1, a0);
+  const V gx = vfma(f[2], dax, a0);             // d/dfx
+  const V ddy = vsub(dy1, dy0);
+  const V gy = vfma(f[2], ddy, dy0);            // d/dfy
+  const V gz = dz;                              // d/dfz
+  const V zero = vsplat<V>(0.0f), ih = vsplat<V>(O.inv_h);
+  s.g[0] = vsel(cl[0], zero, vmul(gx, ih));
+  s.g[1] = vsel(cl[1], zero, vmul(gy, ih));
+  s.g[2] = vsel(cl[2], zero, vmul(gz, ih));
   if (kHess) {
-    const float ih2 = mul_(O.inv_h, O.inv_h);
-    const float hxy = fma_(f[2], sub_(ey1, ey0), ey0);
-    s.hxy = (cl[0] || cl[1]) ? 0.0f : mul_(hxy, ih2);
-    s.hxz = (cl[0] || cl[2]) ? 0.0f : mul_(dax, ih2);
-    s.hyz = (cl[1] || cl[2]) ? 0.0f : mul_(ddy, ih2);
+    const V ih2 = vsplat<V>(mul_(O.inv_h, O.inv_h));
+    const V hxy = vfma(f[2], vsub(ey1, ey0), ey0);
+    s.hxy = vsel(mor(cl[0], cl[1]), zero, vmul(hxy, ih2));
+    s.hxz = vsel(mor(cl[0], cl[2]), zero, vmul(dax, ih2));
+    s.hyz = vsel(mor(cl[1], cl[2]), zero, vmul(ddy, ih2));
   }
-  s.outside = cl[0] || cl[1] || cl[2];
-  s.e = 0.0f;
-  s.eh[0] = s.eh[1] = s.eh[2] = 0.0f;
-  if (s.outside) {
-    const float* du = ix.du;
-    const float dn2 = fma_(du[0], du[0], fma_(du[1], du[1], mul_(du[2], du[2])));
-    const float r = rsqrtf(dn2);                     // dn2 > 0 outside the grid
-    const float dn = mul_(dn2, r);
+  s.outside = mor(mor(cl[0], cl[1]), cl[2]);
+  s.e = zero;
+  s.eh[0] = s.eh[1] = s.eh[2] = zero;
+  if (many(s.outside)) {
+    // du is exactly 0 on unclamped axes, so points inside the grid get eh = 0, e = 0
+    const V dn2 = vfma(du[0], du[0], vfma(du[1], du[1], vmul(du[2], du[2])));
+    const V r = vmap(dn2, rsqrt_or_zero);
+    const V dn = vmul(dn2, r);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      s.eh[k] = mul_(du[k], r);
-      s.g[k] = add_(s.g[k], s.eh[k]);
+      s.eh[k] = vmul(du[k], r);
+      s.g[k] = vsel(s.outside, vadd(s.g[k], s.eh[k]), s.g[k]);
     }
-    s.e = mul_(O.h, dn);
+    s.e = vmul(vsplat<V>(O.h), dn);
   }
-  s.phi = add_(val, s.e);
+  s.phi = vadd(val, s.e);
+}
+
+template <bool kHess>
+__device__ __forceinline__ void sdf_finish(const ObjDev& O, const SdfIndex& ix, const float c[8], SdfSample& s) {
+  sdf_finish_v<kHess, float>(O, ix.f, ix.du, ix.clamped, c, s);
+}
+
+// Two lookups in packed form (points a and b).
+__device__ __forceinline__ void sdf_finish_pair(const ObjDev& O, const SdfIndex& ia, const SdfIndex& ib,
+                                                const float ca[8], const float cb[8], SdfSampleT<float2>& s) {
+  float2 f[3], du[3], c[8];
+  bool2 cl[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    f[k] = make_float2(ia.f[k], ib.f[k]);
+    du[k] = make_float2(ia.du[k], ib.du[k]);
+    cl[k] = bool2{ia.clamped[k], ib.clamped[k]};
+  }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) c[k] = make_float2(ca[k], cb[k]);
+  sdf_finish_v<true, float2>(O, f, du, cl, c, s);
 }
 
 template <bool kHess>
@@ -340,32 +377,49 @@ __device__ __forceinline__ float dot3(const float a[3], const float b[3]) {
 }
 
 // Per-point quantities shared by the 7 simulations.
-struct PointState {
-  float p[3];       // world position (= object frame: canonical object pose)
-  float n[3];       // unit normal grad/|grad|
-  float rg;         // 1/|grad|
-  float phi_hat;    // dilated SDF
+template <class V>
+struct PointStateT {
+  V p[3];       // world position (= object frame: canonical object pose)
+  V n[3];       // unit normal grad/|grad|
+  V rg;         // 1/|grad|
+  V phi_hat;    // dilated SDF
 };
+using PointState = PointStateT<float>;
 
-__device__ __forceinline__ void point_state(const SdfSample& s, const float p[3], float r_dil, PointState& ps) {
-  float g2 = fma_(s.g[0], s.g[0], fma_(s.g[1], s.g[1], mul_(s.g[2], s.g[2])));
-  float rg = g2 > 0.0f ? rsqrtf(g2) : 0.0f;
+template <class V>
+__device__ __forceinline__ void point_state(const SdfSampleT<V>& s, const V p[3], float r_dil, PointStateT<V>& ps) {
+  const V g2 = vfma(s.g[0], s.g[0], vfma(s.g[1], s.g[1], vmul(s.g[2], s.g[2])));
+  const V rg = vmap(g2, rsqrt_or_zero);
   ps.rg = rg;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     ps.p[k] = p[k];
-    ps.n[k] = mul_(s.g[k], rg);
+    ps.n[k] = vmul(s.g[k], rg);
   }
-  ps.phi_hat = sub_(s.phi, r_dil);
+  ps.phi_hat = vsub(s.phi, vsplat<V>(r_dil));
+}
+
+// Lane l of a packed point state.
+__device__ __forceinline__ PointState point_lane(const PointStateT<float2>& ps, int l) {
+  PointState o;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    o.p[k] = vlane(ps.p[k], l);
+    o.n[k] = vlane(ps.n[k], l);
+  }
+  o.rg = vlane(ps.rg, l);
+  o.phi_hat = vlane(ps.phi_hat, l);
+  return o;
 }
 
 // Constraint value on the plane through the query for simulation m:
 // phi_m = phi_hat - dt n . v_m.
-__device__ __forceinline__ float sim_phi(const PointState& ps, int m, float dtV) {
+template <class V>
+__device__ __forceinline__ V sim_phi(const PointStateT<V>& ps, int m, float dtV) {
   if (m == 0) return ps.phi_hat;
   const int ax = sim_axis(m);
-  const float nk = ax == 0 ? ps.n[0] : (ax == 1 ? ps.n[1] : ps.n[2]);
-  return fma_(-sim_sign(m) * dtV, nk, ps.phi_hat);
+  const V nk = ax == 0 ? ps.n[0] : (ax == 1 ? ps.n[1] : ps.n[2]);
+  return vfma(vsplat<V>(-sim_sign(m) * dtV), nk, ps.phi_hat);
 }
 
 // Unit direction of test velocity m (zero for m = 0), by selects so that a
@@ -525,104 +579,175 @@ __device__ __forceinline__ void sim_adjoint(const PointState& ps, int m, float p
   for (int k = 0; k < 3; ++k) dn[k] -= dtV * vd[k] * dphi;
 }
 
-// Component k of a float4 (k is a compile-time constant after unrolling).
-__device__ __forceinline__ float f4c(const float4& v, int k) { return k == 0 ? v.x : (k == 1 ? v.y : v.z); }
+// Constants of the simulation adjoint for one candidate step, in shared memory.
+// Scalar table (float index):  0 1/m, 1 1/I, 2 c = dt V, 3 c^2, 4 2c/I, 5 mu,
+// 6 alpha, 7 alpha c, 8 -c, 9 -mu, 10 -alpha c, 11 -w_pen, 12 w_pen.  The packed
+// table holds each entry twice (a float2 per entry), so that a packed operand is
+// one shared-memory load.
+enum SimConst { kcA = 0, kcB, kcC, kcCC, kcTBC, kcMu, kcAlpha, kcAlphaC, kcMC, kcMMu, kcMAlphaC, kcMWpen, kcWpen,
+                kcCount };
+struct SimConsts {
+  float s[16];
+  float2 p[16];
+};
+__device__ __forceinline__ void sim_constants(const ParamsDev& P, const ObjDev& O, SimConsts& K) {
+  const float c = P.dt * P.V;
+  const float v[kcCount] = {O.inv_mass, O.inv_inertia, c, c * c, 2.0f * c * O.inv_inertia, P.mu, P.alpha,
+                            P.alpha * c, -c, -P.mu, -P.alpha * c, -P.w_pen, P.w_pen};
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const float x = k < kcCount ? v[k] : 0.0f;
+    K.s[k] = x;
+    K.p[k] = make_float2(x, x);
+  }
+}
+__device__ __forceinline__ float simk(const SimConsts& K, float, int k) { return K.s[k]; }
+__device__ __forceinline__ float2 simk(const SimConsts& K, float2, int k) { return K.p[k]; }
 
-// Adjoint of all 7 simulations at one point.  A simulation whose constraint is
-// active (phi_m < 0) takes the general path (sim_adjoint).  An inactive one has
-// C = 0, so only the leaky slope survives:
+// Wrench adjoint of simulation m, (dL/dW_lin, dL/dW_ang), in shared memory:
+// scalar as (Gl, 0), (Ga, 0); packed with every component twice.
+struct SimAdjoints {
+  float4 s[kSims][2];
+  float4 p[kSims][3];
+};
+__device__ __forceinline__ void set_sim_adjoint(SimAdjoints& G, int m, const float gl[3], const float ga[3]) {
+  G.s[m][0] = make_float4(gl[0], gl[1], gl[2], 0.0f);
+  G.s[m][1] = make_float4(ga[0], ga[1], ga[2], 0.0f);
+  G.p[m][0] = make_float4(gl[0], gl[0], gl[1], gl[1]);
+  G.p[m][1] = make_float4(gl[2], gl[2], ga[0], ga[0]);
+  G.p[m][2] = make_float4(ga[1], ga[1], ga[2], ga[2]);
+}
+__device__ __forceinline__ void get_sim_adjoint(const SimAdjoints& G, int m, float gl[3], float ga[3]) {
+  const float4 a = G.s[m][0], b = G.s[m][1];
+  gl[0] = a.x; gl[1] = a.y; gl[2] = a.z;
+  ga[0] = b.x; ga[1] = b.y; ga[2] = b.z;
+}
+__device__ __forceinline__ void get_sim_adjoint(const SimAdjoints& G, int m, float2 gl[3], float2 ga[3]) {
+  const float4 a = G.p[m][0], b = G.p[m][1], c = G.p[m][2];
+  gl[0] = make_float2(a.x, a.y); gl[1] = make_float2(a.z, a.w);
+  gl[2] = make_float2(b.x, b.y); ga[0] = make_float2(b.z, b.w);
+  ga[1] = make_float2(c.x, c.y); ga[2] = make_float2(c.z, c.w);
+}
+
+// gl . a + ga . b
+template <class V>
+__device__ __forceinline__ V dot6(const V gl[3], const V a[3], const V ga[3], const V b[3]) {
+  return vfma(gl[0], a[0], vfma(gl[1], a[1], vfma(gl[2], a[2], vfma(ga[0], b[0], vfma(ga[1], b[1], vmul(ga[2], b[2]))))));
+}
+
+// Adjoint of all 7 simulations at one point (V = float) or two points (float2).
+// A simulation whose constraint is active (phi_m < 0) takes the general path
+// (sim_adjoint, per point).  An inactive one has C = 0, so only the leaky slope
+// survives:
 //   dC = -(gf.n)/w_n - mu (gf.t)/w_t   (kinetic branch, sigma > mu C = 0),
 //   dphi_m = -alpha dC,
 // with gf = Gl_m + Ga_m x d_m, d_m = p - s c e_k, t = s tau_k.  Every term is
 // expanded around quantities shared by the simulations of the point:
 //   d x n   = U - s c E_k,      U = p x n,     E_k = e_k x n,  |E_k|^2 = n_i^2 + n_j^2
 //   d x tau = T_k - s c F_k,    T_k = p x tau_k, F_k = e_k x tau_k
-// so that each inactive simulation costs a few dot products.  G4 holds
-// (Gl_m, 0), (Ga_m, 0) for m = 0..6.
-// Constants of the simulation adjoint for one candidate step, kept in shared
-// memory: K[0] = (1/m, 1/I, c = dt V, c^2), K[1] = (2 c / I, mu, alpha, alpha c),
-// K[2] = (w_pen, 0, 0, 0).
-__device__ __forceinline__ void sim_constants(const ParamsDev& P, const ObjDev& O, float4 K[3]) {
-  const float c = P.dt * P.V;
-  K[0] = make_float4(O.inv_mass, O.inv_inertia, c, c * c);
-  K[1] = make_float4(2.0f * c * O.inv_inertia, P.mu, P.alpha, P.alpha * c);
-  K[2] = make_float4(P.w_pen, 0.0f, 0.0f, 0.0f);
-}
-
-__device__ __forceinline__ void point_sims_adjoint(const PointState& ps, const float4* __restrict__ G4,
-                                                   const float4* __restrict__ Kp, const ParamsDev& P,
-                                                   const ObjDev& O, float& dphi, float dn[3], float dp[3]) {
-  const float4 K0 = Kp[0], K1 = Kp[1];
-  const float a = K0.x, b = K0.y, c = K0.z, cc = K0.w;
-  const float tbc = K1.x, mu = K1.y, alpha = K1.z, alphac = K1.w;
-  const float* n = ps.n;
-  float U[3];
-  cross3(ps.p, n, U);
-  const float Uu = dot3(U, U);
-  unsigned cmask = 0;
+// so that each inactive simulation costs a few dot products.
+template <class V>
+__device__ __forceinline__ void point_sims_adjoint(const PointStateT<V>& ps, const SimAdjoints& G,
+                                                   const SimConsts& K, const ParamsDev& P, const ObjDev& O,
+                                                   V& dphi, V dn[3], V dp[3]) {
+  constexpr int W = VecTraits<V>::width;
+  const V tag{};
+  const V zero = vsplat<V>(0.0f);
+  const V* n = ps.n;
+  V U[3];
+  vcross(ps.p, n, U);
+  const V Uu = vdot(U, U);
+  unsigned cmask[W];
+#pragma unroll
+  for (int l = 0; l < W; ++l) cmask[l] = 0u;
   {  // m = 0: v = 0, d = p, no tangential displacement
-    const bool kap = ps.phi_hat < 0.0f;
-    cmask |= kap ? 1u : 0u;
-    const float4 gl = G4[0], ga = G4[1];
-    const float gfn = gl.x * n[0] + gl.y * n[1] + gl.z * n[2] + ga.x * U[0] + ga.y * U[1] + ga.z * U[2];
-    const float q = gfn * __fdividef(1.0f, a + b * Uu) - Kp[2].x;
-    dphi = fmaf(alpha, kap ? 0.0f : q, dphi);
+    const mask_t<V> kap = vlt(ps.phi_hat, zero);
+#pragma unroll
+    for (int l = 0; l < W; ++l) cmask[l] |= mlane(kap, l) ? 1u : 0u;
+    V gl[3], ga[3];
+    get_sim_adjoint(G, 0, gl, ga);
+    const V gfn = dot6(gl, n, ga, U);
+    const V rw = vmap(vfma(simk(K, tag, kcB), Uu, simk(K, tag, kcA)), rcp_fast);
+    const V q = vfma(gfn, rw, simk(K, tag, kcMWpen));
+    dphi = vfma(simk(K, tag, kcAlpha), vsel(kap, zero, q), dphi);
   }
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const int i = (k + 1) % 3, j = (k + 2) % 3;
-    const float ni = n[i], nj = n[j], nk = n[k];
-    const float rho2 = ni * ni + nj * nj;
-    const float rr = rho2 > 0.0f ? rsqrtf(rho2) : 0.0f;     // tau = 0 when n is parallel to e_k
-    float tau[3];
-    tau[k] = rho2 * rr;
-    const float nkr = -nk * rr;
-    tau[i] = nkr * ni;
-    tau[j] = nkr * nj;
-    float T[3];
-    cross3(ps.p, tau, T);
-    const float UE = U[j] * ni - U[i] * nj;            // U . E_k
-    const float TF = T[j] * tau[i] - T[i] * tau[j];    // T_k . F_k
-    const float Fsq = tau[i] * tau[i] + tau[j] * tau[j];
-    const float wn0 = a + b * fmaf(cc, rho2, Uu), wn1 = tbc * UE;
-    const float wt0 = a + b * fmaf(cc, Fsq, dot3(T, T)), wt1 = tbc * TF;
+    const V ni = n[i], nj = n[j], nk = n[k];
+    const V rho2 = vfma(ni, ni, vmul(nj, nj));
+    const V rr = vmap(rho2, rsqrt_or_zero);          // tau = 0 when n is parallel to e_k
+    V tau[3];
+    tau[k] = vmul(rho2, rr);
+    const V nkr = vsub(zero, vmul(nk, rr));
+    tau[i] = vmul(nkr, ni);
+    tau[j] = vmul(nkr, nj);
+    V T[3];
+    vcross(ps.p, tau, T);
+    const V UE = vsub(vmul(U[j], ni), vmul(U[i], nj));            // U . E_k
+    const V TF = vsub(vmul(T[j], tau[i]), vmul(T[i], tau[j]));    // T_k . F_k
+    const V Fsq = vfma(tau[i], tau[i], vmul(tau[j], tau[j]));
+    const V a = simk(K, tag, kcA), b = simk(K, tag, kcB), cc = simk(K, tag, kcCC), tbc = simk(K, tag, kcTBC);
+    const V wn0 = vfma(b, vfma(cc, rho2, Uu), a), wn1 = vmul(tbc, UE);
+    const V wt0 = vfma(b, vfma(cc, Fsq, vdot(T, T)), a), wt1 = vmul(tbc, TF);
     // per-axis parts of the dot products shared by the two signs
-    float gdn[2], gdt[2];
+    V gdn[2], gdt[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int m = 1 + 2 * k + h;
-      const float4 gl = G4[2 * m], ga = G4[2 * m + 1];
-      const float sc = h == 0 ? c : -c;
-      const float gaE = f4c(ga, j) * ni - f4c(ga, i) * nj;
-      const float gaF = f4c(ga, j) * tau[i] - f4c(ga, i) * tau[j];
-      gdn[h] = fmaf(-sc, gaE, gl.x * n[0] + gl.y * n[1] + gl.z * n[2] + ga.x * U[0] + ga.y * U[1] + ga.z * U[2]);
-      gdt[h] = fmaf(-sc, gaF, gl.x * tau[0] + gl.y * tau[1] + gl.z * tau[2] + ga.x * T[0] + ga.y * T[1] +
-                                  ga.z * T[2]);
+      V gl[3], ga[3];
+      get_sim_adjoint(G, m, gl, ga);
+      const V msc = simk(K, tag, h == 0 ? kcMC : kcC);               // -s c
+      const V gaE = vsub(vmul(ga[j], ni), vmul(ga[i], nj));
+      const V gaF = vsub(vmul(ga[j], tau[i]), vmul(ga[i], tau[j]));
+      gdn[h] = vfma(msc, gaE, dot6(gl, n, ga, U));
+      gdt[h] = vfma(msc, gaF, dot6(gl, tau, ga, T));
     }
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int m = 1 + 2 * k + h;
-      const bool kap = sim_phi(ps, m, c) < 0.0f;
-      cmask |= kap ? (1u << m) : 0u;
+      const mask_t<V> kap = vlt(sim_phi(ps, m, P.dt * P.V), zero);
+#pragma unroll
+      for (int l = 0; l < W; ++l) cmask[l] |= mlane(kap, l) ? (1u << m) : 0u;
       // dph = -alpha dC,  dC = -(gf.n)/w_n - mu s (gf.tau)/w_t,  w = w0 - s w1
-      const float rwn = __fdividef(1.0f, h == 0 ? wn0 - wn1 : wn0 + wn1);
-      const float rwt = __fdividef(1.0f, h == 0 ? wt0 - wt1 : wt0 + wt1);
-      const float q = fmaf(h == 0 ? mu : -mu, gdt[h] * rwt, gdn[h] * rwn);
-      const float qa = kap ? 0.0f : q;
-      dphi = fmaf(alpha, qa, dphi);
-      dn[k] = fmaf(h == 0 ? -alphac : alphac, qa, dn[k]);
+      const V rwn = vmap(h == 0 ? vsub(wn0, wn1) : vadd(wn0, wn1), rcp_fast);
+      const V rwt = vmap(h == 0 ? vsub(wt0, wt1) : vadd(wt0, wt1), rcp_fast);
+      const V q = vfma(simk(K, tag, h == 0 ? kcMu : kcMMu), vmul(gdt[h], rwt), vmul(gdn[h], rwn));
+      const V qa = vsel(kap, zero, q);
+      dphi = vfma(simk(K, tag, kcAlpha), qa, dphi);
+      dn[k] = vfma(simk(K, tag, h == 0 ? kcMAlphaC : kcAlphaC), qa, dn[k]);
     }
   }
   // simulations in which some lane of the warp is in contact: general adjoint,
-  // one instance, visiting only those simulations
-  unsigned wmask = __reduce_or_sync(0xffffffffu, cmask);
+  // one instance per point, visiting only those simulations
+  unsigned any = 0u;
+#pragma unroll
+  for (int l = 0; l < W; ++l) any |= cmask[l];
+  unsigned wmask = __reduce_or_sync(0xffffffffu, any);
+  const float c = P.dt * P.V;
   while (wmask) {
     const int m = __ffs(wmask) - 1;
     wmask &= wmask - 1u;
-    if ((cmask >> m) & 1u) {
-      const float4 gl = G4[2 * m], ga = G4[2 * m + 1];
-      const float Gl[3] = {gl.x, gl.y, gl.z}, Ga[3] = {ga.x, ga.y, ga.z};
-      sim_adjoint(ps, m, sim_phi(ps, m, c), true, Gl, Ga, P, O, m == 0 ? P.w_pen : 0.0f, dphi, dn, dp);
+    float Gl[3], Ga[3];
+    get_sim_adjoint(G, m, Gl, Ga);
+    if constexpr (W == 1) {
+      if ((cmask[0] >> m) & 1u)
+        sim_adjoint(ps, m, sim_phi(ps, m, c), true, Gl, Ga, P, O, m == 0 ? P.w_pen : 0.0f, dphi, dn, dp);
+    } else {
+#pragma unroll 1
+      for (int l = 0; l < W; ++l) {
+        if ((cmask[l] >> m) & 1u) {
+          const PointState s1 = point_lane(ps, l);
+          float dph1 = 0.0f, dn1[3] = {0.0f, 0.0f, 0.0f}, dp1[3] = {0.0f, 0.0f, 0.0f};
+          sim_adjoint(s1, m, sim_phi(s1, m, c), true, Gl, Ga, P, O, m == 0 ? P.w_pen : 0.0f, dph1, dn1, dp1);
+          vlane_add(dphi, l, dph1);
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            vlane_add(dn[k], l, dn1[k]);
+            vlane_add(dp[k], l, dp1[k]);
+          }
+        }
+      }
     }
   }
 }
@@ -631,26 +756,27 @@ __device__ __forceinline__ void point_sims_adjoint(const PointState& ps, const f
 // direct dL/dp, returns the total dL/dp.  n = g/|g|, g = grad phi(p), and the
 // Hessian of phi is the trilinear mixed part plus, outside the grid, the
 // curvature (I - eh eh^T)/e of the excess distance on the clamped axes.
-__device__ __forceinline__ void sdf_adjoint(const SdfSample& s, const PointState& ps, float d_phi_hat,
-                                            const float dn[3], float dp[3]) {
-  float ndn = dot3(ps.n, dn);
-  float dg[3];
+template <class V>
+__device__ __forceinline__ void sdf_adjoint(const SdfSampleT<V>& s, const PointStateT<V>& ps, V d_phi_hat,
+                                            const V dn[3], V dp[3]) {
+  const V ndn = vdot(ps.n, dn);
+  V dg[3];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) dg[k] = (dn[k] - ndn * ps.n[k]) * ps.rg;
-  dp[0] += d_phi_hat * s.g[0] + s.hxy * dg[1] + s.hxz * dg[2];
-  dp[1] += d_phi_hat * s.g[1] + s.hxy * dg[0] + s.hyz * dg[2];
-  dp[2] += d_phi_hat * s.g[2] + s.hxz * dg[0] + s.hyz * dg[1];
-  if (s.outside) {
-    // eh is zero on unclamped axes, so (I - eh eh^T) restricted to clamped axes
-    // is D_c - eh eh^T with D_c the clamped-axis mask (eh_k != 0 or clamped).
-    float re = __fdividef(1.0f, s.e);
-    float ehdg = dot3(s.eh, dg);
-    // clamped mask: an axis is clamped iff its trilinear slope was removed; the
-    // excess direction is nonzero exactly on clamped axes (u - u_c != 0).
+  for (int k = 0; k < 3; ++k) dg[k] = vmul(vsub(dn[k], vmul(ndn, ps.n[k])), ps.rg);
+  dp[0] = vadd(dp[0], vfma(d_phi_hat, s.g[0], vfma(s.hxy, dg[1], vmul(s.hxz, dg[2]))));
+  dp[1] = vadd(dp[1], vfma(d_phi_hat, s.g[1], vfma(s.hxy, dg[0], vmul(s.hyz, dg[2]))));
+  dp[2] = vadd(dp[2], vfma(d_phi_hat, s.g[2], vfma(s.hxz, dg[0], vmul(s.hyz, dg[1]))));
+  if (many(s.outside)) {
+    // eh is zero on unclamped axes (and for points inside the grid, where e = 0
+    // and the term vanishes), so (I - eh eh^T) restricted to clamped axes is
+    // D_c - eh eh^T with D_c the mask of axes where eh != 0.
+    const V zero = vsplat<V>(0.0f), one = vsplat<V>(1.0f);
+    const V re = vmap(s.e, rcp_or_zero);
+    const V ehdg = vdot(s.eh, dg);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
-      float ck = (s.eh[k] != 0.0f) ? 1.0f : 0.0f;
-      dp[k] += (ck * dg[k] - s.eh[k] * ehdg) * re;
+      const V ck = vsel(vne(s.eh[k], zero), one, zero);
+      dp[k] = vadd(dp[k], vmul(vsub(vmul(ck, dg[k]), vmul(s.eh[k], ehdg)), re));
     }
   }
 }

@@ -29,21 +29,27 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
+// Work units whose adjoint sums fit in shared memory (hands up to ~12,000 points);
+// larger hands use fixed per-warp point ranges.
+constexpr int kMaxUnits = 192;
+
 template <int NW>
 struct FusedSmem {
   HandDev H;
   ObjDev O;
   float4 frame4[kMaxLinks][3];     // rows (R_r0, R_r1, R_r2, o_r) of each link frame
-  float4 G4[kSims][2];             // (dL/dW_lin, 0), (dL/dW_ang, 0) per simulation
-  float4 K[3];                     // constants of the simulation adjoint
+  SimAdjoints G;                   // dL/dW_lin, dL/dW_ang per simulation (scalar and packed)
+  SimConsts K;                     // constants of the simulation adjoint
   float q[64];
   float grad[64];
   float wred[NW][kSims][8];        // per warp: W (6), N, pen
-  float lacc[NW][kMaxLinks][6];    // per warp, per link: sum g, sum (p - t) x g
+  float lacc[NW][kMaxLinks][6];    // per warp, per link: sum g, sum (p - t) x g (fixed ranges)
+  float uacc[kMaxUnits][6];        // per work unit: sum g, sum (p - t) x g
   float Wtot[kSims][8];
   float loss;
   int bad_object;
   int n_active;
+  int next_unit;                   // adjoint sweep: next unclaimed work unit
   unsigned active_bits[kMaxCullChunks / 32];
   unsigned short active_list[kMaxCullChunks];
   // source of the current candidate (the call's arguments, or a queue slot)
@@ -54,13 +60,6 @@ struct FusedSmem {
   float* lout;
   int cl, step0, total, nsteps;
 };
-
-// Point range of warp w: contiguous, 32-aligned chunks.
-__device__ __forceinline__ void warp_range(int P, int NW, int w, int& b, int& e) {
-  int chunk = ((P + 32 * NW - 1) / (32 * NW)) * 32;
-  b = w * chunk;
-  e = min(P, b + chunk);
-}
 
 __device__ __forceinline__ void store_frame(const Frame& F, float4* f4) {
   f4[0] = make_float4(F.R[0], F.R[1], F.R[2], F.o[0]);
@@ -102,9 +101,8 @@ __device__ __forceinline__ void world_point(const float4* f4, const float4& sp, 
 
 // Adjoint of one hand point (index i, link frames in smem): dL/dp through the 7
 // simulations, the normal and the SDF lookup.  v = (g, (p - t0) x g).
-__device__ __forceinline__ void point_adjoint(const HandDev& H, const float4 (*frame4)[3],
-                                              const float4* __restrict__ G4, const float4* __restrict__ K,
-                                              const ObjDev& O,
+__device__ __forceinline__ void point_adjoint(const HandDev& H, const float4 (*frame4)[3], const SimAdjoints& G,
+                                              const SimConsts& K, const ObjDev& O,
                                               const ParamsDev& Pm, float r, const float t0[3], int i, bool valid,
                                               float v[6], int& link) {
   const float4 sp = __ldg(H.pts + i);
@@ -116,7 +114,7 @@ __device__ __forceinline__ void point_adjoint(const HandDev& H, const float4 (*f
   PointState ps;
   point_state(smp, p, r, ps);
   float dphi = 0.0f, dn[3] = {0.0f, 0.0f, 0.0f}, dp[3] = {0.0f, 0.0f, 0.0f};
-  point_sims_adjoint(ps, G4, K, Pm, O, dphi, dn, dp);
+  point_sims_adjoint(ps, G, K, Pm, O, dphi, dn, dp);
   sdf_adjoint(smp, ps, dphi, dn, dp);
   if (valid) {
     const float rel[3] = {p[0] - t0[0], p[1] - t0[1], p[2] - t0[2]};
@@ -128,6 +126,74 @@ __device__ __forceinline__ void point_adjoint(const HandDev& H, const float4 (*f
 #pragma unroll
     for (int k = 0; k < 6; ++k) v[k] = 0.0f;
   }
+}
+
+// The same for two points (a, b) at once, in packed f32x2 arithmetic: positions
+// and grid indices per point, everything after the corner gathers on pairs.
+__device__ __forceinline__ void point_adjoint_pair(const HandDev& H, const float4 (*frame4)[3], const SimAdjoints& G,
+                                                   const SimConsts& K, const ObjDev& O, const ParamsDev& Pm, float r,
+                                                   const float t0[3], int ia, int ib, bool va, bool vb,
+                                                   float v[2][6], int link[2]) {
+  const float4 sa = __ldg(H.pts + ia), sb = __ldg(H.pts + ib);
+  link[0] = (int)sa.w;
+  link[1] = (int)sb.w;
+  float pa[3], pb[3];
+  world_point(frame4[link[0]], sa, pa);
+  world_point(frame4[link[1]], sb, pb);
+  SdfIndex xa, xb;
+  sdf_index(O, pa, xa);
+  sdf_index(O, pb, xb);
+  float ca[8], cb[8];
+  sdf_gather(O, xa.cell, ca);
+  sdf_gather(O, xb.cell, cb);
+  SdfSampleT<float2> smp;
+  sdf_finish_pair(O, xa, xb, ca, cb, smp);
+  const float2 p[3] = {make_float2(pa[0], pb[0]), make_float2(pa[1], pb[1]), make_float2(pa[2], pb[2])};
+  PointStateT<float2> ps;
+  point_state(smp, p, r, ps);
+  const float2 zero = make_float2(0.0f, 0.0f);
+  float2 dphi = zero, dn[3] = {zero, zero, zero}, dp[3] = {zero, zero, zero};
+  point_sims_adjoint(ps, G, K, Pm, O, dphi, dn, dp);
+  sdf_adjoint(smp, ps, dphi, dn, dp);
+  const float2 rel[3] = {vsub(p[0], vsplat<float2>(t0[0])), vsub(p[1], vsplat<float2>(t0[1])),
+                         vsub(p[2], vsplat<float2>(t0[2]))};
+  float2 tq[3];
+  vcross(rel, dp, tq);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    v[0][k] = va ? dp[k].x : 0.0f;
+    v[1][k] = vb ? dp[k].y : 0.0f;
+    v[0][3 + k] = va ? tq[k].x : 0.0f;
+    v[1][3 + k] = vb ? tq[k].y : 0.0f;
+  }
+}
+
+// Sums a[0..5] over the 32 lanes in a fixed pattern and stores the 6 totals in
+// slot.  Eight values (6 and two zeros) are halved across lanes at each exchange
+// (xor 16, 8, 4: a lane keeps half of its values and adds its partner's copy of
+// them), then the last value is summed over groups of 4; lane 4k ends with the
+// total of value k.  The order of additions never depends on timing.
+__device__ __forceinline__ void unit_reduce_store(const float a[6], int lane, float* slot) {
+  const float v[8] = {a[0], a[1], a[2], a[3], a[4], a[5], 0.0f, 0.0f};
+  const bool h16 = (lane & 16) != 0, h8 = (lane & 8) != 0, h4 = (lane & 4) != 0;
+  float w4[4], w2[2];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float send = h16 ? v[j] : v[4 + j];
+    const float keep = h16 ? v[4 + j] : v[j];
+    w4[j] = keep + __shfl_xor_sync(kFull, send, 16);
+  }
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const float send = h8 ? w4[j] : w4[2 + j];
+    const float keep = h8 ? w4[2 + j] : w4[j];
+    w2[j] = keep + __shfl_xor_sync(kFull, send, 8);
+  }
+  float w = (h4 ? w2[1] : w2[0]) + __shfl_xor_sync(kFull, h4 ? w2[0] : w2[1], 4);
+  w += __shfl_xor_sync(kFull, w, 2);
+  w += __shfl_xor_sync(kFull, w, 1);
+  const int k = lane >> 2;
+  if ((lane & 3) == 0 && k < 6) slot[k] = w;
 }
 
 // Adds 32 points' (g, r x g) to the warp's per-link sums.  Runs of points of one
@@ -223,8 +289,6 @@ __global__ void __launch_bounds__(NW * 32, MINB) fused_step_kernel(FusedArgs a) 
     }
     const int D = H.D, P = H.P, L = H.L;
     const float dtV = Pm.dt * Pm.V;
-    int pb, pe;
-    warp_range(P, NW, warp, pb, pe);
     const int nwords = (P + 31) >> 5;
     const int cl = S.cl;
     if (tid < D) S.q[tid] = S.qout[(size_t)cl * D + tid];
@@ -393,8 +457,9 @@ __global__ void __launch_bounds__(NW * 32, MINB) fused_step_kernel(FusedArgs a) 
             Lpart = nx + nt;
             const float ax = nx > 0.0f ? sl / (kSims * nx) : 0.0f;
             const float at = nt > 0.0f ? sa / (kSims * nt) : 0.0f;
-            S.G4[m][0] = make_float4(xd[0] * ax, xd[1] * ax, xd[2] * ax, 0.0f);
-            S.G4[m][1] = make_float4(td[0] * at, td[1] * at, td[2] * at, 0.0f);
+            const float gl[3] = {xd[0] * ax, xd[1] * ax, xd[2] * ax};
+            const float ga[3] = {td[0] * at, td[1] * at, td[2] * at};
+            set_sim_adjoint(S.G, m, gl, ga);
           }
           float dj = 0.0f, d2 = 0.0f, lim = 0.0f, th = 0.0f;
           if (lane < H.J) {
@@ -417,6 +482,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) fused_step_kernel(FusedArgs a) 
         }
       }
       for (int idx = tid; idx < NW * kMaxLinks * 6; idx += NW * 32) (&S.lacc[0][0][0])[idx] = 0.0f;
+      if (tid == 0) S.next_unit = 0;
       __syncthreads();
       if (MODE == kModeLossGrad && a.grad == nullptr) {    // loss only: no adjoint
         if (tid == 0) a.loss[c] = S.loss;
@@ -436,20 +502,58 @@ __global__ void __launch_bounds__(NW * 32, MINB) fused_step_kernel(FusedArgs a) 
         const float t0[3] = {S.q[0], S.q[1], S.q[2]};
         int cur = -1;
         float acc[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-        for (int base = pb; base < pe; base += 32 * PPT) {
-          float v[PPT][6];
-          int link[PPT];
-          bool valid[PPT];
+        if (H.nunits <= kMaxUnits) {
+          // Warps claim work units (<= 64 points of one link) from a shared
+          // counter, so a warp that meets contacts (general adjoint) does not hold
+          // the others at the barrier; each unit's sums go to its own slot, so the
+          // result does not depend on which warp ran it.  The next claim is issued
+          // before the current unit so that its latency is hidden.
+          auto claim = [&]() {
+            int j = 0;
+            if (lane == 0) j = atomicAdd(&S.next_unit, 1);
+            return __shfl_sync(kFull, j, 0);
+          };
+          int u = claim();
+          while (u < H.nunits) {
+            const int nu = claim();
+            const int4 U = __ldg(H.units + u);      // first point, count, link
+            float sum[6];
+            if (PPT == 2) {
+              // one point of each half of the unit per lane, packed arithmetic
+              float v[2][6];
+              int link[2];
+              const bool va = lane < U.y, vb = lane + 32 < U.y;
+              point_adjoint_pair(H, S.frame4, S.G, S.K, O, Pm, r, t0, va ? U.x + lane : U.x,
+                                 vb ? U.x + 32 + lane : U.x, va, vb, v, link);
 #pragma unroll
-          for (int u = 0; u < PPT; ++u) {
-            const int bb = base + 32 * u;
-            const int i = bb + lane;
-            valid[u] = i < pe;
-            point_adjoint(H, S.frame4, &S.G4[0][0], S.K, O, Pm, r, t0, valid[u] ? i : base, valid[u], v[u], link[u]);
+              for (int k = 0; k < 6; ++k) sum[k] = v[0][k] + v[1][k];
+            } else {
+#pragma unroll
+              for (int k = 0; k < 6; ++k) sum[k] = 0.0f;
+              for (int h = 0; h < U.y; h += 32) {
+                float v[6];
+                int link;
+                const bool valid = h + lane < U.y;
+                point_adjoint(H, S.frame4, S.G, S.K, O, Pm, r, t0, valid ? U.x + h + lane : U.x, valid, v, link);
+#pragma unroll
+                for (int k = 0; k < 6; ++k) sum[k] += v[k];
+              }
+            }
+            unit_reduce_store(sum, lane, S.uacc[u]);
+            u = nu;
           }
-#pragma unroll
-          for (int u = 0; u < PPT; ++u)
-            if (base + 32 * u < pe) link_accumulate(S.lacc[warp], lane, link[u], valid[u], v[u], cur, acc);
+        } else {
+          // fixed, contiguous 32-aligned point ranges per warp
+          const int span = ((P + 32 * NW - 1) / (32 * NW)) * 32;
+          const int pb = warp * span, pe = min(P, pb + span);
+          for (int base = pb; base < pe; base += 32) {
+            float v[6];
+            int link;
+            const int i = base + lane;
+            const bool valid = i < pe;
+            point_adjoint(H, S.frame4, S.G, S.K, O, Pm, r, t0, valid ? i : base, valid, v, link);
+            link_accumulate(S.lacc[warp], lane, link, valid, v, cur, acc);
+          }
         }
         if (cur >= 0) {
 #pragma unroll
@@ -469,8 +573,12 @@ __global__ void __launch_bounds__(NW * 32, MINB) fused_step_kernel(FusedArgs a) 
         for (int k = 0; k < 6; ++k) {
           float x = 0.0f;
           if (lane < L) {
+            if (H.nunits <= kMaxUnits) {
+              for (int u = H.unit_begin[lane]; u < H.unit_begin[lane + 1]; ++u) x += S.uacc[u][k];
+            } else {
 #pragma unroll
-            for (int w = 0; w < NW; ++w) x += S.lacc[w][lane][k];
+              for (int w = 0; w < NW; ++w) x += S.lacc[w][lane][k];
+            }
           }
 #pragma unroll
           for (int o = 1; o < 32; o <<= 1) {
@@ -552,6 +660,6 @@ cudaError_t launch_fused_cfg(const FusedArgs& a, cudaStream_t st) {
 // warps per candidate, the minimum resident CTAs per SM the register
 // allocation is held to, and points per thread in the adjoint sweep.  The autotuner times them on a workload.
 // (warps per candidate, min CTAs per SM, points per thread per adjoint iteration)
-#define FG_FUSED_CONFIGS(X) X(4, 4, 1) X(4, 5, 1) X(4, 6, 1) X(4, 8, 1) X(8, 3, 1) X(2, 8, 1)
+#define FG_FUSED_CONFIGS(X) X(4, 4, 1) X(4, 5, 1) X(4, 6, 1) X(4, 8, 1) X(8, 3, 1) X(2, 8, 1) X(4, 3, 2) X(4, 4, 2) X(4, 5, 2) X(8, 2, 2)
 
 }  // namespace fg

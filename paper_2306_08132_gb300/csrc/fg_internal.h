@@ -14,6 +14,7 @@ struct fg_hand {
   float4* pts;               // device [P]
   float4* chunk_sphere;      // device [nchunks]
   int* chunk_link;           // device [nchunks]
+  int4* units;               // device [nunits]
   int subtree_end[FG_MAX_LINKS];
 };
 
