@@ -231,7 +231,13 @@ __device__ __forceinline__ void sdf_gather(const ObjDev& O, const float* G, floa
 
 __device__ __forceinline__ float rsqrt_or_zero(float x) { return x > 0.0f ? rsqrtf(x) : 0.0f; }
 __device__ __forceinline__ float rcp_or_zero(float x) { return x > 0.0f ? __fdividef(1.0f, x) : 0.0f; }
-__device__ __forceinline__ float rcp_fast(float x) { return __fdividef(1.0f, x); }
+// Reciprocal of a positive, normal float (the effective inverse masses w_n, w_t
+// >= 1/m of the simulation adjoint): the hardware approximation, one instruction.
+__device__ __forceinline__ float rcp_fast(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 
 // Value, gradient and (kHess) mixed second derivatives from the fractions f, the
 // excess du = u - u_c, the clamp flags and the corners
@@ -629,10 +635,11 @@ __device__ __forceinline__ void get_sim_adjoint(const SimAdjoints& G, int m, flo
   ga[1] = make_float2(c.x, c.y); ga[2] = make_float2(c.z, c.w);
 }
 
-// gl . a + ga . b
+// gl . a + ga . b, as two independent 3-term chains (shorter dependency path)
 template <class V>
 __device__ __forceinline__ V dot6(const V gl[3], const V a[3], const V ga[3], const V b[3]) {
-  return vfma(gl[0], a[0], vfma(gl[1], a[1], vfma(gl[2], a[2], vfma(ga[0], b[0], vfma(ga[1], b[1], vmul(ga[2], b[2]))))));
+  return vadd(vfma(gl[0], a[0], vfma(gl[1], a[1], vmul(gl[2], a[2]))),
+              vfma(ga[0], b[0], vfma(ga[1], b[1], vmul(ga[2], b[2]))));
 }
 
 // Adjoint of all 7 simulations at one point (V = float) or two points (float2).
@@ -679,13 +686,13 @@ __device__ __forceinline__ void point_sims_adjoint(const PointStateT<V>& ps, con
     const V rr = vmap(rho2, rsqrt_or_zero);          // tau = 0 when n is parallel to e_k
     V tau[3];
     tau[k] = vmul(rho2, rr);
-    const V nkr = vsub(zero, vmul(nk, rr));
+    const V nkr = vnmul(nk, rr);
     tau[i] = vmul(nkr, ni);
     tau[j] = vmul(nkr, nj);
     V T[3];
     vcross(ps.p, tau, T);
-    const V UE = vsub(vmul(U[j], ni), vmul(U[i], nj));            // U . E_k
-    const V TF = vsub(vmul(T[j], tau[i]), vmul(T[i], tau[j]));    // T_k . F_k
+    const V UE = vdiff(U[j], ni, U[i], nj);            // U . E_k
+    const V TF = vdiff(T[j], tau[i], T[i], tau[j]);    // T_k . F_k
     const V Fsq = vfma(tau[i], tau[i], vmul(tau[j], tau[j]));
     const V a = simk(K, tag, kcA), b = simk(K, tag, kcB), cc = simk(K, tag, kcCC), tbc = simk(K, tag, kcTBC);
     const V wn0 = vfma(b, vfma(cc, rho2, Uu), a), wn1 = vmul(tbc, UE);
@@ -698,8 +705,8 @@ __device__ __forceinline__ void point_sims_adjoint(const PointStateT<V>& ps, con
       V gl[3], ga[3];
       get_sim_adjoint(G, m, gl, ga);
       const V msc = simk(K, tag, h == 0 ? kcMC : kcC);               // -s c
-      const V gaE = vsub(vmul(ga[j], ni), vmul(ga[i], nj));
-      const V gaF = vsub(vmul(ga[j], tau[i]), vmul(ga[i], tau[j]));
+      const V gaE = vdiff(ga[j], ni, ga[i], nj);
+      const V gaF = vdiff(ga[j], tau[i], ga[i], tau[j]);
       gdn[h] = vfma(msc, gaE, dot6(gl, n, ga, U));
       gdt[h] = vfma(msc, gaF, dot6(gl, tau, ga, T));
     }
@@ -762,7 +769,7 @@ __device__ __forceinline__ void sdf_adjoint(const SdfSampleT<V>& s, const PointS
   const V ndn = vdot(ps.n, dn);
   V dg[3];
 #pragma unroll
-  for (int k = 0; k < 3; ++k) dg[k] = vmul(vsub(dn[k], vmul(ndn, ps.n[k])), ps.rg);
+  for (int k = 0; k < 3; ++k) dg[k] = vmul(vfnma(ndn, ps.n[k], dn[k]), ps.rg);
   dp[0] = vadd(dp[0], vfma(d_phi_hat, s.g[0], vfma(s.hxy, dg[1], vmul(s.hxz, dg[2]))));
   dp[1] = vadd(dp[1], vfma(d_phi_hat, s.g[1], vfma(s.hxy, dg[0], vmul(s.hyz, dg[2]))));
   dp[2] = vadd(dp[2], vfma(d_phi_hat, s.g[2], vfma(s.hxz, dg[0], vmul(s.hyz, dg[1]))));
@@ -776,7 +783,7 @@ __device__ __forceinline__ void sdf_adjoint(const SdfSampleT<V>& s, const PointS
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       const V ck = vsel(vne(s.eh[k], zero), one, zero);
-      dp[k] = vadd(dp[k], vmul(vsub(vmul(ck, dg[k]), vmul(s.eh[k], ehdg)), re));
+      dp[k] = vfma(vfnma(s.eh[k], ehdg, vmul(ck, dg[k])), re, dp[k]);
     }
   }
 }

@@ -47,15 +47,22 @@ __device__ __forceinline__ float2 vadd(float2 a, float2 b) { return __fadd2_rn(a
 // a - b as one rounding of a + (-1) b: the same bits as a subtraction
 __device__ __forceinline__ float2 vsub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
 
+// c - a b (scalar: one fused multiply-add with a negated operand)
+__device__ __forceinline__ float vfnma(float a, float b, float c) { return __fmaf_rn(-a, b, c); }
+__device__ __forceinline__ float2 vfnma(float2 a, float2 b, float2 c) { return vsub(c, vmul(a, b)); }
+// a b - c d (not used for decisions)
+__device__ __forceinline__ float vdiff(float a, float b, float c, float d) { return __fmaf_rn(a, b, -__fmul_rn(c, d)); }
+__device__ __forceinline__ float2 vdiff(float2 a, float2 b, float2 c, float2 d) { return vsub(vmul(a, b), vmul(c, d)); }
+// -(a b)
+__device__ __forceinline__ float vnmul(float a, float b) { return -__fmul_rn(a, b); }
+__device__ __forceinline__ float2 vnmul(float2 a, float2 b) { return vmul(vmul(a, b), make_float2(-1.0f, -1.0f)); }
+
 template <class V>
 __device__ __forceinline__ V vsplat(float x);
 template <>
 __device__ __forceinline__ float vsplat<float>(float x) { return x; }
 template <>
 __device__ __forceinline__ float2 vsplat<float2>(float x) { return make_float2(x, x); }
-
-__device__ __forceinline__ float vpack(float a, float) { return a; }
-__device__ __forceinline__ float2 vpack2(float a, float b) { return make_float2(a, b); }
 
 // component k (0 or 1) of a lane vector
 __device__ __forceinline__ float vlane(float v, int) { return v; }
@@ -106,9 +113,9 @@ __device__ __forceinline__ void vcross(const float a[3], const float b[3], float
   c[2] = __fmaf_rn(a[0], b[1], -__fmul_rn(a[1], b[0]));
 }
 __device__ __forceinline__ void vcross(const float2 a[3], const float2 b[3], float2 c[3]) {
-  c[0] = vsub(vmul(a[1], b[2]), vmul(a[2], b[1]));
-  c[1] = vsub(vmul(a[2], b[0]), vmul(a[0], b[2]));
-  c[2] = vsub(vmul(a[0], b[1]), vmul(a[1], b[0]));
+  c[0] = vdiff(a[1], b[2], a[2], b[1]);
+  c[1] = vdiff(a[2], b[0], a[0], b[2]);
+  c[2] = vdiff(a[0], b[1], a[1], b[0]);
 }
 template <class V>
 __device__ __forceinline__ V vdot(const V a[3], const V b[3]) {
