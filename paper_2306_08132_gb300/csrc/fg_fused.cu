@@ -15,7 +15,7 @@ static const int kCfgMinB[] = {FG_FUSED_CONFIGS(FG_CFG_MB)};
 static const int kCfgPPT[] = {FG_FUSED_CONFIGS(FG_CFG_PPT)};
 static const FusedLaunchFn kLossGradLaunch[] = {FG_FUSED_CONFIGS(FG_CFG_LOSSGRAD)};
 constexpr int kNumCfg = sizeof(kCfgNW) / sizeof(kCfgNW[0]);
-constexpr int kDefaultCfg = 2;   // 4 warps per candidate, >= 6 CTAs per SM, 1 point per thread
+constexpr int kDefaultCfg = 1;   // 4 warps per candidate, >= 5 CTAs per SM, 1 point per thread
 
 static int g_selected[64] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1,
                              -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1, -1,
@@ -44,7 +44,7 @@ cudaError_t launch_fused(int mode, const FusedArgs& a, const fg_hand* h, cudaStr
   if (a.B <= 0) return cudaSuccess;
   const int cfg = fused_config_current();
   switch (mode) {
-    case kModeWrench: return launch_fused_cfg<kModeWrench, 4, 6, 1>(a, st);
+    case kModeWrench: return launch_fused_cfg<kModeWrench, 4, 5, 1>(a, st);
     case kModeLossGrad: return kLossGradLaunch[cfg](a, st);
     default: return kOptimizeLaunch[cfg](a, st);
   }
@@ -53,7 +53,7 @@ cudaError_t launch_fused(int mode, const FusedArgs& a, const fg_hand* h, cudaStr
 // One round of a request queue: every active request's candidates in one launch.
 cudaError_t launch_queue_round(const FusedArgs& a, cudaStream_t st) {
   if (a.B <= 0) return cudaSuccess;
-  return launch_fused_cfg<kModeQueue, 4, 6, 1>(a, st);
+  return launch_fused_cfg<kModeQueue, 4, 5, 1>(a, st);
 }
 
 cudaError_t autotune_fused(const FusedArgs& base, int reps, float* times_ms, int* best, cudaStream_t st) {

@@ -23,8 +23,8 @@ def fg():
 
 
 def _queue_config_index(fg):
-    """Configuration the queue's kernel uses (4 warps, >= 6 CTAs per SM, 1 point per thread)."""
-    return fg.fused_configs().index((4, 6, 1))
+    """Configuration the queue's kernel uses (4 warps, >= 5 CTAs per SM, 1 point per thread)."""
+    return fg.fused_configs().index((4, 5, 1))
 
 
 @pytest.fixture(scope="module")
