@@ -156,12 +156,14 @@ def oracle_rate(w, budget_s: float, r: float, max_cands: int | None = None):
     return done / dt, done, dt, torch.get_num_threads()
 
 
-def run_serving(fg, n_requests: int, rate_hz: float, device, budget_bytes: int, steps_per_launch: int = 10):
-    """Replays a Poisson stream of grasp-search requests into a request queue in
-    real time and returns latency percentiles and throughput."""
+def run_serving(fg, n_requests: int, rates_hz, device, budget_bytes: int, steps_per_launch: int = 10):
+    """Replays the first n_requests of the seeded Poisson request stream into a
+    request queue in real time, once per arrival rate (the stream's arrival times
+    scaled to the rate), and returns latency percentiles and throughput per rate."""
     import synth
     from synth.workloads import build_request
-    specs = synth.serving_stream(n_requests=n_requests, rate_hz=rate_hz)
+    base_rate = 200.0
+    specs = synth.serving_stream(n_requests=n_requests, rate_hz=base_rate)
     cache = {}
     built = []
     for sp in specs:
@@ -170,28 +172,36 @@ def run_serving(fg, n_requests: int, rate_hz: float, device, budget_bytes: int, 
         if ("h", key) not in cache:
             cache[("h", key)] = fg.Hand.from_synth(hand_d)
         built.append((cache[("h", key)], fg.Sdf.from_synth(obj), q0, params, steps, sp["arrival_s"]))
-    queue = fg.Queue(budget_bytes, steps_per_launch=steps_per_launch)
-    ids, lat = [], []
     cand_steps = sum(b[2].shape[0] * b[4] for b in built)
-    t0 = time.perf_counter()
-    try:
-        for hand, sdf, q0, params, steps, t_arr in built:
-            while time.perf_counter() - t0 < t_arr:
-                time.sleep(0.0005)
-            ids.append(queue.submit(hand, sdf, q0, steps, params))
-        for rid in ids:
-            queue.wait(rid, 600000)
-            lat.append(queue.result(rid)[2])
-        makespan = time.perf_counter() - t0
-        st = queue.stats()
-    finally:
-        queue.close()
-    lat = np.array(lat)
-    return {"requests": n_requests, "arrival_rate_hz": rate_hz, "p50_s": float(np.percentile(lat, 50)),
-            "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()), "makespan_s": makespan,
-            "candidate_steps_per_s": cand_steps / makespan, "rounds": st["rounds"],
-            "steps_per_launch": steps_per_launch,
-            "note": "offered load exceeds capacity at this arrival rate; latency includes queueing"}
+    out = []
+    for rate in rates_hz:
+        scale = base_rate / rate
+        queue = fg.Queue(budget_bytes, steps_per_launch=steps_per_launch)
+        ids, lat = [], []
+        t0 = time.perf_counter()
+        try:
+            for hand, sdf, q0, params, steps, t_arr in built:
+                while time.perf_counter() - t0 < t_arr * scale:
+                    time.sleep(0.0005)
+                ids.append(queue.submit(hand, sdf, q0, steps, params))
+            for rid in ids:
+                queue.wait(rid, 600000)
+                lat.append(queue.result(rid)[2])
+            makespan = time.perf_counter() - t0
+            st = queue.stats()
+        finally:
+            queue.close()
+        lat = np.array(lat)
+        span = max(built[-1][5] * scale, 1e-9)
+        offered = cand_steps / span
+        served = cand_steps / makespan
+        out.append({"requests": n_requests, "arrival_rate_hz": rate, "p50_s": float(np.percentile(lat, 50)),
+                    "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()), "makespan_s": makespan,
+                    "offered_candidate_steps_per_s": offered, "candidate_steps_per_s": served,
+                    "rounds": st["rounds"], "steps_per_launch": steps_per_launch,
+                    "note": ("offered load exceeds capacity: latency includes queueing" if served < 0.9 * offered
+                             else "offered load within capacity")})
+    return out
 
 
 def run_reference(args):
@@ -239,6 +249,8 @@ def main():
     ap.add_argument("--config", type=int, default=None, help="fused configuration index (default: autotune)")
     ap.add_argument("--serving", type=int, default=40, help="requests in the serving (p50/p99) run; 0 skips it")
     ap.add_argument("--serving-rate", type=float, default=200.0)
+    ap.add_argument("--serving-sweep", default="",
+                    help="comma-separated arrival rates (req/s) for a latency-vs-load sweep of the same stream")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -396,16 +408,28 @@ def main():
                 "frac_kernel_min": min_achieved / peak,
                 "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
 
-    serving = None
+    serving, sweep = None, None
     if args.serving > 0:
         free, _ = torch.cuda.mem_get_info()
-        serving = run_serving(fg, args.serving, args.serving_rate, dev, int(0.5 * free))
+        rates = [args.serving_rate] + [float(x) for x in args.serving_sweep.split(",") if x.strip()]
+        runs = run_serving(fg, args.serving, rates, dev, int(0.5 * free))
+        serving, sweep = runs[0], (runs[1:] or None)
 
     if rank == 0:
         r0 = O.dilation_radius(O.Params.from_dict(w.params), 0, K)
         rate, n, dt, cores = oracle_rate(w, args.cpu_budget, r0)
         cpu = {"value": rate, "unit": "candidate-steps/s", "cores": cores, "kind": "oracle",
                "sample": "%d candidates x 1 step of the same workload in %.1f s (FP64, torch CPU)" % (n, dt)}
+        if args.cpu_budget > 0:
+            import torch as _t
+            threads = _t.get_num_threads()
+            _t.set_num_threads(1)
+            try:
+                r1, n1, dt1, _ = oracle_rate(w, args.cpu_budget / 3.0, r0)
+            finally:
+                _t.set_num_threads(threads)
+            cpu["value_1_thread"] = r1
+            cpu["sample_1_thread"] = "%d candidates x 1 step in %.1f s on one thread" % (n1, dt1)
         line = {"metric": METRIC, "value": value, "unit": "candidate-steps/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -420,7 +444,7 @@ def main():
                                                             for c, t in zip(cfgs, cfg_ms)}}},
                 "plain": plain, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
                 "latency": None if serving is None else {"p50_s": serving["p50_s"], "p99_s": serving["p99_s"]},
-                "serving": serving,
+                "serving": serving, "serving_sweep": sweep,
                 "gpu_launches": args.steps * 1, "clocks": clocks, "wall_s_timed_region": wall,
                 "per_step_ms": {"min": float(np.min(ms)), "median": float(np.median(ms)), "max": float(np.max(ms))}}
         print(json.dumps(line))
