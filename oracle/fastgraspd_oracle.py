@@ -99,6 +99,7 @@ class Params:
     w_limit: float = 1.0
     w_pen: float = 0.0
     schedule: str = "fixed"
+    sim_steps: int = 0          # 0: one step, plane-linearised query; T >= 1: T steps, re-queried
 
     @staticmethod
     def from_dict(d: dict) -> "Params":
@@ -342,12 +343,162 @@ def evaluate(hand: Hand, obj: Obj, q: torch.Tensor, r: float, prm: Params,
             "sigma": sig, "dec": dec}
 
 
+@dataclass
+class StepDecisions:
+    """Branches of one simulation step of the T-step form (per point and simulation)."""
+    sdf: dict = None
+    grad_nz: torch.Tensor = None     # [B,P,M]
+    kappa: torch.Tensor = None       # [B,P,M]
+    has_t: torch.Tensor = None       # [B,P,M]
+    static: torch.Tensor = None      # [B,P,M]
+    anchor: torch.Tensor = None      # [B,P,M]
+    ncontact: torch.Tensor = None    # [B,M]
+
+
+@dataclass
+class TStepDecisions:
+    steps: list = field(default_factory=list)
+    v_nz: torch.Tensor = None
+    w_nz: torch.Tensor = None
+    range_nz: torch.Tensor = None
+    above: torch.Tensor = None
+    below: torch.Tensor = None
+
+
+def _joint_losses(hand: Hand, q: torch.Tensor, dec):
+    th = q[:, 6:]
+    mid = 0.5 * (hand.q_up + hand.q_low)
+    if dec.range_nz is None:
+        dec.range_nz = ((th.detach() - mid) ** 2).sum(-1) > 0
+        dec.above = th.detach() > hand.q_up
+        dec.below = th.detach() < hand.q_low
+    L_range = _safe_norm(th - mid, dec.range_nz)                                             # Eq. (3)
+    L_limit = (torch.where(dec.above, th - hand.q_up, torch.zeros_like(th)) +
+               torch.where(dec.below, hand.q_low - th, torch.zeros_like(th))).sum(-1)        # Eq. (4)
+    return L_range, L_limit
+
+
+def evaluate_tstep(hand: Hand, obj: Obj, q: torch.Tensor, r: float, prm: Params, T: int,
+                   dec: TStepDecisions | None = None, anchor_mode: bool = False) -> dict:
+    """The grasp metric with T simulation steps per test velocity (Sec. IV-A: the
+    object's velocity after T steps; the paper's experiments take T = 1).
+
+    Each simulation starts at the canonical pose with velocity V e_m and no spin.
+    One step (Sec. III-C):
+      predict (symplectic Euler, no external force)  x~ = x + dt v,  R~ = Exp(dt w) R;
+      every hand point in the object frame at the predicted pose, r = R~^T (p - x~),
+      re-queried in the SDF: phi_hat = phi(r) - r_dil, world normal n = R~ grad/|grad|;
+      C = max(0, -phi_hat) with the leaky rule; the projection of Eq. (1) with lever
+      d = p - x~; Coulomb friction on the tangential part of the displacement of the
+      object's material point at the contact, s = p - (x + R r);
+      corrections averaged over the N active contacts (Jacobi reading):
+      x+ = x~ + dx,  R+ = Exp(dtheta) R~,  v+ = (x+ - x)/dt,  w+ = w + dtheta/dt.
+    L_stable (Eq. 2) on (v, w) after T steps.  At T = 1 this is the one-step metric
+    with the SDF evaluated at the moved pose instead of on the plane through the
+    query; on a linear field the two coincide."""
+    take = dec is None
+    if take:
+        dec = TStepDecisions()
+    B = q.shape[0]
+    M = M_SIMS
+    Rh, oh = forward_kinematics(hand, q)
+    p = hand_points(hand, Rh, oh)                                     # [B,P,3], the hand is static
+    P = p.shape[1]
+    V = torch.tensor(TEST_DIRECTIONS, dtype=F64) * prm.v_test         # [M,3]
+    x = torch.zeros(B, M, 3, dtype=F64)
+    Rb = torch.eye(3, dtype=F64).expand(B, M, 3, 3)
+    v = V[None].expand(B, M, 3)
+    w = torch.zeros(B, M, 3, dtype=F64)
+    alpha = prm.alpha_leak
+    pe = p[:, :, None, :]                                             # [B,P,1,3]
+    C_first = None
+    trace = []
+    for t in range(T):
+        sd = StepDecisions() if take else dec.steps[t]
+        x_t = x + prm.dt * v                                          # [B,M,3]
+        R_t = so3_exp(prm.dt * w) @ Rb                                # [B,M,3,3]
+        d = pe - x_t[:, None]                                         # [B,P,M,3]
+        rr = (R_t.transpose(-1, -2)[:, None] @ d[..., None])[..., 0]  # object frame
+        if take:
+            sd.sdf = sdf_decisions(obj, rr)
+        phi, g_obj = sdf_eval(obj, rr, sd.sdf)
+        phi_hat = phi - r
+        if take:
+            sd.grad_nz = (g_obj.detach() * g_obj.detach()).sum(-1) > 0
+        gn = _safe_norm(g_obj, sd.grad_nz)
+        n_obj = g_obj / torch.where(sd.grad_nz, gn, torch.ones_like(gn))[..., None]
+        n = (R_t[:, None] @ n_obj[..., None])[..., 0]                 # world normal
+        if take:
+            sd.kappa = phi_hat.detach() < 0
+        if anchor_mode:
+            anchor = sd.anchor
+        else:
+            anchor = phi_hat.detach()
+            if take:
+                sd.anchor = anchor
+        C = torch.where(sd.kappa, -phi_hat, -alpha * (phi_hat - anchor))
+        if t == 0:
+            C_first = C
+        u_n = _cross(d, n)
+        w_n = obj.inv_mass + obj.inv_inertia * _dot(u_n, u_n)
+        lam_n = C / w_n
+        s_raw = pe - x[:, None] - (Rb[:, None] @ rr[..., None])[..., 0]
+        s = s_raw - _dot(s_raw, n)[..., None] * n
+        if take:
+            sd.has_t = (s.detach() * s.detach()).sum(-1) > 0
+        sig = _safe_norm(s, sd.has_t)
+        t_hat = s / torch.where(sd.has_t, sig, torch.ones_like(sig))[..., None]
+        u_t = _cross(d, t_hat)
+        w_t = obj.inv_mass + obj.inv_inertia * _dot(u_t, u_t)
+        if take:
+            sd.static = sig.detach() <= prm.mu * C.detach()
+        lam_t = torch.where(sd.has_t, torch.where(sd.static, sig, prm.mu * C) / w_t, torch.zeros_like(sig))
+        f = -(lam_n[..., None] * n + lam_t[..., None] * t_hat)
+        W_lin = f.sum(1)
+        W_ang = _cross(d, f).sum(1)
+        if t == 0:
+            W_first = torch.cat([W_lin, W_ang], -1)
+        trace.append({"r": rr.detach(), "phi_hat": phi_hat.detach(), "C": C.detach(), "sigma": sig.detach(),
+                      "s_raw": _safe_norm(s_raw.detach(), torch.ones_like(sd.kappa)), "kappa": sd.kappa,
+                      "has_t": sd.has_t})
+        if take:
+            sd.ncontact = sd.kappa.sum(1).to(F64)
+        Nc = torch.clamp(sd.ncontact, min=1.0)
+        dx = W_lin * obj.inv_mass / Nc[..., None]
+        dth = W_ang * obj.inv_inertia / Nc[..., None]
+        x_new = x_t + dx
+        R_new = so3_exp(dth) @ R_t
+        v = (x_new - x) / prm.dt
+        w = w + dth / prm.dt
+        x, Rb = x_new, R_new
+        if take:
+            dec.steps.append(sd)
+    if take:
+        dec.v_nz = (v.detach() ** 2).sum(-1) > 0
+        dec.w_nz = (w.detach() ** 2).sum(-1) > 0
+    L_stable = (_safe_norm(v, dec.v_nz) + _safe_norm(w, dec.w_nz)).sum(-1) / M_SIMS       # Eq. (2)
+    L_range, L_limit = _joint_losses(hand, q, dec)
+    L_pen = C_first[..., 0].sum(-1)
+    L = L_stable + prm.w_range * L_range + prm.w_limit * L_limit + prm.w_pen * L_pen
+    return {"L": L, "L_stable": L_stable, "L_range": L_range, "L_limit": L_limit, "L_pen": L_pen,
+            "xdot": v, "thdot": w, "W": W_first, "N": dec.steps[0].ncontact, "kappa": dec.steps[0].kappa,
+            "points": p, "dec": dec, "trace": trace}
+
+
+def evaluate_any(hand: Hand, obj: Obj, q: torch.Tensor, r: float, prm: Params, dec=None,
+                 anchor_mode: bool = False) -> dict:
+    """evaluate (sim_steps = 0) or evaluate_tstep (sim_steps = T >= 1)."""
+    if prm.sim_steps >= 1:
+        return evaluate_tstep(hand, obj, q, r, prm, prm.sim_steps, dec=dec, anchor_mode=anchor_mode)
+    return evaluate(hand, obj, q, r, prm, dec=dec, anchor_mode=anchor_mode)
+
+
 def loss_and_grad(hand: Hand, obj: Obj, q32, r: float, prm: Params, alpha=None):
     """Loss, gradient dL/dq (leaky rule) and the forward outputs for candidates q [B,D]."""
     if alpha is not None:
         prm = Params(**{**prm.__dict__, "alpha_leak": alpha})
     q = torch.as_tensor(np.asarray(q32, dtype=np.float64)).clone().requires_grad_(True)
-    out = evaluate(hand, obj, q, r, prm)
+    out = evaluate_any(hand, obj, q, r, prm)
     (g,) = torch.autograd.grad(out["L"].sum(), q)
     out["grad"] = g
     return out
@@ -403,6 +554,33 @@ def optimize(setup: Setup, q32: np.ndarray, obj_of_cand: np.ndarray, step0: int,
 
 # ----------------------------------------------------------------------------- guard band
 
+def guard_margins_tstep(hand: Hand, obj: Obj, q32, r: float, prm: Params) -> dict:
+    """guard_margins for the T-step form: the same distances over every step and
+    simulation (object-frame query points r, phi_hat, friction regime), and the
+    sine of the angle between the normal and the material point's displacement."""
+    with torch.no_grad():
+        q = torch.as_tensor(np.asarray(q32, dtype=np.float64))
+        out = evaluate_tstep(hand, obj, q, r, prm, prm.sim_steps)
+        inf = float("inf")
+        B = q.shape[0]
+        face = torch.full((B,), inf, dtype=F64)
+        phim = torch.full((B,), inf, dtype=F64)
+        fr = torch.full((B,), inf, dtype=F64)
+        par = torch.full((B,), inf, dtype=F64)
+        for tr in out["trace"]:
+            u = (tr["r"] - obj.origin) / obj.pitch
+            face = torch.minimum(face, (u - torch.round(u)).abs().amin(dim=(1, 2, 3)))
+            phim = torch.minimum(phim, tr["phi_hat"].abs().amin(dim=(1, 2)))
+            f = (tr["sigma"] - prm.mu * tr["C"]).abs()
+            f = torch.where(tr["kappa"] & tr["has_t"], f, torch.full_like(f, inf)).amin(dim=(1, 2))
+            fr = torch.minimum(fr, f)
+            moving = tr["s_raw"] > 0
+            ratio = torch.where(moving, tr["sigma"] / torch.where(moving, tr["s_raw"], torch.ones_like(tr["s_raw"])),
+                                torch.full_like(tr["sigma"], inf))
+            par = torch.minimum(par, ratio.amin(dim=(1, 2)))
+    return {"face": face.numpy(), "phi": phim.numpy(), "friction": fr.numpy(), "parallel": par.numpy()}
+
+
 def guard_margins(hand: Hand, obj: Obj, q32, r: float, prm: Params) -> dict:
     """Distances of every decision from its threshold, per candidate (minimum over
     points): voxel faces / clamp planes (in voxels), |phi_m| for the contact flag
@@ -427,6 +605,6 @@ def clean_candidates(hand: Hand, obj: Obj, q32, r: float, prm: Params, face_tol:
                      phi_tol: float = 1e-6, fr_tol: float = 1e-6, par_tol: float = 1e-3) -> np.ndarray:
     """Candidates whose decisions all sit outside the guard band, so that a float32
     evaluation takes the same branches as this float64 one."""
-    m = guard_margins(hand, obj, q32, r, prm)
+    m = guard_margins_tstep(hand, obj, q32, r, prm) if prm.sim_steps >= 1 else guard_margins(hand, obj, q32, r, prm)
     return ((m["face"] > face_tol) & (m["phi"] > phi_tol) & (m["friction"] > fr_tol)
             & (m["parallel"] > par_tol))
