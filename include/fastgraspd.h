@@ -92,7 +92,15 @@ typedef struct {
  * Sec. III-C, IV-A).  v_test (test-velocity magnitude, m/s), mu (Coulomb
  * coefficient), the loss weights and the dilation start r0 (metres) are not
  * fixed by the paper.  schedule: 0 = constant dilation r0, 1 = r decreases
- * linearly from r0 at step 0 to 0 at step total_steps - 1 (Sec. III-B). */
+ * linearly from r0 at step 0 to 0 at step total_steps - 1 (Sec. III-B).
+ * sim_steps: the number T of simulated steps in the grasp metric (Sec. IV-A:
+ * the object's velocity after T steps; the paper's experiments use T = 1).
+ *   0: one step, each simulation's constraint on the plane through the single
+ *      SDF query of the point (the default path of every entry point);
+ *   1..FG_MAX_SIM_STEPS: T steps, every point re-queried in the SDF at each
+ *      simulation's predicted object pose of every step (Sec. III-C); accepted
+ *      by fg_loss_and_grad and fg_optimize_step only (FG_ERR_INVALID elsewhere). */
+#define FG_MAX_SIM_STEPS 8
 typedef struct {
   float alpha_leak;
   float dt;
@@ -104,6 +112,7 @@ typedef struct {
   float w_limit;
   float w_pen;
   int schedule;
+  int sim_steps;
 } fg_params;
 
 /* ------------------------------------------------------------------ misc */

@@ -554,6 +554,17 @@ def optimize(setup: Setup, q32: np.ndarray, obj_of_cand: np.ndarray, step0: int,
 
 # ----------------------------------------------------------------------------- guard band
 
+def _face_margin(obj: Obj, pts: torch.Tensor) -> torch.Tensor:
+    """Per point and axis, the distance (in voxels) of the lookup's decision from its
+    threshold: inside the grid range the cell choice (distance to the nearest
+    node plane), outside it the clamp (distance to the clamp plane)."""
+    n = torch.tensor(obj.dims, dtype=F64)
+    u = (pts - obj.origin) / obj.pitch
+    uc = torch.minimum(torch.maximum(u, torch.zeros_like(u)), n - 1)
+    inside = u == uc
+    return torch.where(inside, (u - torch.round(u)).abs(), (u - uc).abs())
+
+
 def guard_margins_tstep(hand: Hand, obj: Obj, q32, r: float, prm: Params) -> dict:
     """guard_margins for the T-step form: the same distances over every step and
     simulation (object-frame query points r, phi_hat, friction regime), and the
@@ -568,8 +579,7 @@ def guard_margins_tstep(hand: Hand, obj: Obj, q32, r: float, prm: Params) -> dic
         fr = torch.full((B,), inf, dtype=F64)
         par = torch.full((B,), inf, dtype=F64)
         for tr in out["trace"]:
-            u = (tr["r"] - obj.origin) / obj.pitch
-            face = torch.minimum(face, (u - torch.round(u)).abs().amin(dim=(1, 2, 3)))
+            face = torch.minimum(face, _face_margin(obj, tr["r"]).amin(dim=(1, 2, 3)))
             phim = torch.minimum(phim, tr["phi_hat"].abs().amin(dim=(1, 2)))
             f = (tr["sigma"] - prm.mu * tr["C"]).abs()
             f = torch.where(tr["kappa"] & tr["has_t"], f, torch.full_like(f, inf)).amin(dim=(1, 2))
@@ -591,8 +601,7 @@ def guard_margins(hand: Hand, obj: Obj, q32, r: float, prm: Params) -> dict:
     with torch.no_grad():
         q = torch.as_tensor(np.asarray(q32, dtype=np.float64))
         out = evaluate(hand, obj, q, r, prm)
-        u = (out["points"] - obj.origin) / obj.pitch
-        face = (u - torch.round(u)).abs().amin(dim=(-1, -2))
+        face = _face_margin(obj, out["points"]).amin(dim=(-1, -2))
         phim = out["phi_m"].abs().amin(dim=(-1, -2))
         kap = out["kappa"]
         fr = (out["sigma"] - prm.mu * out["C"]).abs()

@@ -49,6 +49,7 @@ ParamsDev params_from(const fg_params* p) {
   d.w_limit = p->w_limit;
   d.w_pen = p->w_pen;
   d.schedule = p->schedule;
+  d.sim_steps = p->sim_steps;
   return d;
 }
 
@@ -67,6 +68,8 @@ static fg_status check_params(const fg_params* p) {
   if (!std::isfinite(p->lr) || !std::isfinite(p->w_range) || !std::isfinite(p->w_limit) || !std::isfinite(p->w_pen))
     return invalid("params has a non-finite weight");
   if (p->schedule != 0 && p->schedule != 1) return invalid("params.schedule must be 0 or 1");
+  if (p->sim_steps < 0 || p->sim_steps > FG_MAX_SIM_STEPS)
+    return invalid("params.sim_steps must be in [0, FG_MAX_SIM_STEPS]");
   return FG_OK;
 }
 
@@ -390,10 +393,19 @@ static fg_status check_common(const char* fn, const fg_hand* h, const fg_scene* 
   return check_params(p);
 }
 
+// Entry points that implement the one-step metric only.
+static fg_status check_one_step(const char* fn, const fg_params* p) {
+  if (p->sim_steps != 0)
+    return invalid(std::string(fn) + ": params.sim_steps must be 0 here (T-step metric: fg_loss_and_grad, "
+                   "fg_optimize_step)");
+  return FG_OK;
+}
+
 fg_status fg_contact_wrench(const fg_hand* h, const fg_scene* sc, const int* oc, const float* q, int B,
                             const fg_params* p, float r, float* wrench, int* ncontact, uint32_t* bits,
                             void* stream) {
   fg_status st = check_common("fg_contact_wrench", h, sc, B, p);
+  if (st == FG_OK) st = check_one_step("fg_contact_wrench", p);
   if (st != FG_OK) return st;
   if (B == 0) return FG_OK;
   if (!q || !wrench || !ncontact) return invalid("fg_contact_wrench: NULL buffer");
@@ -435,6 +447,8 @@ fg_status fg_loss_and_grad(const fg_hand* h, const fg_scene* sc, const int* oc, 
   a.nsteps = 1;
   a.loss = loss;
   a.grad = grad;
+  if (a.P.sim_steps >= 1)
+    return cuda_status(launch_tstep(kModeLossGrad, a, (cudaStream_t)stream), "fg_loss_and_grad (T-step)");
   return cuda_status(launch_fused(kModeLossGrad, a, h, (cudaStream_t)stream), "fg_loss_and_grad");
 }
 
@@ -459,6 +473,8 @@ fg_status fg_optimize_step(const fg_hand* h, const fg_scene* sc, const int* oc, 
   a.total_steps = total_steps;
   a.nsteps = nsteps;
   a.loss = loss;
+  if (a.P.sim_steps >= 1)
+    return cuda_status(launch_tstep(kModeOptimize, a, (cudaStream_t)stream), "fg_optimize_step (T-step)");
   return cuda_status(launch_fused(kModeOptimize, a, h, (cudaStream_t)stream), "fg_optimize_step");
 }
 
@@ -472,6 +488,7 @@ fg_status fg_optimize_step_plain(const fg_hand* h, const fg_scene* sc, const int
                                  const fg_params* p, int step, int total_steps, int nsteps, float* loss, void* ws,
                                  size_t ws_bytes, void* stream) {
   fg_status st = check_common("fg_optimize_step_plain", h, sc, B, p);
+  if (st == FG_OK) st = check_one_step("fg_optimize_step_plain", p);
   if (st != FG_OK) return st;
   if (nsteps < 1) return invalid("fg_optimize_step_plain: nsteps must be >= 1");
   if (step < 0 || total_steps < 1) return invalid("fg_optimize_step_plain: need step >= 0 and total_steps >= 1");
@@ -513,6 +530,7 @@ fg_status fg_autotune(const fg_hand* h, const fg_scene* sc, const int* oc, const
                       int step, int total_steps, int nsteps, int reps, float* host_times_ms, int* best,
                       void* stream) {
   fg_status st = check_common("fg_autotune", h, sc, B, p);
+  if (st == FG_OK) st = check_one_step("fg_autotune", p);
   if (st != FG_OK) return st;
   if (B < 1 || !q) return invalid("fg_autotune: need B >= 1 and q");
   if (nsteps < 1 || reps < 1 || step < 0 || total_steps < 1) return invalid("fg_autotune: bad step arguments");

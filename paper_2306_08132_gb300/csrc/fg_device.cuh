@@ -63,6 +63,7 @@ struct ObjDev {
 struct ParamsDev {
   float alpha, dt, V, mu, lr, r0, w_range, w_limit, w_pen;
   int schedule;
+  int sim_steps;                 // 0: one plane-linearised step; T >= 1: T re-queried steps
 };
 
 // -------------------------------------------------------------------- rounding

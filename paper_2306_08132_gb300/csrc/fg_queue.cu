@@ -283,6 +283,7 @@ fg_status fg_queue_submit(fg_queue* Q, const fg_request* r, uint64_t* id) {
   if (!(p.dt > 0.0f) || !(p.v_test >= 0.0f) || !(p.mu >= 0.0f) || !(p.alpha_leak >= 0.0f && p.alpha_leak <= 1.0f) ||
       !(p.r0 >= 0.0f) || (p.schedule != 0 && p.schedule != 1))
     return qinvalid("fg_queue_submit: invalid params");
+  if (p.sim_steps != 0) return qinvalid("fg_queue_submit: params.sim_steps must be 0 (one-step metric)");
   const int D = r->hand->host.D;
   const size_t state = sizeof(float) * (size_t)r->B * (D + 1);
   if (state + sdf_bytes(r->sdf) > Q->budget) {

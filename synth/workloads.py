@@ -34,6 +34,7 @@ def default_params(r0: float = 0.004, schedule: str = "fixed") -> dict:
         "w_limit": 1.0,      # weight of L_limit (reading)
         "w_pen": 0.0,        # weight of the explicit penetration sum (reading: off)
         "schedule": schedule,  # "fixed" r = r0, or "linear" r0 -> 0 over the run
+        "sim_steps": 0,      # 0: one step on the plane through the query; T >= 1: T re-queried steps
     }
 
 
