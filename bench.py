@@ -249,6 +249,8 @@ def main():
     ap.add_argument("--config", type=int, default=None, help="fused configuration index (default: autotune)")
     ap.add_argument("--serving", type=int, default=40, help="requests in the serving (p50/p99) run; 0 skips it")
     ap.add_argument("--serving-rate", type=float, default=200.0)
+    ap.add_argument("--tstep", default="",
+                    help="comma-separated T: also time the T-step metric (SDF re-queried for T steps) on this workload")
     ap.add_argument("--serving-sweep", default="",
                     help="comma-separated arrival rates (req/s) for a latency-vs-load sweep of the same stream")
     args = ap.parse_args()
@@ -408,6 +410,21 @@ def main():
                 "frac_kernel_min": min_achieved / peak,
                 "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
 
+    tstep = None
+    if args.tstep:
+        tstep = []
+        for T in [int(x) for x in args.tstep.split(",") if x.strip()]:
+            pT = dict(w.params, sim_steps=T)
+
+            def tstep_step(pT=pT):
+                q.copy_(q0)
+                fg.optimize_step(hand, scene, q, pT, 0, K, S_in, obj_of_cand=oc, loss=loss)
+
+            tms = timed(graphed(tstep_step), max(3, args.steps // 4), 3)
+            t_ms = max_over_ranks(float(np.mean(tms)), world, dev)
+            tstep.append({"T": T, "ms_per_step": t_ms, "value": cand_steps / (t_ms / 1000.0),
+                          "unit": "candidate-steps/s", "sdf_queries_per_point_step": 2 * 7 * T})
+
     serving, sweep = None, None
     if args.serving > 0:
         free, _ = torch.cuda.mem_get_info()
@@ -444,7 +461,7 @@ def main():
                                                             for c, t in zip(cfgs, cfg_ms)}}},
                 "plain": plain, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
                 "latency": None if serving is None else {"p50_s": serving["p50_s"], "p99_s": serving["p99_s"]},
-                "serving": serving, "serving_sweep": sweep,
+                "serving": serving, "serving_sweep": sweep, "tstep": tstep,
                 "gpu_launches": args.steps * 1, "clocks": clocks, "wall_s_timed_region": wall,
                 "per_step_ms": {"min": float(np.min(ms)), "median": float(np.median(ms)), "max": float(np.max(ms))}}
         print(json.dumps(line))

@@ -103,7 +103,7 @@ def count_step(setup: O.Setup, q32: np.ndarray, obj_index: int, r: float, want_g
     hand, obj = setup.hand, setup.objs[obj_index]
     q = torch.as_tensor(np.asarray(q32, dtype=np.float64)).clone().requires_grad_(want_grad)
     with FlopCounter() as fc:
-        out = O.evaluate(hand, obj, q, r, setup.prm)
+        out = O.evaluate_any(hand, obj, q, r, setup.prm)
         if want_grad:
             torch.autograd.grad(out["L"].sum(), q)
     units = q.shape[0] * hand.P

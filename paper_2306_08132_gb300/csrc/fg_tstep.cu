@@ -56,6 +56,7 @@ struct TstepSmem {
   float ab[kSims][12];        // adjoint of a state: x, R (world-frame rotation vector), v, w
   float red[kTW][kSims][12];  // per-warp partial sums
   float lacc[kTW][kMaxLinks][6];
+  unsigned act[kSims][kMaxCullChunks / 32];   // forward: chunks that may touch the object, per simulation
   float loss;
   int bad_object;
   const HandDev* hand_loaded;
@@ -227,8 +228,64 @@ __device__ void contact_adjoint(const float d[3], const float n[3], const float 
   dphi = kappa ? -dC : -P.alpha * dC;
 }
 
+// Whether a chunk of points can hold a contact at a step's predicted pose: its
+// bounding sphere (centre cw in the world, radius R), moved into the object frame,
+// lies in a box over which the min-pyramid bounds the interpolated field; with
+// that bound above r_dil (plus float32 slack on positions and values) no point of
+// the chunk is in contact.  Same test as the one-step kernel's culling, without
+// the plane term.
+__device__ __forceinline__ bool chunk_may_touch(const ObjDev& O, const SimStep& st, const float cw[3], float R,
+                                                float rdil) {
+  float d[3], c[3];
+  step_query(st, cw, d, c);
+  const float slack = 1e-6f + 1e-5f * (fabsf(cw[0]) + fabsf(cw[1]) + fabsf(cw[2]) + fabsf(d[0]) + fabsf(d[1]) +
+                                       fabsf(d[2]));
+  const float Ru = (R + slack) * O.inv_h;
+  const float org[3] = {O.ox, O.oy, O.oz};
+  float lo[3], hi[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float u = (c[k] - org[k]) * O.inv_h;
+    lo[k] = u - Ru - 1e-3f;
+    hi[k] = u + Ru + 1e-3f;
+  }
+  const float mn = region_min(O, lo, hi);
+  return !(mn - rdil - (1e-6f + 1e-5f * fabsf(mn)) > 0.0f);
+}
+
+// Contact flag of a query from its cell and corners: the same arithmetic as the
+// full lookup's value (sdf_finish), so the decision is the same bit for bit.
+__device__ __forceinline__ bool query_in_contact(const ObjDev& O, const SdfIndex& ix, const float c[8], float rdil) {
+  SdfSample smp;
+  sdf_finish<false>(O, ix, c, smp);
+  return sub_(smp.phi, rdil) < 0.0f;
+}
+
+// dL/dphi_hat of a point out of contact (C = 0, kinetic friction since
+// sigma > mu C = 0): dC = -(gf . n)/w_n - mu (gf . t)/w_t, dphi_hat = -alpha dC.
+__device__ __forceinline__ float leaky_adjoint(const float d[3], const float n[3], const float sr[3],
+                                               const float Gl[3], const float Ga[3], const ParamsDev& P,
+                                               const ObjDev& O, float extra_dC) {
+  float gad[3];
+  cross3(Ga, d, gad);
+  const float gf[3] = {Gl[0] + gad[0], Gl[1] + gad[1], Gl[2] + gad[2]};
+  float un[3];
+  cross3(d, n, un);
+  const float wn = fma_(O.inv_inertia, dot3(un, un), O.inv_mass);
+  float dC = -dot3(gf, n) * __fdividef(1.0f, wn) + extra_dC;
+  float t[3];
+  const float sig = tangent_of(n, sr, t);
+  if (sig > 0.0f) {
+    float ut[3];
+    cross3(d, t, ut);
+    const float wt = fma_(O.inv_inertia, dot3(ut, ut), O.inv_mass);
+    dC -= P.mu * dot3(gf, t) * __fdividef(1.0f, wt);
+  }
+  return -P.alpha * dC;
+}
+
 template <int MODE>
-__global__ void __launch_bounds__(kTW * 32, 3) tstep_kernel(FusedArgs a) {
+__global__ void __launch_bounds__(kTW * 32, 4) tstep_kernel(FusedArgs a) {
   __shared__ TstepSmem S;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) S.hand_loaded = nullptr;
@@ -299,10 +356,32 @@ __global__ void __launch_bounds__(kTW * 32, 3) tstep_kernel(FusedArgs a) {
           exp_coeffs(st.wdt, st.c1, st.c2);
         }
         __syncthreads();
+        const bool cull = H.nchunks <= kMaxCullChunks;
+        if (cull) {
+          const int span = ((H.nchunks + 31) >> 5) * 32;
+          for (int e = tid; e < kSims * span; e += kTW * 32) {      // a warp's 32 entries share m
+            const int m = e / span, j = e - m * span;
+            bool active = false;
+            if (j < H.nchunks) {
+              const int l = H.chunk_link[j];
+              active = true;
+              if (l >= 0) {
+                const float4 cs = __ldg(H.chunk_sphere + j);
+                float cw[3];
+                world_point(S.frame4[l], cs, cw);
+                active = chunk_may_touch(O, S.st[t][m], cw, cs.w, rdil);
+              }
+            }
+            const unsigned word = __ballot_sync(kFull, active);
+            if (lane == 0) S.act[m][j >> 5] = word;
+          }
+          __syncthreads();
+        }
         for (int m = 0; m < kSims; ++m) {
           const SimStep& st = S.st[t][m];
           float W[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, cnt = 0.0f;
           for (int j = warp; j < H.nchunks; j += kTW) {
+            if (cull && !((S.act[m][j >> 5] >> (j & 31)) & 1u)) continue;   // no contact possible
             const int base = 32 * j, i = base + lane;
             const bool valid = i < P;
             const float4 sp = __ldg(H.pts + (valid ? i : base));
@@ -446,46 +525,80 @@ __global__ void __launch_bounds__(kTW * 32, 3) tstep_kernel(FusedArgs a) {
             float p[3], d[3], r[3];
             world_point(S.frame4[link], sp, p);
             step_query(st, p, d, r);
-            SdfSample smp;
-            sdf_lookup<true>(O, r, smp);
-            PointState ps;
-            point_state(smp, r, rdil, ps);
-            const bool kap = ps.phi_hat < 0.0f;
-            float n[3], sr[3];
-            matvec3(st.Rt, ps.n, n);
-            material_displacement(st, d, sr);
-            float dphi, dn[3], dd[3], dsr[3];
-            contact_adjoint(d, n, sr, ps.phi_hat, kap, Gl, Ga, Pm, O, extra, dphi, dn, dd, dsr);
-            // sr = p - x - R r: r gets -R^T dsr, with R^T = R~^T Exp(wdt)
-            float e[3], rb[3];
-            exp_apply(st.wdt, st.c1, st.c2, 1.0f, dsr, e);
-            mat_t_vec(st.Rt, e, rb);
-            rb[0] = -rb[0]; rb[1] = -rb[1]; rb[2] = -rb[2];
-            // n = R~ n_obj
-            float dno[3], rtb[3];
-            mat_t_vec(st.Rt, dn, dno);
-            cross3(n, dn, rtb);
-            sdf_adjoint(smp, ps, dphi, dno, rb);          // adds the lookup's adjoint to rb
-            // r = R~^T d
-            float Rrb[3], tmp[3];
-            matvec3(st.Rt, rb, Rrb);
-            cross3(Rrb, d, tmp);
-            float pb[3], Rr[3], rRb[3];
+            // A warp with no point in contact in this simulation and step takes the
+            // leaky-only adjoint: C = 0 there, so the force direction (normal,
+            // tangent) carries no gradient and only dphi_hat = -alpha dC reaches
+            // the query, through the gradient of the SDF (no curvature term).
+            SdfIndex ix;
+            sdf_index(O, r, ix);
+            float corner[8];
+            sdf_gather(O, ix.cell, corner);
+            float pb[3];
+            if (!__any_sync(kFull, valid && query_in_contact(O, ix, corner, rdil))) {
+              SdfSample smp;
+              sdf_finish<false>(O, ix, corner, smp);
+              PointState ps;
+              point_state(smp, r, rdil, ps);
+              float n[3], sr[3];
+              matvec3(st.Rt, ps.n, n);
+              material_displacement(st, d, sr);
+              const float dphi = leaky_adjoint(d, n, sr, Gl, Ga, Pm, O, extra);
+              float rb[3], Rrb[3], rtb[3];
 #pragma unroll
-            for (int k = 0; k < 3; ++k) {
-              dd[k] += Rrb[k];
-              rtb[k] += tmp[k];
-              pb[k] = dd[k] + dsr[k];
-              Rr[k] = d[k] + st.dtv[k] - sr[k];           // R r = p - x - sr
-            }
-            cross3(dsr, Rr, rRb);
-            if (valid) {
+              for (int k = 0; k < 3; ++k) rb[k] = dphi * smp.g[k];
+              matvec3(st.Rt, rb, Rrb);
+              cross3(Rrb, d, rtb);
+#pragma unroll
+              for (int k = 0; k < 3; ++k) pb[k] = Rrb[k];
+              if (valid) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                  accS[k] -= Rrb[k];         // x~
+                  accS[3 + k] += rtb[k];     // R~
+                }
+              }
+            } else {
+              SdfSample smp;
+              sdf_finish<true>(O, ix, corner, smp);
+              PointState ps;
+              point_state(smp, r, rdil, ps);
+              const bool kap = ps.phi_hat < 0.0f;
+              float n[3], sr[3];
+              matvec3(st.Rt, ps.n, n);
+              material_displacement(st, d, sr);
+              float dphi, dn[3], dd[3], dsr[3];
+              contact_adjoint(d, n, sr, ps.phi_hat, kap, Gl, Ga, Pm, O, extra, dphi, dn, dd, dsr);
+              // sr = p - x - R r: r gets -R^T dsr, with R^T = R~^T Exp(wdt)
+              float e[3], rb[3];
+              exp_apply(st.wdt, st.c1, st.c2, 1.0f, dsr, e);
+              mat_t_vec(st.Rt, e, rb);
+              rb[0] = -rb[0]; rb[1] = -rb[1]; rb[2] = -rb[2];
+              // n = R~ n_obj
+              float dno[3], rtb[3];
+              mat_t_vec(st.Rt, dn, dno);
+              cross3(n, dn, rtb);
+              sdf_adjoint(smp, ps, dphi, dno, rb);          // adds the lookup's adjoint to rb
+              // r = R~^T d
+              float Rrb[3], tmp[3];
+              matvec3(st.Rt, rb, Rrb);
+              cross3(Rrb, d, tmp);
+              float Rr[3], rRb[3];
 #pragma unroll
               for (int k = 0; k < 3; ++k) {
-                accS[k] -= dd[k];          // x~
-                accS[3 + k] += rtb[k];     // R~
-                accS[6 + k] -= dsr[k];     // x (through sr)
-                accS[9 + k] += rRb[k];     // R (through sr)
+                dd[k] += Rrb[k];
+                rtb[k] += tmp[k];
+                pb[k] = dd[k] + dsr[k];
+                Rr[k] = d[k] + st.dtv[k] - sr[k];           // R r = p - x - sr
+              }
+              cross3(dsr, Rr, rRb);
+              if (valid) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                  accS[k] -= dd[k];          // x~
+                  accS[3 + k] += rtb[k];     // R~
+                  accS[6 + k] -= dsr[k];     // x (through sr)
+                  accS[9 + k] += rRb[k];     // R (through sr)
+                }
               }
             }
             float vL[6];
