@@ -292,8 +292,14 @@ def main():
     if args.profile_kernel:
         if args.config is not None:
             fg.fused_config_select(args.config)
-        for _ in range(5):
-            fused_step()
+        if args.tstep:                       # the T-step kernel instead, T = the first value
+            pT = dict(w.params, sim_steps=int(args.tstep.split(",")[0]))
+            for _ in range(3):
+                q.copy_(q0)
+                fg.optimize_step(hand, scene, q, pT, 0, K, S_in, obj_of_cand=oc, loss=loss)
+        else:
+            for _ in range(5):
+                fused_step()
         torch.cuda.synchronize()
         return
 

@@ -378,7 +378,7 @@ __global__ void __launch_bounds__(kTW * 32, 4) tstep_kernel(FusedArgs a) {
           __syncthreads();
         }
         for (int m = 0; m < kSims; ++m) {
-          const SimStep& st = S.st[t][m];
+          const SimStep st = S.st[t][m];          // registers: the sweep also writes shared memory
           float W[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, cnt = 0.0f;
           for (int j = warp; j < H.nchunks; j += kTW) {
             if (cull && !((S.act[m][j >> 5] >> (j & 31)) & 1u)) continue;   // no contact possible
@@ -507,7 +507,7 @@ __global__ void __launch_bounds__(kTW * 32, 4) tstep_kernel(FusedArgs a) {
         }
         __syncthreads();
         for (int m = 0; m < kSims; ++m) {
-          const SimStep& st = S.st[t][m];
+          const SimStep st = S.st[t][m];          // registers: the sweep also writes shared memory
           const float Gl[3] = {S.G[m][0], S.G[m][1], S.G[m][2]};
           const float Ga[3] = {S.G[m][3], S.G[m][4], S.G[m][5]};
           const float extra = (m == 0 && t == 0) ? Pm.w_pen : 0.0f;   // L_pen on the first step at rest
@@ -517,7 +517,9 @@ __global__ void __launch_bounds__(kTW * 32, 4) tstep_kernel(FusedArgs a) {
           for (int k = 0; k < 12; ++k) accS[k] = 0.0f;
           int cur = -1;
           float accL[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
-          for (int j = warp; j < H.nchunks; j += kTW) {
+          // contiguous chunks per warp: a warp meets each link in one run
+          const int span = (H.nchunks + kTW - 1) / kTW, jb = warp * span, je = min(H.nchunks, jb + span);
+          for (int j = jb; j < je; ++j) {
             const int base = 32 * j, i = base + lane;
             const bool valid = i < P;
             const float4 sp = __ldg(H.pts + (valid ? i : base));

@@ -83,3 +83,52 @@ def test_loss_only_path_equals_loss_with_gradient(fg):
     # no gradient requested through autograd: forward only
     l3 = fg.grasp_loss(q, hand, scene, w.params, 0.004)
     assert torch.equal(l1, l3)
+
+
+def _repeat_tstep_decisions(dec: O.TStepDecisions, n: int) -> O.TStepDecisions:
+    rep = lambda t: t.repeat((n,) + (1,) * (t.dim() - 1))
+    steps = []
+    for sd in dec.steps:
+        out = O.StepDecisions()
+        for k, v in sd.__dict__.items():
+            setattr(out, k, {kk: rep(vv) for kk, vv in v.items()} if isinstance(v, dict) else rep(v))
+        steps.append(out)
+    return O.TStepDecisions(steps=steps, **{k: rep(getattr(dec, k))
+                                           for k in ("v_nz", "w_nz", "range_nz", "above", "below")})
+
+
+def _fd_tstep(S, obj, q_row, r, T):
+    """Richardson-extrapolated central differences (h = 2e-10, 1e-10) of the
+    oracle's T-step loss with every branch frozen at q_row."""
+    qb = torch.tensor(q_row[None].astype(np.float64))
+    base = O.evaluate_tstep(S.hand, obj, qb, r, S.prm, T)
+    D = qb.shape[1]
+    dec = _repeat_tstep_decisions(base["dec"], 2 * D)
+    fd = np.zeros(D)
+    for h, wgt in ((2e-10, -1.0 / 3.0), (1e-10, 4.0 / 3.0)):
+        E = torch.eye(D, dtype=torch.float64) * h
+        L = O.evaluate_tstep(S.hand, obj, torch.cat([qb + E, qb - E]), r, S.prm, T, dec=dec, anchor_mode=True)["L"]
+        fd += wgt * ((L[:D] - L[D:]) / (2 * h)).numpy()
+    return fd
+
+
+def test_autograd_tstep_gradient_matches_oracle_finite_differences(fg):
+    """The T-step metric (T = 2) through GraspLoss against finite differences of the
+    oracle's branch-frozen T-step loss."""
+    w = synth.tiny_sphere_workload(n_cand=32)
+    params = dict(w.params, sim_steps=2)
+    S = O.Setup(w.hand, w.objects, params)
+    hand = fg.Hand.from_synth(w.hand)
+    scene = fg.Scene([fg.Sdf.from_synth(w.objects[0])])
+    q = torch.tensor(w.q0, device="cuda", requires_grad=True)
+    fg.grasp_loss(q, hand, scene, params, 0.004).sum().backward()
+    g_gpu = q.grad.cpu().numpy().astype(np.float64)
+    compared = 0
+    for b in range(w.B):
+        if not O.clean_candidates(S.hand, S.objs[0], w.q0[b:b + 1], 0.004, S.prm)[0]:
+            continue
+        fd = _fd_tstep(S, S.objs[0], w.q0[b], 0.004, 2)
+        rel = np.linalg.norm(g_gpu[b] - fd) / max(np.linalg.norm(fd), 1e-6)
+        assert rel < 1e-3, (b, rel)
+        compared += 1
+    assert compared >= 16, compared
