@@ -39,6 +39,8 @@ from dataclasses import dataclass, field
 import numpy as np
 import torch
 
+from . import mesh_sdf as _mesh
+
 F64 = torch.float64
 
 # Sec. IV-A: zero velocity plus positive and negative velocity along each axis.
@@ -174,7 +176,10 @@ def _safe_norm(x: torch.Tensor, nonzero: torch.Tensor):
 
 def sdf_decisions(obj: Obj, p: torch.Tensor) -> dict:
     """Branches of the grid lookup: per axis clamped below/above, and the cell index
-    i0 = min(floor(clamp(u, 0, n-1)), n-2)."""
+    i0 = min(floor(clamp(u, 0, n-1)), n-2).  For a mesh object, the mesh query's
+    (closest face, sign, Phong point; oracle/mesh_sdf.py)."""
+    if isinstance(obj, _mesh.MeshObj):
+        return _mesh.mesh_decisions(obj, p)
     with torch.no_grad():
         n = torch.tensor(obj.dims, dtype=F64)
         u = (p - obj.origin) / obj.pitch
@@ -189,7 +194,10 @@ def sdf_eval(obj: Obj, p: torch.Tensor, dec: dict):
 
     u = (p - origin)/h; u_c = u clamped into [0, n-1] (per the decisions);
     f = u_c - i0; phi = trilinear(G, i0, f) + h |u - u_c|;
-    grad = (1/h) d trilinear/d f on unclamped axes + (u - u_c)/|u - u_c| outside."""
+    grad = (1/h) d trilinear/d f on unclamped axes + (u - u_c)/|u - u_c| outside.
+    For a mesh object: the Phong SDF rho and its gradient (oracle/mesh_sdf.py)."""
+    if isinstance(obj, _mesh.MeshObj):
+        return _mesh.mesh_eval(obj, p, dec)
     n = torch.tensor(obj.dims, dtype=F64)
     h = obj.pitch
     u = (p - obj.origin) / h
@@ -511,7 +519,7 @@ class Setup:
 
     def __init__(self, hand: dict, objects: list, params: dict):
         self.hand = Hand.from_synth(hand)
-        self.objs = [Obj.from_synth(o) for o in objects]
+        self.objs = [_mesh.MeshObj.from_synth(o) if "faces" in o else Obj.from_synth(o) for o in objects]
         self.prm = Params.from_dict(params)
 
 
@@ -557,7 +565,14 @@ def optimize(setup: Setup, q32: np.ndarray, obj_of_cand: np.ndarray, step0: int,
 def _face_margin(obj: Obj, pts: torch.Tensor) -> torch.Tensor:
     """Per point and axis, the distance (in voxels) of the lookup's decision from its
     threshold: inside the grid range the cell choice (distance to the nearest
-    node plane), outside it the clamp (distance to the clamp plane)."""
+    node plane), outside it the clamp (distance to the clamp plane).  For a mesh,
+    ten times (in metres) the smaller of the gap to the next distinct closest
+    point (the face choice) and the distance to the flat surface (the sign), so
+    that the default tolerance of 1e-5 is 1 micrometre."""
+    if isinstance(obj, _mesh.MeshObj):
+        with torch.no_grad():
+            dec = _mesh.mesh_decisions(obj, pts)
+            return (10.0 * torch.minimum(dec["gap"], dec["dist"]))[..., None]
     n = torch.tensor(obj.dims, dtype=F64)
     u = (pts - obj.origin) / obj.pitch
     uc = torch.minimum(torch.maximum(u, torch.zeros_like(u)), n - 1)
