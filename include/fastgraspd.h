@@ -147,6 +147,30 @@ fg_status fg_sdf_create(const float* grid, int nx, int ny, int nz, const float* 
                         float pitch, float mass, float inertia, fg_sdf** out);
 fg_status fg_sdf_destroy(fg_sdf* sdf);
 
+/* Creates an object handle from a watertight triangle mesh, queried directly
+ * (Sec. III-B, "Signed distance function" and "Phong SDF"): phi(r) = s |r - r*|
+ * with r* the closest point on the mesh (found through a bounding volume
+ * hierarchy) and s = -1 inside the mesh volume (from the angle-weighted
+ * pseudonormal of the closest face, edge or vertex; on a watertight mesh this
+ * is the sign the paper's ray test gives); contacts use the Phong SDF
+ * rho(r) = s |r - r*_rho|, r*_rho = (1 - a) r* + a sum_x b_x psi_x(r*), where b are the
+ * barycentric coordinates of r* on its face, psi_x(q) = q - ((q - v_x) . n_x) n_x
+ * projects onto the tangent plane at vertex x (angle-weighted vertex normal n_x)
+ * and a = phong_alpha in [0, 1] (0: the flat mesh), with the paper's gradient
+ * grad rho = s (r - r*_rho)/|r - r*_rho|.
+ *   vertices  host [n_vertices][3] float32, in the object frame (centre of mass at
+ *             the origin at the canonical pose);
+ *   faces     host [n_faces][3] vertex indices, counter-clockwise about the
+ *             outward normal; every edge shared by exactly two faces (watertight,
+ *             consistently oriented), no zero-area face.
+ * The handle is an fg_sdf: fg_sdf_query, scenes, fg_contact_wrench, fg_loss_and_grad,
+ * fg_optimize_step and the request queue take it; the T-step metric and the
+ * per-stage form take grid objects only (FG_ERR_INVALID).  Built on the host,
+ * copied to the current device (synchronous).
+ * Errors: FG_ERR_INVALID (with the reason), FG_ERR_OOM, FG_ERR_CUDA. */
+fg_status fg_sdf_create_mesh(const float* host_vertices, int n_vertices, const int* host_faces, int n_faces,
+                             float phong_alpha, float mass, float inertia, fg_sdf** out);
+
 /* A scene is an ordered table of objects; candidates select theirs by index
  * (obj_of_cand).  The scene keeps pointers to the objects' grids: destroy the
  * scene before its objects.  Errors: FG_ERR_INVALID, FG_ERR_OOM, FG_ERR_CUDA. */

@@ -79,9 +79,17 @@ class Hand:
 
 
 class Sdf:
-    """fg_sdf: a voxel SDF grid [nz, ny, nx] (x fastest) with the object's mass properties."""
+    """fg_sdf: a voxel SDF grid [nz, ny, nx] (x fastest) with the object's mass
+    properties, or (``Sdf.from_mesh``) a watertight triangle mesh queried directly."""
 
-    def __init__(self, grid: torch.Tensor, origin, pitch: float, mass: float, inertia: float):
+    PHONG_ALPHA = 0.75
+
+    def __init__(self, grid: torch.Tensor | None, origin=None, pitch: float = 0.0, mass: float = 1.0,
+                 inertia: float = 1.0, _handle=None):
+        if _handle is not None:
+            self.handle = _handle
+            self.dims = None
+            return
         lib = _lib.load()
         g = grid.detach().to(_F32).contiguous()
         nz, ny, nx = g.shape
@@ -93,7 +101,23 @@ class Sdf:
         self.dims = (nx, ny, nz)
 
     @classmethod
+    def from_mesh(cls, vertices, faces, mass: float, inertia: float, phong_alpha: float = PHONG_ALPHA) -> "Sdf":
+        """fg_sdf_create_mesh: vertices [V,3], faces [F,3] (counter-clockwise about the outward normal)."""
+        lib = _lib.load()
+        V = np.ascontiguousarray(np.asarray(vertices, dtype=np.float32))
+        F = np.ascontiguousarray(np.asarray(faces, dtype=np.int32))
+        if V.ndim != 2 or V.shape[1] != 3 or F.ndim != 2 or F.shape[1] != 3:
+            raise ValueError("vertices and faces must be [n, 3]")
+        h = C.c_void_p()
+        check(lib.fg_sdf_create_mesh(V.ctypes.data_as(C.POINTER(C.c_float)), V.shape[0],
+                                     F.ctypes.data_as(C.POINTER(C.c_int)), F.shape[0], float(phong_alpha),
+                                     float(mass), float(inertia), C.byref(h)), "fg_sdf_create_mesh")
+        return cls(None, _handle=h)
+
+    @classmethod
     def from_synth(cls, o: dict) -> "Sdf":
+        if "faces" in o:
+            return cls.from_mesh(o["vertices"], o["faces"], o["mass"], o["inertia"])
         return cls(o["grid"], o["origin"], o["pitch"], o["mass"], o["inertia"])
 
     def __del__(self):

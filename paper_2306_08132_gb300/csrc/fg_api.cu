@@ -323,13 +323,16 @@ fg_status fg_sdf_create(const float* grid, int nx, int ny, int nz, const float* 
   }
   o.pyr = s->pyr;
   o.pyr_levels = levels;
+  o.kind = kObjGrid;
   s->pyr_bytes = sizeof(float) * pf;
+  s->mesh = nullptr;
   *out = s;
   return FG_OK;
 }
 
 fg_status fg_sdf_destroy(fg_sdf* s) {
   if (!s) return FG_OK;
+  cudaFree(s->mesh);
   cudaFree(s->pyr);
   cudaFree(s->grid);
   delete s;
@@ -347,6 +350,8 @@ fg_status fg_scene_create(const fg_sdf* const* sdfs, int n, fg_scene** out) {
   fg_scene* sc = new (std::nothrow) fg_scene;
   if (!sc) return FG_ERR_OOM;
   sc->n = n;
+  sc->has_mesh = 0;
+  for (int i = 0; i < n; ++i) sc->has_mesh |= tab[i].kind == kObjMesh;
   cudaError_t e = cudaMalloc(&sc->dev, sizeof(ObjDev) * n);
   if (e != cudaSuccess) {
     delete sc;
@@ -447,8 +452,10 @@ fg_status fg_loss_and_grad(const fg_hand* h, const fg_scene* sc, const int* oc, 
   a.nsteps = 1;
   a.loss = loss;
   a.grad = grad;
-  if (a.P.sim_steps >= 1)
+  if (a.P.sim_steps >= 1) {
+    if (sc->has_mesh) return invalid("fg_loss_and_grad: the T-step metric takes grid objects only");
     return cuda_status(launch_tstep(kModeLossGrad, a, (cudaStream_t)stream), "fg_loss_and_grad (T-step)");
+  }
   return cuda_status(launch_fused(kModeLossGrad, a, h, (cudaStream_t)stream), "fg_loss_and_grad");
 }
 
@@ -473,8 +480,10 @@ fg_status fg_optimize_step(const fg_hand* h, const fg_scene* sc, const int* oc, 
   a.total_steps = total_steps;
   a.nsteps = nsteps;
   a.loss = loss;
-  if (a.P.sim_steps >= 1)
+  if (a.P.sim_steps >= 1) {
+    if (sc->has_mesh) return invalid("fg_optimize_step: the T-step metric takes grid objects only");
     return cuda_status(launch_tstep(kModeOptimize, a, (cudaStream_t)stream), "fg_optimize_step (T-step)");
+  }
   return cuda_status(launch_fused(kModeOptimize, a, h, (cudaStream_t)stream), "fg_optimize_step");
 }
 
@@ -490,6 +499,7 @@ fg_status fg_optimize_step_plain(const fg_hand* h, const fg_scene* sc, const int
   fg_status st = check_common("fg_optimize_step_plain", h, sc, B, p);
   if (st == FG_OK) st = check_one_step("fg_optimize_step_plain", p);
   if (st != FG_OK) return st;
+  if (sc->has_mesh) return invalid("fg_optimize_step_plain: the per-stage form takes grid objects only");
   if (nsteps < 1) return invalid("fg_optimize_step_plain: nsteps must be >= 1");
   if (step < 0 || total_steps < 1) return invalid("fg_optimize_step_plain: need step >= 0 and total_steps >= 1");
   if (B == 0) return FG_OK;

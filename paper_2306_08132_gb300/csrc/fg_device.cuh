@@ -58,7 +58,19 @@ struct ObjDev {
   float uo[3];                   // -origin / pitch: index coordinate u = p / pitch + uo
   const float* pyr;              // min-pyramid, level k at pyr + pyr_off[k - 1]
   int pyr_off[kMaxPyrLevels];
+  // kind 1: a watertight triangle mesh queried directly (Phong SDF); the grid
+  // fields above are unused and the min-pyramid is absent.
+  int kind;                      // 0 grid, 1 mesh
+  int n_faces;
+  float phong_alpha;
+  const float4* bvh;             // 2 per node: (min, right child | first face), (max, face count; 0 = inner)
+  const float4* tri;             // 3 per face (BVH order): vertices a, b, c
+  const float4* face_nrm;        // 7 per face: vertex normals n_a, n_b, n_c, face normal, edge
+                                 // pseudonormals of (a,b), (b,c), (c,a)
 };
+
+constexpr int kObjGrid = 0;
+constexpr int kObjMesh = 1;
 
 struct ParamsDev {
   float alpha, dt, V, mu, lr, r0, w_range, w_limit, w_pen;
@@ -188,6 +200,7 @@ struct SdfSampleT {
   V hxy, hxz, hyz;
   V eh[3];
   V e;
+  V curv;          // mesh objects: s / |p - r*_rho| (curvature of the Phong SDF about r*_rho); 0 for grids
   mask_t<V> outside;
 };
 using SdfSample = SdfSampleT<float>;
@@ -273,6 +286,7 @@ __device__ __forceinline__ void sdf_finish_v(const ObjDev& O, const V f[3], cons
     s.hyz = vsel(mor(cl[1], cl[2]), zero, vmul(ddy, ih2));
   }
   s.outside = mor(mor(cl[0], cl[1]), cl[2]);
+  s.curv = zero;
   s.e = zero;
   s.eh[0] = s.eh[1] = s.eh[2] = zero;
   if (many(s.outside)) {
@@ -311,14 +325,6 @@ __device__ __forceinline__ void sdf_finish_pair(const ObjDev& O, const SdfIndex&
   sdf_finish_v<true, float2>(O, f, du, cl, c, s);
 }
 
-template <bool kHess>
-__device__ __forceinline__ void sdf_lookup(const ObjDev& O, const float p[3], SdfSample& s) {
-  SdfIndex ix;
-  sdf_index(O, p, ix);
-  float c[8];
-  sdf_gather(O, ix.cell, c);
-  sdf_finish<kHess>(O, ix, c, s);
-}
 
 // Lower bound of the interpolated SDF over every point whose index coordinates
 // lie in the box [lo, hi] (any values; clamped to the grid, which also covers
@@ -381,6 +387,187 @@ __device__ __forceinline__ void cross3(const float a[3], const float b[3], float
 }
 __device__ __forceinline__ float dot3(const float a[3], const float b[3]) {
   return fma_(a[0], b[0], fma_(a[1], b[1], mul_(a[2], b[2])));
+}
+
+// ----------------------------------------------------------------- mesh SDF
+//
+// Sec. III-B: phi(r) = s |r - r*| with r* the closest point on the mesh and s the
+// inside/outside sign; the Phong SDF rho(r) = s |r - r*_rho| replaces r* by the
+// point of the Phong-tessellated surface, r*_rho = (1 - a) r* + a sum_x b_x psi_x(r*),
+// psi_x(q) = q - ((q - v_x) . n_x) n_x, with (b_a, b_b, b_c) the barycentric
+// coordinates of r* on its face and n_x the vertex normals; grad rho =
+// s (r - r*_rho)/|r - r*_rho| (r*_rho held fixed, as the paper gives it).  The sign is
+// that of (r - r*) . N with N the angle-weighted pseudonormal of the closest
+// feature (face, edge or vertex), which on a watertight mesh matches the ray
+// test without a second search.
+
+// Closest point of p on triangle (a, b, c) by the Voronoi regions of its
+// vertices, edges and face: barycentric coordinates and the feature
+// (0 face, 1 edge ab, 2 edge bc, 3 edge ca, 4/5/6 vertex a/b/c).
+__device__ __forceinline__ float closest_on_triangle(const float p[3], const float a[3], const float b[3],
+                                                     const float c[3], float bary[3], int& feature) {
+  float ab[3], ac[3], ap[3], bp[3], cp[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    ab[k] = b[k] - a[k];
+    ac[k] = c[k] - a[k];
+    ap[k] = p[k] - a[k];
+    bp[k] = p[k] - b[k];
+    cp[k] = p[k] - c[k];
+  }
+  const float d1 = dot3(ab, ap), d2 = dot3(ac, ap), d3 = dot3(ab, bp), d4 = dot3(ac, bp);
+  const float d5 = dot3(ab, cp), d6 = dot3(ac, cp);
+  const float vc = d1 * d4 - d3 * d2, vb = d5 * d2 - d1 * d6, va = d3 * d6 - d5 * d4;
+  float u, v, w;
+  if (d1 <= 0.0f && d2 <= 0.0f) {
+    u = 1.0f; v = 0.0f; w = 0.0f; feature = 4;
+  } else if (d3 >= 0.0f && d4 <= d3) {
+    u = 0.0f; v = 1.0f; w = 0.0f; feature = 5;
+  } else if (vc <= 0.0f && d1 >= 0.0f && d3 <= 0.0f) {
+    v = d1 / (d1 - d3); u = 1.0f - v; w = 0.0f; feature = 1;
+  } else if (d6 >= 0.0f && d5 <= d6) {
+    u = 0.0f; v = 0.0f; w = 1.0f; feature = 6;
+  } else if (vb <= 0.0f && d2 >= 0.0f && d6 <= 0.0f) {
+    w = d2 / (d2 - d6); u = 1.0f - w; v = 0.0f; feature = 3;
+  } else if (va <= 0.0f && (d4 - d3) >= 0.0f && (d5 - d6) >= 0.0f) {
+    w = (d4 - d3) / ((d4 - d3) + (d5 - d6)); v = 1.0f - w; u = 0.0f; feature = 2;
+  } else {
+    const float den = 1.0f / (va + vb + vc);
+    v = vb * den; w = vc * den; u = 1.0f - v - w; feature = 0;
+  }
+  bary[0] = u; bary[1] = v; bary[2] = w;
+  float d2sum = 0.0f;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float q = u * a[k] + v * b[k] + w * c[k];
+    d2sum += (p[k] - q) * (p[k] - q);
+  }
+  return d2sum;
+}
+
+__device__ __forceinline__ float box_dist2(const float p[3], const float4& lo, const float4& hi) {
+  const float dx = fmaxf(fmaxf(lo.x - p[0], p[0] - hi.x), 0.0f);
+  const float dy = fmaxf(fmaxf(lo.y - p[1], p[1] - hi.y), 0.0f);
+  const float dz = fmaxf(fmaxf(lo.z - p[2], p[2] - hi.z), 0.0f);
+  return dx * dx + dy * dy + dz * dz;
+}
+
+constexpr int kBvhStack = 64;
+
+// Closest face of the mesh to p: depth-first over the BVH, nearer child first,
+// subtrees farther than the best distance found so far skipped.
+__device__ inline int mesh_closest(const ObjDev& O, const float p[3], float bary[3], int& feature) {
+  int stack[kBvhStack];
+  int sp = 0, node = 0, best = -1;
+  float best_d2 = 3.0e38f;
+  for (;;) {
+    const float4 lo = __ldg(O.bvh + 2 * node), hi = __ldg(O.bvh + 2 * node + 1);
+    const int count = __float_as_int(hi.w);
+    if (count > 0) {
+      const int first = __float_as_int(lo.w);
+      for (int f = first; f < first + count; ++f) {
+        const float4 A = __ldg(O.tri + 3 * f), B = __ldg(O.tri + 3 * f + 1), C = __ldg(O.tri + 3 * f + 2);
+        const float a[3] = {A.x, A.y, A.z}, b[3] = {B.x, B.y, B.z}, c[3] = {C.x, C.y, C.z};
+        float bb[3];
+        int ft;
+        const float d2 = closest_on_triangle(p, a, b, c, bb, ft);
+        if (d2 < best_d2) {
+          best_d2 = d2;
+          best = f;
+          bary[0] = bb[0]; bary[1] = bb[1]; bary[2] = bb[2];
+          feature = ft;
+        }
+      }
+    } else {
+      const int l = node + 1, r = __float_as_int(lo.w);
+      const float dl = box_dist2(p, __ldg(O.bvh + 2 * l), __ldg(O.bvh + 2 * l + 1));
+      const float dr = box_dist2(p, __ldg(O.bvh + 2 * r), __ldg(O.bvh + 2 * r + 1));
+      const int nearc = dl <= dr ? l : r, farc = dl <= dr ? r : l;
+      const float dn = fminf(dl, dr), df = fmaxf(dl, dr);
+      if (df < best_d2 && sp < kBvhStack) stack[sp++] = farc;
+      if (dn < best_d2) {
+        node = nearc;
+        continue;
+      }
+    }
+    // next subtree still worth visiting
+    bool found = false;
+    while (sp > 0) {
+      const int cand = stack[--sp];
+      if (box_dist2(p, __ldg(O.bvh + 2 * cand), __ldg(O.bvh + 2 * cand + 1)) < best_d2) {
+        node = cand;
+        found = true;
+        break;
+      }
+    }
+    if (!found) break;
+  }
+  return best;
+}
+
+__device__ inline void mesh_lookup(const ObjDev& O, const float p[3], SdfSample& s) {
+  float bary[3];
+  int feature = 0;
+  const int f = mesh_closest(O, p, bary, feature);
+  if (f < 0) {                                  // p not finite: no face compares closer
+    const float nan = __int_as_float(0x7fc00000);
+    s.phi = s.curv = s.e = nan;
+    s.g[0] = s.g[1] = s.g[2] = nan;
+    s.eh[0] = s.eh[1] = s.eh[2] = 0.0f;
+    s.hxy = s.hxz = s.hyz = 0.0f;
+    s.outside = false;
+    return;
+  }
+  const float4 A = __ldg(O.tri + 3 * f), B = __ldg(O.tri + 3 * f + 1), C = __ldg(O.tri + 3 * f + 2);
+  const float4* X = O.face_nrm + 7 * f;
+  const float4 na = __ldg(X), nb = __ldg(X + 1), nc = __ldg(X + 2);
+  const float v[3][3] = {{A.x, A.y, A.z}, {B.x, B.y, B.z}, {C.x, C.y, C.z}};
+  const float n[3][3] = {{na.x, na.y, na.z}, {nb.x, nb.y, nb.z}, {nc.x, nc.y, nc.z}};
+  float q[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) q[k] = bary[0] * v[0][k] + bary[1] * v[1][k] + bary[2] * v[2][k];
+  // pseudonormal of the closest feature: face 3, edges 4..6, vertices 0..2
+  const int slot = feature == 0 ? 3 : (feature <= 3 ? 3 + feature : feature - 4);
+  const float4 N = __ldg(X + slot);
+  const float side = (p[0] - q[0]) * N.x + (p[1] - q[1]) * N.y + (p[2] - q[2]) * N.z;
+  const float sgn = side < 0.0f ? -1.0f : 1.0f;
+  // Phong point
+  float acc[3] = {0.0f, 0.0f, 0.0f};
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    const float t = (q[0] - v[j][0]) * n[j][0] + (q[1] - v[j][1]) * n[j][1] + (q[2] - v[j][2]) * n[j][2];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) acc[k] += bary[j] * (q[k] - t * n[j][k]);
+  }
+  const float al = O.phong_alpha;
+  float diff[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) diff[k] = p[k] - ((1.0f - al) * q[k] + al * acc[k]);
+  const float d2 = dot3(diff, diff);
+  const float inv = d2 > 0.0f ? rsqrtf(d2) : 0.0f;
+  s.phi = sgn * d2 * inv;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    s.g[k] = sgn * diff[k] * inv;
+    s.eh[k] = 0.0f;
+  }
+  s.hxy = s.hxz = s.hyz = 0.0f;
+  s.e = 0.0f;
+  s.curv = sgn * inv;
+  s.outside = false;
+}
+
+template <bool kHess>
+__device__ __forceinline__ void sdf_lookup(const ObjDev& O, const float p[3], SdfSample& s) {
+  if (O.kind == kObjMesh) {
+    mesh_lookup(O, p, s);
+    return;
+  }
+  SdfIndex ix;
+  sdf_index(O, p, ix);
+  float c[8];
+  sdf_gather(O, ix.cell, c);
+  sdf_finish<kHess>(O, ix, c, s);
 }
 
 // Per-point quantities shared by the 7 simulations.
@@ -771,9 +958,9 @@ __device__ __forceinline__ void sdf_adjoint(const SdfSampleT<V>& s, const PointS
   V dg[3];
 #pragma unroll
   for (int k = 0; k < 3; ++k) dg[k] = vmul(vfnma(ndn, ps.n[k], dn[k]), ps.rg);
-  dp[0] = vadd(dp[0], vfma(d_phi_hat, s.g[0], vfma(s.hxy, dg[1], vmul(s.hxz, dg[2]))));
-  dp[1] = vadd(dp[1], vfma(d_phi_hat, s.g[1], vfma(s.hxy, dg[0], vmul(s.hyz, dg[2]))));
-  dp[2] = vadd(dp[2], vfma(d_phi_hat, s.g[2], vfma(s.hxz, dg[0], vmul(s.hyz, dg[1]))));
+  dp[0] = vadd(dp[0], vfma(d_phi_hat, s.g[0], vfma(s.hxy, dg[1], vfma(s.hxz, dg[2], vmul(s.curv, dg[0])))));
+  dp[1] = vadd(dp[1], vfma(d_phi_hat, s.g[1], vfma(s.hxy, dg[0], vfma(s.hyz, dg[2], vmul(s.curv, dg[1])))));
+  dp[2] = vadd(dp[2], vfma(d_phi_hat, s.g[2], vfma(s.hxz, dg[0], vfma(s.hyz, dg[1], vmul(s.curv, dg[2])))));
   if (many(s.outside)) {
     // eh is zero on unclamped axes (and for points inside the grid, where e = 0
     // and the term vanishes), so (I - eh eh^T) restricted to clamped axes is

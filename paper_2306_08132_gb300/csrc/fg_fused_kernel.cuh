@@ -140,14 +140,29 @@ __device__ __forceinline__ void point_adjoint_pair(const HandDev& H, const float
   float pa[3], pb[3];
   world_point(frame4[link[0]], sa, pa);
   world_point(frame4[link[1]], sb, pb);
-  SdfIndex xa, xb;
-  sdf_index(O, pa, xa);
-  sdf_index(O, pb, xb);
-  float ca[8], cb[8];
-  sdf_gather(O, xa.cell, ca);
-  sdf_gather(O, xb.cell, cb);
   SdfSampleT<float2> smp;
-  sdf_finish_pair(O, xa, xb, ca, cb, smp);
+  if (O.kind == kObjMesh) {
+    SdfSample sa, sb;
+    mesh_lookup(O, pa, sa);
+    mesh_lookup(O, pb, sb);
+    smp.phi = make_float2(sa.phi, sb.phi);
+    smp.hxy = smp.hxz = smp.hyz = smp.e = make_float2(0.0f, 0.0f);
+    smp.curv = make_float2(sa.curv, sb.curv);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      smp.g[k] = make_float2(sa.g[k], sb.g[k]);
+      smp.eh[k] = make_float2(0.0f, 0.0f);
+    }
+    smp.outside = bool2{false, false};
+  } else {
+    SdfIndex xa, xb;
+    sdf_index(O, pa, xa);
+    sdf_index(O, pb, xb);
+    float ca[8], cb[8];
+    sdf_gather(O, xa.cell, ca);
+    sdf_gather(O, xb.cell, cb);
+    sdf_finish_pair(O, xa, xb, ca, cb, smp);
+  }
   const float2 p[3] = {make_float2(pa[0], pb[0]), make_float2(pa[1], pb[1]), make_float2(pa[2], pb[2])};
   PointStateT<float2> ps;
   point_state(smp, p, r, ps);
@@ -325,7 +340,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) fused_step_kernel(FusedArgs a) 
       // so a chunk with  min - r - dt V (1 + 1e-5) - slack > 0  has no contact in
       // any simulation; the slack covers float32 rounding of positions and values.
       // Its contact flags are all zero and its forces are not computed.
-      const bool cull = H.nchunks <= kMaxCullChunks;
+      const bool cull = H.nchunks <= kMaxCullChunks && O.kind == kObjGrid;   // meshes have no min-pyramid
       if (cull) {
         for (int j0 = warp * 32; j0 < H.nchunks; j0 += NW * 32) {
           const int j = j0 + lane;

@@ -24,10 +24,12 @@ struct fg_sdf {
   float* pyr;
   size_t bytes;              // grid bytes
   size_t pyr_bytes;          // min-pyramid bytes
+  float4* mesh;              // mesh objects: BVH, triangles and normals (one allocation); bytes is its size
 };
 
 struct fg_scene {
   int n;
+  int has_mesh;              // some object is a mesh
   fg::ObjDev* dev;           // device [n]
 };
 

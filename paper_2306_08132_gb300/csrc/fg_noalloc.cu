@@ -72,6 +72,10 @@ extern "C" fg_status fg_optimize_step_plain_noalloc(const fg_hand* h, const fg_s
     set_error("fg_optimize_step_plain_noalloc: invalid params (sim_steps must be 0)");
     return FG_ERR_INVALID;
   }
+  if (sc->has_mesh) {
+    set_error("fg_optimize_step_plain_noalloc: the per-stage form takes grid objects only");
+    return FG_ERR_INVALID;
+  }
   if (B == 0) return FG_OK;
   if (!q) {
     set_error("fg_optimize_step_plain_noalloc: NULL q");

@@ -92,3 +92,31 @@ def _last(lib):
     buf = C.create_string_buffer(512)
     lib.fg_last_error(buf, 512)
     return buf.value
+
+
+def test_invalid_meshes_are_rejected_on_the_host(lib):
+    """fg_sdf_create_mesh validates on the host: index range, repeated vertices,
+    zero-area faces, orientation, watertightness; each with its reason."""
+    import numpy as np
+    from synth import meshes as SM
+    m = SM.box_mesh((0.03, 0.02, 0.05))
+    V, F = m["vertices"], m["faces"].copy()
+    out = C.c_void_p()
+
+    def create(Vx, Fx, alpha=0.75):
+        Vx = np.ascontiguousarray(Vx, dtype=np.float32)
+        Fx = np.ascontiguousarray(Fx, dtype=np.int32)
+        return lib.fg_sdf_create_mesh(Vx.ctypes.data_as(C.POINTER(C.c_float)), len(Vx),
+                                      Fx.ctypes.data_as(C.POINTER(C.c_int)), len(Fx), alpha, 1.0, 1.0,
+                                      C.byref(out))
+    bad = F.copy(); bad[3, 1] = 99
+    assert create(V, bad) == 1 and b"out of range" in _last(lib)
+    bad = F.copy(); bad[2, 2] = bad[2, 0]
+    assert create(V, bad) == 1 and b"repeated" in _last(lib)
+    assert create(V, F[:, ::-1]) == 1 and b"counter-clockwise" in _last(lib)
+    assert create(V, F[:-1]) == 1 and b"watertight" in _last(lib)
+    bad = F.copy(); bad[0] = bad[0][[0, 2, 1]]
+    assert create(V, bad) == 1 and b"directed edge" in _last(lib)
+    Vd = V.copy(); Vd[1] = Vd[0] + 1e-12
+    assert create(Vd, F) == 1 and (b"zero-area" in _last(lib) or b"directed" in _last(lib))
+    assert create(V, F, alpha=1.5) == 1 and b"phong_alpha" in _last(lib)

@@ -1,0 +1,171 @@
+"""Mesh objects on the GPU (fg_sdf_create_mesh: the mesh queried through a BVH,
+Phong SDF) against the FP64 oracle (oracle/mesh_sdf.py, brute-force closest
+points), through the C ABI: point queries, loss and gradient in mesh and mixed
+grid + mesh scenes, optimisation steps, every fused configuration, and the
+entry points that refuse mesh scenes.
+
+Tolerances: SDF values 2e-6 m + 1e-4 of the distance and gradient directions 5e-4 (the float32 limit
+of choosing between nearly coplanar neighbouring faces by distance) on points
+whose closest-face choice and sign sit outside the guard band (gap to a
+non-adjacent face and distance to the surface above 1 micrometre); loss 1e-4
+and gradient 1e-3 relative on clean candidates, as for grids."""
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+from oracle import fastgraspd_oracle as O
+from oracle import mesh_sdf as MS
+from synth import meshes as SM
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fg():
+    from paper_2306_08132_gb300.build import build_library
+    build_library()
+    import paper_2306_08132_gb300 as m
+    return m
+
+
+def _dev():
+    return torch.device("cuda:0")
+
+
+MESHES = {
+    "box_flat": (SM.box_mesh((0.03, 0.02, 0.05)), 0.0),
+    "icosphere": (SM.icosphere(0.04, 3), MS.PHONG_ALPHA),
+    "superquadric": (SM.superquadric_mesh((0.05, 0.03, 0.04), 0.7, 1.3, 20, 40), MS.PHONG_ALPHA),
+    "hull": (SM.hull_mesh(np.random.default_rng(7).normal(size=(40, 3)) * 0.04), MS.PHONG_ALPHA),
+}
+
+
+@pytest.mark.parametrize("name", list(MESHES))
+def test_mesh_query_matches_oracle(fg, name):
+    m, alpha = MESHES[name]
+    sdf = fg.Sdf.from_mesh(m["vertices"], m["faces"], m["mass"], m["inertia"], phong_alpha=alpha)
+    ref_mesh = MS.MeshObj.from_synth(m, alpha=alpha)
+    rng = np.random.default_rng(11)
+    for n in (1, 37, 3000):
+        p = rng.uniform(-0.09, 0.09, size=(n, 3))
+        p32 = p.astype(np.float32)
+        phi, g = fg.sdf_query(sdf, torch.tensor(p32.T.copy(), device=_dev()), 0.002)
+        res = MS.mesh_query(ref_mesh, p32.astype(np.float64))
+        diff = p32.astype(np.float64) - res["q_rho"]
+        d = np.linalg.norm(diff, axis=1)
+        rho = res["sign"] * d
+        grad = res["sign"][:, None] * diff / d[:, None]
+        clean = (res["gap"] > 1e-6) & (res["dist"] > 1e-6) & (d > 1e-6)
+        assert clean.sum() >= 0.9 * n
+        # with Phong smoothing the sideways slack of the face choice (below) moves the
+        # value at first order, by up to ~1e-4 of the distance
+        err = np.abs(phi.cpu().numpy().astype(np.float64) - (rho - 0.002))[clean]
+        assert (err < 2e-6 + 1e-4 * d[clean]).all(), (name, n, err.max())
+        assert np.median(err) < 1e-7
+        # The direction (p - r*_rho)/|p - r*_rho| carries the float32 error of the closest
+        # point divided by the distance.  Between two nearly coplanar faces whose
+        # closest points lie close together, float32 squared distances (relative
+        # rounding ~1.2e-7) cannot tell apart points up to ~sqrt(2.4e-7) d apart, so the
+        # chosen point may move sideways by that much: a direction error <= 5e-4.
+        gerr = np.abs(g.cpu().numpy().T.astype(np.float64) - grad).max(axis=1)[clean]
+        assert (gerr < 5e-4 + 2e-8 / d[clean]).all(), (name, n, gerr.max())
+        assert np.median(gerr) < 1e-5
+
+
+class Case:
+    def __init__(self, fg, hand, objects, obj_of_cand, q0, params):
+        self.hand_d, self.objects, self.oc_np, self.q0, self.params = hand, objects, obj_of_cand, q0, params
+        self.S = O.Setup(hand, objects, params)
+        self.hand = fg.Hand.from_synth(hand)
+        self.sdfs = [fg.Sdf.from_synth(o) for o in objects]
+        self.scene = fg.Scene(self.sdfs)
+        self.oc = torch.tensor(obj_of_cand, device=_dev(), dtype=torch.int32)
+
+    def clean(self, q, r):
+        mask = np.zeros(len(q), dtype=bool)
+        for k in np.unique(self.oc_np):
+            idx = np.nonzero(self.oc_np == k)[0]
+            mask[idx] = O.clean_candidates(self.S.hand, self.S.objs[int(k)], q[idx], r, self.S.prm)
+        return mask
+
+
+def _compare(loss, grad, ref, clean):
+    idx = np.nonzero(clean)[0]
+    L = loss.astype(np.float64)[idx]
+    lrel = np.abs(L - ref["L"][idx]) / np.maximum(np.abs(ref["L"][idx]), 1e-6)
+    G = grad.astype(np.float64)[idx]
+    grel = np.linalg.norm(G - ref["grad"][idx], axis=1) / np.maximum(np.linalg.norm(ref["grad"][idx], axis=1), 1e-6)
+    assert lrel.max() < 1e-4, (idx[np.argmax(lrel)], lrel.max())
+    assert grel.max() < 1e-3, (idx[np.argmax(grel)], grel.max())
+
+
+@pytest.fixture(scope="module")
+def sphere_case(fg):
+    w = synth.tiny_sphere_workload(n_cand=48)
+    return Case(fg, w.hand, [SM.icosphere(0.04, 3)], w.obj_of_cand, w.q0, w.params)
+
+
+@pytest.mark.parametrize("alpha", [0.1, 0.0])
+def test_mesh_loss_and_grad_match_oracle(fg, sphere_case, alpha):
+    c = sphere_case
+    params = dict(c.params, alpha_leak=alpha)
+    S = O.Setup(c.hand_d, c.objects, params)
+    loss, grad = fg.loss_and_grad(c.hand, c.scene, torch.tensor(c.q0, device=_dev()), params, 0.004,
+                                  obj_of_cand=c.oc)
+    ref = O.batch_loss_and_grad(S, c.q0, c.oc_np, 0.004)
+    clean = c.clean(c.q0, 0.004)
+    assert clean.sum() >= 0.6 * len(clean)
+    assert (ref["N"].sum(axis=1) > 0).sum() >= 5, "workload must exercise contacts"
+    _compare(loss.cpu().numpy(), grad.cpu().numpy(), ref, clean)
+
+
+def test_mixed_grid_and_mesh_scene_four_finger(fg):
+    """Superquadric grids and superquadric meshes in one batch, 4-finger hand."""
+    w = synth.batched_superquadric_workload(n_obj=2, per_obj=10, grid_n=48, points_per_link=32, steps=50,
+                                            device="cuda")
+    rng = np.random.default_rng(5)
+    objects = list(w.objects) + [SM.random_superquadric_mesh(rng, 16, 32), SM.random_superquadric_mesh(rng, 16, 32)]
+    oc = np.concatenate([w.obj_of_cand, w.obj_of_cand + 2])
+    q0 = np.concatenate([w.q0, w.q0])
+    c = Case(fg, w.hand, objects, oc, q0, w.params)
+    r = O.dilation_radius(c.S.prm, 5, w.steps)
+    loss, grad = fg.loss_and_grad(c.hand, c.scene, torch.tensor(q0, device=_dev()), w.params, r, obj_of_cand=c.oc)
+    ref = O.batch_loss_and_grad(c.S, q0, oc, r)
+    clean = c.clean(q0, r)
+    assert clean.sum() >= 0.5 * len(clean)
+    _compare(loss.cpu().numpy(), grad.cpu().numpy(), ref, clean)
+
+
+def test_mesh_optimize_step_every_configuration(fg, sphere_case):
+    c = sphere_case
+    K = 20
+    r = O.dilation_radius(c.S.prm, 0, K)
+    ref = O.batch_loss_and_grad(c.S, c.q0, c.oc_np, r)
+    clean = c.clean(c.q0, r)
+    q0 = torch.tensor(c.q0, device=_dev())
+    try:
+        for i in range(len(fg.fused_configs())):
+            fg.fused_config_select(i)
+            q1 = q0.clone()
+            loss = fg.optimize_step(c.hand, c.scene, q1, c.params, 0, K, 1, obj_of_cand=c.oc)
+            step = (q1 - q0).cpu().numpy().astype(np.float64) / -c.params["lr"]
+            _compare(loss.cpu().numpy(), step, ref, clean)
+    finally:
+        fg.fused_config_select(-1)
+    # contact wrench on a mesh scene runs (counts match the oracle's flags on clean candidates)
+    W, N, _ = fg.contact_wrench(c.hand, c.scene, q0, c.params, r, obj_of_cand=c.oc)
+    Nn = N.cpu().numpy()
+    for b in np.nonzero(clean)[0]:
+        assert np.array_equal(Nn[b], ref["N"][b].astype(np.int32)), b
+
+
+def test_mesh_scenes_refused_where_unsupported(fg, sphere_case):
+    from paper_2306_08132_gb300 import _lib
+    c = sphere_case
+    q = torch.tensor(c.q0[:4], device=_dev())
+    with pytest.raises(_lib.FgError):
+        fg.loss_and_grad(c.hand, c.scene, q, dict(c.params, sim_steps=1), 0.004)
+    with pytest.raises(_lib.FgError):
+        fg.optimize_step_plain(c.hand, c.scene, q.clone(), c.params, 0, 10, 1)
