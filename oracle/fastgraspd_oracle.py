@@ -17,7 +17,8 @@ What it computes, step by step, in the paper's order (Sec. III-C, Sec. IV-A):
             C = max(0, -phi) (Sec. III-C) on the plane through the query, and the
             single-constraint projection of Eq. (1) with J = [n^T, (d x n)^T];
             Coulomb friction at position level; corrections averaged over the
-            active contacts (Jacobi reading of the Gauss-Seidel step).
+            active contacts (Jacobi reading of the Gauss-Seidel step; ``evaluate_gs``
+            projects them one after another in point order instead).
   Loss      L_stable of Eq. (2), L_range (Eq. 3), L_limit (Eq. 4) and an optional
             penetration sum; L = L_stable + w_r L_range + w_l L_limit + w_pen L_pen.
   Gradient  reverse mode (torch autograd in float64) with the paper's leaky rule:
@@ -102,6 +103,7 @@ class Params:
     w_pen: float = 0.0
     schedule: str = "fixed"
     sim_steps: int = 0          # 0: one step, plane-linearised query; T >= 1: T steps, re-queried
+    gauss_seidel: int = 0       # 0: Jacobi-averaged corrections; 1: Gauss-Seidel in point order (one step)
 
     @staticmethod
     def from_dict(d: dict) -> "Params":
@@ -493,11 +495,143 @@ def evaluate_tstep(hand: Hand, obj: Obj, q: torch.Tensor, r: float, prm: Params,
             "points": p, "dec": dec, "trace": trace}
 
 
+@dataclass
+class GSDecisions:
+    """Branches of the Gauss-Seidel form (per point and simulation unless noted)."""
+    sdf: dict = None
+    grad_nz: torch.Tensor = None     # [B,P]
+    kappa: torch.Tensor = None       # [B,P,M]
+    has_t: torch.Tensor = None       # [B,P,M]
+    static: torch.Tensor = None      # [B,P,M]
+    anchor: torch.Tensor = None      # [B,P,M] leak surrogate: phi_m at the decision state
+    state: torch.Tensor = None       # [B,P,M,6] (dx, dth) before each point at the decision state
+    v_nz: torch.Tensor = None
+    w_nz: torch.Tensor = None
+    range_nz: torch.Tensor = None
+    above: torch.Tensor = None
+    below: torch.Tensor = None
+
+
+def evaluate_gs(hand: Hand, obj: Obj, q: torch.Tensor, r: float, prm: Params,
+                dec: GSDecisions | None = None, anchor_mode: bool = False) -> dict:
+    """The one-step grasp metric with the constraints projected by a Gauss-Seidel
+    sweep (Sec. III-C: the update of Eq. (1) for each constraint, applied in turn).
+
+    Everything up to the constraint is the one-step form of ``evaluate``: FK, one SDF
+    query per point, the plane through it, the 7 test velocities.  Each simulation
+    keeps a correction state (dx, dth), zero at the predicted pose x~ = dt v_m, and
+    visits the hand points in index order.  Point i sees the object's material
+    point at p_i displaced by D = dt v_m + dx + dth x d (d = p_i - x~, the lever
+    held at the predicted pose), so
+        phi_m  = phi_hat_i - n_i . D,         C = max(0, -phi_m),
+        lambda_n = C / w_n (Eq. 1),           Coulomb friction on s = D - (D . n) n,
+    exactly the per-point correction of the Jacobi form evaluated at the current
+    state, and the correction M^-1 [f; d x f] is added to the state in full (no
+    averaging).  x_dot+ = v_m + dx / dt, theta_dot+ = dth / dt and the loss follow
+    Eqs. (2)-(4).
+
+    Leaky rule (Sec. III-C states the biased derivative of C with respect to the hand
+    point): outside contact C = -alpha (phi_m - anchor) is taken through the hand
+    point only; the state that earlier projections left is held constant in it, so a
+    non-contact constraint neither moves the state nor passes gradient between
+    states (its exact derivative with respect to the state is 0).  With a frozen
+    ``dec`` and ``anchor_mode`` that state is the one recorded at the decision point,
+    which makes the leaky gradient the exact gradient of the frozen surrogate."""
+    take = dec is None
+    if take:
+        dec = GSDecisions()
+    B = q.shape[0]
+    P = hand.P
+    R, o = forward_kinematics(hand, q)
+    p = hand_points(hand, R, o)                                      # [B,P,3]
+    if take:
+        dec.sdf = sdf_decisions(obj, p)
+    phi, grad = sdf_eval(obj, p, dec.sdf)
+    phi_hat = phi - r
+    if take:
+        dec.grad_nz = (grad.detach() * grad.detach()).sum(-1) > 0
+    gnorm = _safe_norm(grad, dec.grad_nz)
+    nrm = grad / torch.where(dec.grad_nz, gnorm, torch.ones_like(gnorm))[..., None]
+
+    V = torch.tensor(TEST_DIRECTIONS, dtype=F64) * prm.v_test         # [M,3]
+    x_pred = (prm.dt * V)[None]                                       # [1,M,3]
+    alpha = prm.alpha_leak
+    if take:
+        dec.kappa = torch.zeros(B, P, M_SIMS, dtype=torch.bool)
+        dec.has_t = torch.zeros(B, P, M_SIMS, dtype=torch.bool)
+        dec.static = torch.zeros(B, P, M_SIMS, dtype=torch.bool)
+        dec.anchor = torch.zeros(B, P, M_SIMS, dtype=F64)
+        dec.state = torch.zeros(B, P, M_SIMS, 6, dtype=F64)
+    dx = torch.zeros(B, M_SIMS, 3, dtype=F64)
+    dth = torch.zeros(B, M_SIMS, 3, dtype=F64)
+    Wsum = torch.zeros(B, M_SIMS, 6, dtype=F64)
+    phi_ms, Cs, sigs = [], [], []
+    for i in range(P):
+        n_ = nrm[:, i, None, :].expand(B, M_SIMS, 3)
+        d = p[:, i, None, :] - x_pred                                 # [B,M,3]
+        Dsp = x_pred + dx + _cross(dth, d)                            # material point's displacement
+        phi_m = phi_hat[:, i, None] - _dot(n_, Dsp)                   # [B,M]
+        if take:
+            dec.state[:, i] = torch.cat([dx, dth], -1).detach()
+            dec.kappa[:, i] = phi_m.detach() < 0
+        if anchor_mode:
+            st = dec.state[:, i].clone()
+            dx_c, dth_c = st[..., :3], st[..., 3:]
+        else:
+            dx_c, dth_c = dx.detach(), dth.detach()
+        phi_p = phi_hat[:, i, None] - _dot(n_, x_pred + dx_c + _cross(dth_c, d))
+        if take:
+            dec.anchor[:, i] = phi_p.detach()
+        anchor = dec.anchor[:, i].clone() if anchor_mode else phi_p.detach()
+        kap = dec.kappa[:, i].clone()           # copies: the decision tables are filled in place
+        C = torch.where(kap, -phi_m, -alpha * (phi_p - anchor))
+        u_n = _cross(d, n_)
+        w_n = obj.inv_mass + obj.inv_inertia * _dot(u_n, u_n)
+        lam_n = C / w_n
+        s = Dsp - _dot(Dsp, n_)[..., None] * n_                       # tangential displacement
+        if take:
+            dec.has_t[:, i] = (s.detach() * s.detach()).sum(-1) > 0
+        ht = dec.has_t[:, i].clone()
+        sig = _safe_norm(s, ht)
+        t_hat = s / torch.where(ht, sig, torch.ones_like(sig))[..., None]
+        u_t = _cross(d, t_hat)
+        w_t = obj.inv_mass + obj.inv_inertia * _dot(u_t, u_t)
+        if take:
+            dec.static[:, i] = sig.detach() <= prm.mu * C.detach()
+        stat = dec.static[:, i].clone()
+        lam_t = torch.where(ht, torch.where(stat, sig, prm.mu * C) / w_t, torch.zeros_like(sig))
+        f = -(lam_n[..., None] * n_ + lam_t[..., None] * t_hat)       # [B,M,3]
+        tq = _cross(d, f)
+        dx = dx + obj.inv_mass * f
+        dth = dth + obj.inv_inertia * tq
+        Wsum = Wsum + torch.cat([f, tq], -1)
+        phi_ms.append(phi_m)
+        Cs.append(C)
+        sigs.append(sig)
+    xdot = V[None] + dx / prm.dt
+    thdot = dth / prm.dt
+    if take:
+        dec.v_nz = (xdot.detach() ** 2).sum(-1) > 0
+        dec.w_nz = (thdot.detach() ** 2).sum(-1) > 0
+    L_stable = (_safe_norm(xdot, dec.v_nz) + _safe_norm(thdot, dec.w_nz)).sum(-1) / M_SIMS   # Eq. (2)
+    L_range, L_limit = _joint_losses(hand, q, dec)
+    C = torch.stack(Cs, 1)                                            # [B,P,M]
+    L_pen = C[..., 0].sum(-1)
+    L = L_stable + prm.w_range * L_range + prm.w_limit * L_limit + prm.w_pen * L_pen
+    return {"L": L, "L_stable": L_stable, "L_range": L_range, "L_limit": L_limit, "L_pen": L_pen,
+            "W": Wsum, "N": dec.kappa.sum(1).to(F64), "kappa": dec.kappa, "dx": dx, "dth": dth,
+            "points": p, "phi_hat": phi_hat, "grad_phi": grad, "phi_m": torch.stack(phi_ms, 1), "C": C,
+            "sigma": torch.stack(sigs, 1), "dec": dec}
+
+
 def evaluate_any(hand: Hand, obj: Obj, q: torch.Tensor, r: float, prm: Params, dec=None,
                  anchor_mode: bool = False) -> dict:
-    """evaluate (sim_steps = 0) or evaluate_tstep (sim_steps = T >= 1)."""
+    """evaluate (sim_steps = 0), evaluate_gs (sim_steps = 0, gauss_seidel = 1) or
+    evaluate_tstep (sim_steps = T >= 1)."""
     if prm.sim_steps >= 1:
         return evaluate_tstep(hand, obj, q, r, prm, prm.sim_steps, dec=dec, anchor_mode=anchor_mode)
+    if prm.gauss_seidel:
+        return evaluate_gs(hand, obj, q, r, prm, dec=dec, anchor_mode=anchor_mode)
     return evaluate(hand, obj, q, r, prm, dec=dec, anchor_mode=anchor_mode)
 
 
@@ -625,10 +759,31 @@ def guard_margins(hand: Hand, obj: Obj, q32, r: float, prm: Params) -> dict:
     return {"face": face.numpy(), "phi": phim.numpy(), "friction": fr.numpy(), "parallel": par.numpy()}
 
 
+def guard_margins_gs(hand: Hand, obj: Obj, q32, r: float, prm: Params) -> dict:
+    """guard_margins for the Gauss-Seidel form: the same distances, with each point's
+    constraint value, friction regime and tangential direction taken at the state
+    the sweep reaches it with."""
+    with torch.no_grad():
+        q = torch.as_tensor(np.asarray(q32, dtype=np.float64))
+        out = evaluate_gs(hand, obj, q, r, prm)
+        face = _face_margin(obj, out["points"]).amin(dim=(-1, -2))
+        phim = out["phi_m"].abs().amin(dim=(-1, -2))
+        dec = out["dec"]
+        fr = (out["sigma"] - prm.mu * out["C"]).abs()
+        fr = torch.where(dec.kappa & dec.has_t, fr, torch.full_like(fr, float("inf"))).amin(dim=(-1, -2))
+        par = (out["sigma"][..., 1:] / (prm.dt * prm.v_test)).amin(dim=(-1, -2))
+    return {"face": face.numpy(), "phi": phim.numpy(), "friction": fr.numpy(), "parallel": par.numpy()}
+
+
 def clean_candidates(hand: Hand, obj: Obj, q32, r: float, prm: Params, face_tol: float = 1e-5,
                      phi_tol: float = 1e-6, fr_tol: float = 1e-6, par_tol: float = 1e-3) -> np.ndarray:
     """Candidates whose decisions all sit outside the guard band, so that a float32
     evaluation takes the same branches as this float64 one."""
-    m = guard_margins_tstep(hand, obj, q32, r, prm) if prm.sim_steps >= 1 else guard_margins(hand, obj, q32, r, prm)
+    if prm.sim_steps >= 1:
+        m = guard_margins_tstep(hand, obj, q32, r, prm)
+    elif prm.gauss_seidel:
+        m = guard_margins_gs(hand, obj, q32, r, prm)
+    else:
+        m = guard_margins(hand, obj, q32, r, prm)
     return ((m["face"] > face_tol) & (m["phi"] > phi_tol) & (m["friction"] > fr_tol)
             & (m["parallel"] > par_tol))
