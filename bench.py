@@ -251,6 +251,10 @@ def main():
     ap.add_argument("--serving-rate", type=float, default=200.0)
     ap.add_argument("--tstep", default="",
                     help="comma-separated T: also time the T-step metric (SDF re-queried for T steps) on this workload")
+    ap.add_argument("--mesh", action="store_true",
+                    help="also time the fused step on mesh objects (the same superquadrics as watertight meshes, "
+                         "queried through the BVH with the Phong SDF)")
+    ap.add_argument("--mesh-res", default="24,48", help="latitude,longitude divisions of the superquadric meshes")
     ap.add_argument("--serving-sweep", default="",
                     help="comma-separated arrival rates (req/s) for a latency-vs-load sweep of the same stream")
     args = ap.parse_args()
@@ -431,6 +435,28 @@ def main():
             tstep.append({"T": T, "ms_per_step": t_ms, "value": cand_steps / (t_ms / 1000.0),
                           "unit": "candidate-steps/s", "sdf_queries_per_point_step": 2 * 7 * T})
 
+    mesh = None
+    if args.mesh:
+        from synth import meshes as SM
+        n_lat, n_lon = [int(x) for x in args.mesh_res.split(",")]
+        mobjs = []
+        for o in w.objects:
+            pr = o["params"]
+            # exponents held to [0.5, 1.5]: sharper ones fold the pole triangles of a lat/long mesh
+            e1, e2 = [float(np.clip(pr[k], 0.5, 1.5)) for k in ("eps1", "eps2")]
+            mobjs.append(SM.superquadric_mesh(pr["semi_axes"], e1, e2, n_lat, n_lon))
+        mscene = fg.Scene([fg.Sdf.from_synth(m) for m in mobjs])
+
+        def mesh_step():
+            q.copy_(q0)
+            fg.optimize_step(hand, mscene, q, w.params, 0, K, S_in, obj_of_cand=oc, loss=loss)
+
+        mms = timed(graphed(mesh_step), max(3, args.steps // 4), 3)
+        m_ms = max_over_ranks(float(np.mean(mms)), world, dev)
+        mesh = {"ms_per_step": m_ms, "value": cand_steps / (m_ms / 1000.0), "unit": "candidate-steps/s",
+                "objects": "%d superquadric meshes, %d faces each, Phong SDF" % (len(mobjs), len(mobjs[0]["faces"])),
+                "fused_config": "%dw/%d/%dp" % fg.fused_configs()[fg.fused_config_current()]}
+
     serving, sweep = None, None
     if args.serving > 0:
         free, _ = torch.cuda.mem_get_info()
@@ -467,7 +493,7 @@ def main():
                                                             for c, t in zip(cfgs, cfg_ms)}}},
                 "plain": plain, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
                 "latency": None if serving is None else {"p50_s": serving["p50_s"], "p99_s": serving["p99_s"]},
-                "serving": serving, "serving_sweep": sweep, "tstep": tstep,
+                "serving": serving, "serving_sweep": sweep, "tstep": tstep, "mesh": mesh,
                 "gpu_launches": args.steps * 1, "clocks": clocks, "wall_s_timed_region": wall,
                 "per_step_ms": {"min": float(np.min(ms)), "median": float(np.median(ms)), "max": float(np.max(ms))}}
         print(json.dumps(line))

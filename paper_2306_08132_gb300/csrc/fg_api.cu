@@ -420,6 +420,7 @@ fg_status fg_contact_wrench(const fg_hand* h, const fg_scene* sc, const int* oc,
   a.hand_D = h->host.D;
   a.objs = sc->dev;
   a.n_obj = sc->n;
+  a.any_mesh = sc->has_mesh;
   a.obj_of_cand = oc;
   a.q = const_cast<float*>(q);
   a.B = B;
@@ -444,6 +445,7 @@ fg_status fg_loss_and_grad(const fg_hand* h, const fg_scene* sc, const int* oc, 
   a.hand_D = h->host.D;
   a.objs = sc->dev;
   a.n_obj = sc->n;
+  a.any_mesh = sc->has_mesh;
   a.obj_of_cand = oc;
   a.q = const_cast<float*>(q);
   a.B = B;
@@ -472,6 +474,7 @@ fg_status fg_optimize_step(const fg_hand* h, const fg_scene* sc, const int* oc, 
   a.hand_D = h->host.D;
   a.objs = sc->dev;
   a.n_obj = sc->n;
+  a.any_mesh = sc->has_mesh;
   a.obj_of_cand = oc;
   a.q = q;
   a.B = B;
@@ -549,6 +552,7 @@ fg_status fg_autotune(const fg_hand* h, const fg_scene* sc, const int* oc, const
   a.hand_D = h->host.D;
   a.objs = sc->dev;
   a.n_obj = sc->n;
+  a.any_mesh = sc->has_mesh;
   a.obj_of_cand = oc;
   a.q = const_cast<float*>(q);
   a.B = B;

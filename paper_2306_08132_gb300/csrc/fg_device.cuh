@@ -557,11 +557,14 @@ __device__ inline void mesh_lookup(const ObjDev& O, const float p[3], SdfSample&
   s.outside = false;
 }
 
-template <bool kHess>
+// kAnyObj = false compiles the grid lookup alone (callers that only see grids).
+template <bool kHess, bool kAnyObj = true>
 __device__ __forceinline__ void sdf_lookup(const ObjDev& O, const float p[3], SdfSample& s) {
-  if (O.kind == kObjMesh) {
-    mesh_lookup(O, p, s);
-    return;
+  if constexpr (kAnyObj) {
+    if (O.kind == kObjMesh) {
+      mesh_lookup(O, p, s);
+      return;
+    }
   }
   SdfIndex ix;
   sdf_index(O, p, ix);

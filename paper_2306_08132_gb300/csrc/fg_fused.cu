@@ -43,6 +43,13 @@ cudaError_t launch_fused(int mode, const FusedArgs& a, const fg_hand* h, cudaStr
   (void)h;
   if (a.B <= 0) return cudaSuccess;
   const int cfg = fused_config_current();
+  if (a.any_mesh) {
+    switch (mode) {
+      case kModeWrench: return launch_wrench_any(a, st);
+      case kModeLossGrad: return kLossGradLaunchAny[cfg](a, st);
+      default: return kOptimizeLaunchAny[cfg](a, st);
+    }
+  }
   switch (mode) {
     case kModeWrench: return launch_fused_cfg<kModeWrench, 4, 5, 1>(a, st);
     case kModeLossGrad: return kLossGradLaunch[cfg](a, st);
@@ -53,6 +60,7 @@ cudaError_t launch_fused(int mode, const FusedArgs& a, const fg_hand* h, cudaStr
 // One round of a request queue: every active request's candidates in one launch.
 cudaError_t launch_queue_round(const FusedArgs& a, cudaStream_t st) {
   if (a.B <= 0) return cudaSuccess;
+  if (a.any_mesh) return launch_queue_round_any(a, st);
   return launch_fused_cfg<kModeQueue, 4, 5, 1>(a, st);
 }
 
@@ -83,7 +91,7 @@ cudaError_t autotune_fused(const FusedArgs& base, int reps, float* times_ms, int
       e = cudaMemcpyAsync(qtmp, base.q, sizeof(float) * (size_t)base.B * D, cudaMemcpyDeviceToDevice, st);
       if (e != cudaSuccess) break;
       cudaEventRecord(t0, st);
-      e = kOptimizeLaunch[i](a, st);
+      e = (base.any_mesh ? kOptimizeLaunchAny : kOptimizeLaunch)[i](a, st);
       cudaEventRecord(t1, st);
       if (e == cudaSuccess) e = cudaEventSynchronize(t1);
       float ms = 0.0f;

@@ -101,6 +101,7 @@ __device__ __forceinline__ void world_point(const float4* f4, const float4& sp, 
 
 // Adjoint of one hand point (index i, link frames in smem): dL/dp through the 7
 // simulations, the normal and the SDF lookup.  v = (g, (p - t0) x g).
+template <bool ANY>
 __device__ __forceinline__ void point_adjoint(const HandDev& H, const float4 (*frame4)[3], const SimAdjoints& G,
                                               const SimConsts& K, const ObjDev& O,
                                               const ParamsDev& Pm, float r, const float t0[3], int i, bool valid,
@@ -110,7 +111,7 @@ __device__ __forceinline__ void point_adjoint(const HandDev& H, const float4 (*f
   float p[3];
   world_point(frame4[link], sp, p);
   SdfSample smp;
-  sdf_lookup<true>(O, p, smp);
+  sdf_lookup<true, ANY>(O, p, smp);
   PointState ps;
   point_state(smp, p, r, ps);
   float dphi = 0.0f, dn[3] = {0.0f, 0.0f, 0.0f}, dp[3] = {0.0f, 0.0f, 0.0f};
@@ -130,6 +131,7 @@ __device__ __forceinline__ void point_adjoint(const HandDev& H, const float4 (*f
 
 // The same for two points (a, b) at once, in packed f32x2 arithmetic: positions
 // and grid indices per point, everything after the corner gathers on pairs.
+template <bool ANY>
 __device__ __forceinline__ void point_adjoint_pair(const HandDev& H, const float4 (*frame4)[3], const SimAdjoints& G,
                                                    const SimConsts& K, const ObjDev& O, const ParamsDev& Pm, float r,
                                                    const float t0[3], int ia, int ib, bool va, bool vb,
@@ -141,7 +143,7 @@ __device__ __forceinline__ void point_adjoint_pair(const HandDev& H, const float
   world_point(frame4[link[0]], sa, pa);
   world_point(frame4[link[1]], sb, pb);
   SdfSampleT<float2> smp;
-  if (O.kind == kObjMesh) {
+  if (ANY && O.kind == kObjMesh) {
     SdfSample sa, sb;
     mesh_lookup(O, pa, sa);
     mesh_lookup(O, pb, sb);
@@ -253,7 +255,8 @@ __device__ __forceinline__ void link_accumulate(float (*lacc)[6], int lane, int 
   for (int k = 0; k < 6; ++k) acc[k] = 0.0f;
 }
 
-template <int MODE, int NW, int MINB, int PPT>
+// ANY = false: grid objects only (the mesh lookup is compiled out).
+template <int MODE, int NW, int MINB, int PPT, bool ANY>
 __global__ void __launch_bounds__(NW * 32, MINB) fused_step_kernel(FusedArgs a) {
   __shared__ FusedSmem<NW> S;
   constexpr bool kOpt = MODE == kModeOptimize || MODE == kModeQueue;
@@ -406,7 +409,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) fused_step_kernel(FusedArgs a) 
           float p[3];
           world_point(S.frame4[(int)sp.w], sp, p);
           SdfSample smp;
-          sdf_lookup<false>(O, p, smp);
+          sdf_lookup<false, ANY>(O, p, smp);
           PointState ps;
           point_state(smp, p, r, ps);
 #pragma unroll
@@ -538,7 +541,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) fused_step_kernel(FusedArgs a) 
               float v[2][6];
               int link[2];
               const bool va = lane < U.y, vb = lane + 32 < U.y;
-              point_adjoint_pair(H, S.frame4, S.G, S.K, O, Pm, r, t0, va ? U.x + lane : U.x,
+              point_adjoint_pair<ANY>(H, S.frame4, S.G, S.K, O, Pm, r, t0, va ? U.x + lane : U.x,
                                  vb ? U.x + 32 + lane : U.x, va, vb, v, link);
 #pragma unroll
               for (int k = 0; k < 6; ++k) sum[k] = v[0][k] + v[1][k];
@@ -549,7 +552,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) fused_step_kernel(FusedArgs a) 
                 float v[6];
                 int link;
                 const bool valid = h + lane < U.y;
-                point_adjoint(H, S.frame4, S.G, S.K, O, Pm, r, t0, valid ? U.x + h + lane : U.x, valid, v, link);
+                point_adjoint<ANY>(H, S.frame4, S.G, S.K, O, Pm, r, t0, valid ? U.x + h + lane : U.x, valid, v, link);
 #pragma unroll
                 for (int k = 0; k < 6; ++k) sum[k] += v[k];
               }
@@ -566,7 +569,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) fused_step_kernel(FusedArgs a) 
             int link;
             const int i = base + lane;
             const bool valid = i < pe;
-            point_adjoint(H, S.frame4, S.G, S.K, O, Pm, r, t0, valid ? i : base, valid, v, link);
+            point_adjoint<ANY>(H, S.frame4, S.G, S.K, O, Pm, r, t0, valid ? i : base, valid, v, link);
             link_accumulate(S.lacc[warp], lane, link, valid, v, cur, acc);
           }
         }
@@ -653,21 +656,21 @@ __global__ void __launch_bounds__(NW * 32, MINB) fused_step_kernel(FusedArgs a) 
 
 // Launch of one compiled configuration: a persistent grid of (SMs x resident
 // CTAs) blocks, capped at B.
-template <int MODE, int NW, int MINB, int PPT>
+template <int MODE, int NW, int MINB, int PPT, bool ANY = false>
 cudaError_t launch_fused_cfg(const FusedArgs& a, cudaStream_t st) {
   static int blocks_per_sm[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
   int& bps = blocks_per_sm[dev & 63];
   if (bps <= 0) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fused_step_kernel<MODE, NW, MINB, PPT>, NW * 32, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fused_step_kernel<MODE, NW, MINB, PPT, ANY>, NW * 32, 0);
     if (e != cudaSuccess) return e;
     if (bps < 1) bps = 1;
   }
   long long grid = (long long)device_sm_count() * bps;
   if (grid > a.B) grid = a.B;
   if (grid < 1) return cudaSuccess;
-  fused_step_kernel<MODE, NW, MINB, PPT><<<(int)grid, NW * 32, 0, st>>>(a);
+  fused_step_kernel<MODE, NW, MINB, PPT, ANY><<<(int)grid, NW * 32, 0, st>>>(a);
   return cudaGetLastError();
 }
 

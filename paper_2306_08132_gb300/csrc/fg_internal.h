@@ -73,9 +73,15 @@ struct FusedArgs {
   int hand_D;
   const QueueSlotDev* slots;   // queue mode: slot table (device), sorted by cand_start
   int nslots;
+  int any_mesh;                // some object is a mesh: the kernels with the mesh lookup
 };
 typedef cudaError_t (*FusedLaunchFn)(const FusedArgs&, cudaStream_t);
+// Compiled configurations: grid objects only, and any object (grids and meshes).
 extern const FusedLaunchFn kOptimizeLaunch[];
+extern const FusedLaunchFn kOptimizeLaunchAny[];
+extern const FusedLaunchFn kLossGradLaunchAny[];
+cudaError_t launch_wrench_any(const FusedArgs& a, cudaStream_t st);
+cudaError_t launch_queue_round_any(const FusedArgs& a, cudaStream_t st);
 cudaError_t launch_fused(int mode, const FusedArgs& a, const fg_hand* h, cudaStream_t st);
 // T-step metric (params.sim_steps >= 1): loss and gradient, or optimisation steps (fg_tstep.cu)
 cudaError_t launch_tstep(int mode, const FusedArgs& a, cudaStream_t st);

@@ -118,7 +118,7 @@ __global__ void sdf_stage_kernel(const HandDev* __restrict__ Hp, const ObjDev* _
     const ObjDev O = *obj_for(objs, n_obj, oc, b);
     float p[3] = {pts[idx], pts[BP + idx], pts[2 * BP + idx]};
     SdfSample s;
-    sdf_lookup<true>(O, p, s);
+    sdf_lookup<true, false>(O, p, s);   // the per-stage form takes grid objects only
     float v[kSampleFloats] = {s.phi, s.g[0], s.g[1], s.g[2], s.hxy, s.hxz, s.hyz, s.eh[0], s.eh[1], s.eh[2], s.e};
 #pragma unroll
     for (int k = 0; k < kSampleFloats; ++k) smp[k * BP + idx] = v[k];

@@ -174,6 +174,7 @@ void scheduler(fg_queue* Q) {
     a.B = total;
     a.slots = Q->d_slots;
     a.nslots = n;
+    for (int i = 0; i < n; ++i) a.any_mesh |= Q->h_slots[i].obj.kind == fg::kObjMesh;
     if (e == cudaSuccess) e = fg::launch_queue_round(a, Q->stream);
     if (e == cudaSuccess) e = cudaEventRecord(Q->event, Q->stream);
     lock.unlock();

@@ -389,7 +389,7 @@ __global__ void __launch_bounds__(kTW * 32, 4) tstep_kernel(FusedArgs a) {
             world_point(S.frame4[(int)sp.w], sp, p);
             step_query(st, p, d, r);
             SdfSample smp;
-            sdf_lookup<false>(O, r, smp);
+            sdf_lookup<false, false>(O, r, smp);   // grid objects only
             PointState ps;
             point_state(smp, r, rdil, ps);
             const bool kap = valid && ps.phi_hat < 0.0f;
