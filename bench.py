@@ -37,6 +37,8 @@ FLOPS_PER_POINT_STEP = 2092
 # The fused kernel's own minimal count for a point out of contact (forward once +
 # leaky adjoint once, FMA = 2), reported beside it.
 KERNEL_MIN_FLOPS_PER_POINT_STEP = 599
+# The same count for the Gauss-Seidel form (oracle counting instantiation, this workload).
+GS_FLOPS_PER_POINT_STEP = 2540
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 METRIC = "candidate-steps/sec fused fwd+bwd vs plain GPU form at 1e-3 grad tol; p50/p99 latency"
@@ -251,6 +253,8 @@ def main():
     ap.add_argument("--serving-rate", type=float, default=200.0)
     ap.add_argument("--tstep", default="",
                     help="comma-separated T: also time the T-step metric (SDF re-queried for T steps) on this workload")
+    ap.add_argument("--gs", action="store_true",
+                    help="also time the Gauss-Seidel form (constraints projected in point order) on this workload")
     ap.add_argument("--mesh", action="store_true",
                     help="also time the fused step on mesh objects (the same superquadrics as watertight meshes, "
                          "queried through the BVH with the Phong SDF)")
@@ -435,6 +439,20 @@ def main():
             tstep.append({"T": T, "ms_per_step": t_ms, "value": cand_steps / (t_ms / 1000.0),
                           "unit": "candidate-steps/s", "sdf_queries_per_point_step": 2 * 7 * T})
 
+    gs = None
+    if args.gs:
+        pG = dict(w.params, gauss_seidel=1)
+
+        def gs_step():
+            q.copy_(q0)
+            fg.optimize_step(hand, scene, q, pG, 0, K, S_in, obj_of_cand=oc, loss=loss)
+
+        gms = timed(graphed(gs_step), max(3, args.steps // 4), 3)
+        g_ms = max_over_ranks(float(np.mean(gms)), world, dev)
+        gs = {"ms_per_step": g_ms, "value": cand_steps / (g_ms / 1000.0), "unit": "candidate-steps/s",
+              "flops_per_point_step": GS_FLOPS_PER_POINT_STEP,
+              "achieved_tflops": GS_FLOPS_PER_POINT_STEP * w.B * w.hand["P"] * S_in / (g_ms / 1000.0) / 1e12}
+
     mesh = None
     if args.mesh:
         from synth import meshes as SM
@@ -493,7 +511,7 @@ def main():
                                                             for c, t in zip(cfgs, cfg_ms)}}},
                 "plain": plain, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
                 "latency": None if serving is None else {"p50_s": serving["p50_s"], "p99_s": serving["p99_s"]},
-                "serving": serving, "serving_sweep": sweep, "tstep": tstep, "mesh": mesh,
+                "serving": serving, "serving_sweep": sweep, "tstep": tstep, "gauss_seidel": gs, "mesh": mesh,
                 "gpu_launches": args.steps * 1, "clocks": clocks, "wall_s_timed_region": wall,
                 "per_step_ms": {"min": float(np.min(ms)), "median": float(np.median(ms)), "max": float(np.max(ms))}}
         print(json.dumps(line))

@@ -101,6 +101,13 @@ typedef struct {
  *      simulation's predicted object pose of every step (Sec. III-C); accepted
  *      by fg_loss_and_grad and fg_optimize_step only (FG_ERR_INVALID elsewhere). */
 #define FG_MAX_SIM_STEPS 8
+/* gauss_seidel (with sim_steps = 0): 0 = the corrections of all contacts are
+ * taken at the predicted pose and averaged over the active contacts (Jacobi);
+ * 1 = they are projected one after another in point order, each seeing the
+ * object displaced by the corrections before it (Sec. III-C: "a Gauss-Seidel
+ * step" over the constraints of Eq. 1), and applied in full.  Gauss-Seidel is
+ * accepted by fg_loss_and_grad and fg_optimize_step on grid objects, for hands
+ * of at most 8,192 points (FG_ERR_INVALID elsewhere). */
 typedef struct {
   float alpha_leak;
   float dt;
@@ -113,6 +120,7 @@ typedef struct {
   float w_pen;
   int schedule;
   int sim_steps;
+  int gauss_seidel;
 } fg_params;
 
 /* ------------------------------------------------------------------ misc */

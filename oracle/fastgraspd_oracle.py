@@ -566,11 +566,13 @@ def evaluate_gs(hand: Hand, obj: Obj, q: torch.Tensor, r: float, prm: Params,
     dth = torch.zeros(B, M_SIMS, 3, dtype=F64)
     Wsum = torch.zeros(B, M_SIMS, 6, dtype=F64)
     phi_ms, Cs, sigs = [], [], []
+    # per-point views (unbind: the reverse pass gathers their gradients once)
+    p_i, n_i, ph_i = p.unbind(1), nrm.unbind(1), phi_hat.unbind(1)
     for i in range(P):
-        n_ = nrm[:, i, None, :].expand(B, M_SIMS, 3)
-        d = p[:, i, None, :] - x_pred                                 # [B,M,3]
+        n_ = n_i[i][:, None, :].expand(B, M_SIMS, 3)
+        d = p_i[i][:, None, :] - x_pred                               # [B,M,3]
         Dsp = x_pred + dx + _cross(dth, d)                            # material point's displacement
-        phi_m = phi_hat[:, i, None] - _dot(n_, Dsp)                   # [B,M]
+        phi_m = ph_i[i][:, None] - _dot(n_, Dsp)                      # [B,M]
         if take:
             dec.state[:, i] = torch.cat([dx, dth], -1).detach()
             dec.kappa[:, i] = phi_m.detach() < 0
@@ -579,7 +581,7 @@ def evaluate_gs(hand: Hand, obj: Obj, q: torch.Tensor, r: float, prm: Params,
             dx_c, dth_c = st[..., :3], st[..., 3:]
         else:
             dx_c, dth_c = dx.detach(), dth.detach()
-        phi_p = phi_hat[:, i, None] - _dot(n_, x_pred + dx_c + _cross(dth_c, d))
+        phi_p = ph_i[i][:, None] - _dot(n_, x_pred + dx_c + _cross(dth_c, d))
         if take:
             dec.anchor[:, i] = phi_p.detach()
         anchor = dec.anchor[:, i].clone() if anchor_mode else phi_p.detach()

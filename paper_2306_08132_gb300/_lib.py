@@ -35,7 +35,8 @@ class HandDesc(C.Structure):
 class Params(C.Structure):
     _fields_ = [("alpha_leak", C.c_float), ("dt", C.c_float), ("v_test", C.c_float), ("mu", C.c_float),
                 ("lr", C.c_float), ("r0", C.c_float), ("w_range", C.c_float), ("w_limit", C.c_float),
-                ("w_pen", C.c_float), ("schedule", C.c_int), ("sim_steps", C.c_int)]
+                ("w_pen", C.c_float), ("schedule", C.c_int), ("sim_steps", C.c_int),
+                ("gauss_seidel", C.c_int)]
 
 
 class QueueOpts(C.Structure):

@@ -42,7 +42,8 @@ def make_params(d: dict) -> _lib.Params:
         sched = {"fixed": 0, "linear": 1}[sched]
     return _lib.Params(float(d["alpha_leak"]), float(d["dt"]), float(d["v_test"]), float(d["mu"]),
                        float(d["lr"]), float(d["r0"]), float(d["w_range"]), float(d["w_limit"]),
-                       float(d["w_pen"]), int(sched), int(d.get("sim_steps", 0)))
+                       float(d["w_pen"]), int(sched), int(d.get("sim_steps", 0)),
+                       int(d.get("gauss_seidel", 0)))
 
 
 class Hand:

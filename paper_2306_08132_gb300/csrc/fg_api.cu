@@ -50,6 +50,7 @@ ParamsDev params_from(const fg_params* p) {
   d.w_pen = p->w_pen;
   d.schedule = p->schedule;
   d.sim_steps = p->sim_steps;
+  d.gauss_seidel = p->gauss_seidel;
   return d;
 }
 
@@ -70,6 +71,9 @@ static fg_status check_params(const fg_params* p) {
   if (p->schedule != 0 && p->schedule != 1) return invalid("params.schedule must be 0 or 1");
   if (p->sim_steps < 0 || p->sim_steps > FG_MAX_SIM_STEPS)
     return invalid("params.sim_steps must be in [0, FG_MAX_SIM_STEPS]");
+  if (p->gauss_seidel != 0 && p->gauss_seidel != 1) return invalid("params.gauss_seidel must be 0 or 1");
+  if (p->gauss_seidel && p->sim_steps != 0)
+    return invalid("params.gauss_seidel needs sim_steps = 0 (the one-step metric)");
   return FG_OK;
 }
 
@@ -403,6 +407,17 @@ static fg_status check_one_step(const char* fn, const fg_params* p) {
   if (p->sim_steps != 0)
     return invalid(std::string(fn) + ": params.sim_steps must be 0 here (T-step metric: fg_loss_and_grad, "
                    "fg_optimize_step)");
+  if (p->gauss_seidel != 0)
+    return invalid(std::string(fn) + ": params.gauss_seidel must be 0 here (Gauss-Seidel form: fg_loss_and_grad, "
+                   "fg_optimize_step)");
+  return FG_OK;
+}
+
+// The Gauss-Seidel form: grid objects, hands whose chunks fit the kernel's tables.
+static fg_status check_gs(const char* fn, const fg_hand* h, const fg_scene* sc) {
+  if (sc->has_mesh) return invalid(std::string(fn) + ": the Gauss-Seidel form takes grid objects only");
+  if (h->host.nchunks > kMaxCullChunks)
+    return invalid(std::string(fn) + ": the Gauss-Seidel form takes hands of at most 8,192 points");
   return FG_OK;
 }
 
@@ -458,6 +473,12 @@ fg_status fg_loss_and_grad(const fg_hand* h, const fg_scene* sc, const int* oc, 
     if (sc->has_mesh) return invalid("fg_loss_and_grad: the T-step metric takes grid objects only");
     return cuda_status(launch_tstep(kModeLossGrad, a, (cudaStream_t)stream), "fg_loss_and_grad (T-step)");
   }
+  if (a.P.gauss_seidel) {
+    st = check_gs("fg_loss_and_grad", h, sc);
+    if (st != FG_OK) return st;
+    return cuda_status(launch_gs(kModeLossGrad, a, h->host.nchunks, (cudaStream_t)stream),
+                       "fg_loss_and_grad (Gauss-Seidel)");
+  }
   return cuda_status(launch_fused(kModeLossGrad, a, h, (cudaStream_t)stream), "fg_loss_and_grad");
 }
 
@@ -486,6 +507,12 @@ fg_status fg_optimize_step(const fg_hand* h, const fg_scene* sc, const int* oc, 
   if (a.P.sim_steps >= 1) {
     if (sc->has_mesh) return invalid("fg_optimize_step: the T-step metric takes grid objects only");
     return cuda_status(launch_tstep(kModeOptimize, a, (cudaStream_t)stream), "fg_optimize_step (T-step)");
+  }
+  if (a.P.gauss_seidel) {
+    st = check_gs("fg_optimize_step", h, sc);
+    if (st != FG_OK) return st;
+    return cuda_status(launch_gs(kModeOptimize, a, h->host.nchunks, (cudaStream_t)stream),
+                       "fg_optimize_step (Gauss-Seidel)");
   }
   return cuda_status(launch_fused(kModeOptimize, a, h, (cudaStream_t)stream), "fg_optimize_step");
 }

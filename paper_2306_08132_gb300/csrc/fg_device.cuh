@@ -76,6 +76,7 @@ struct ParamsDev {
   float alpha, dt, V, mu, lr, r0, w_range, w_limit, w_pen;
   int schedule;
   int sim_steps;                 // 0: one plane-linearised step; T >= 1: T re-queried steps
+  int gauss_seidel;              // 1: constraints projected one after another in point order
 };
 
 // -------------------------------------------------------------------- rounding

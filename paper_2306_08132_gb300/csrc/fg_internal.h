@@ -85,6 +85,8 @@ cudaError_t launch_queue_round_any(const FusedArgs& a, cudaStream_t st);
 cudaError_t launch_fused(int mode, const FusedArgs& a, const fg_hand* h, cudaStream_t st);
 // T-step metric (params.sim_steps >= 1): loss and gradient, or optimisation steps (fg_tstep.cu)
 cudaError_t launch_tstep(int mode, const FusedArgs& a, cudaStream_t st);
+// Gauss-Seidel form (params.gauss_seidel = 1): loss and gradient, or optimisation steps (fg_gs.cu)
+cudaError_t launch_gs(int mode, const FusedArgs& a, int nchunks, cudaStream_t st);
 int fused_config_count();
 void fused_config_info(int i, int* nw, int* minb, int* ppt);
 int fused_config_current();

@@ -68,8 +68,8 @@ extern "C" fg_status fg_optimize_step_plain_noalloc(const fg_hand* h, const fg_s
   }
   if (!(p->dt > 0.0f) || !std::isfinite(p->dt) || !(p->v_test >= 0.0f) || !(p->mu >= 0.0f) ||
       !(p->alpha_leak >= 0.0f && p->alpha_leak <= 1.0f) || !(p->r0 >= 0.0f) || !std::isfinite(p->lr) ||
-      (p->schedule != 0 && p->schedule != 1) || p->sim_steps != 0) {
-    set_error("fg_optimize_step_plain_noalloc: invalid params (sim_steps must be 0)");
+      (p->schedule != 0 && p->schedule != 1) || p->sim_steps != 0 || p->gauss_seidel != 0) {
+    set_error("fg_optimize_step_plain_noalloc: invalid params (sim_steps and gauss_seidel must be 0)");
     return FG_ERR_INVALID;
   }
   if (sc->has_mesh) {

@@ -285,6 +285,7 @@ fg_status fg_queue_submit(fg_queue* Q, const fg_request* r, uint64_t* id) {
       !(p.r0 >= 0.0f) || (p.schedule != 0 && p.schedule != 1))
     return qinvalid("fg_queue_submit: invalid params");
   if (p.sim_steps != 0) return qinvalid("fg_queue_submit: params.sim_steps must be 0 (one-step metric)");
+  if (p.gauss_seidel != 0) return qinvalid("fg_queue_submit: params.gauss_seidel must be 0 (Jacobi form)");
   const int D = r->hand->host.D;
   const size_t state = sizeof(float) * (size_t)r->B * (D + 1);
   if (state + sdf_bytes(r->sdf) > Q->budget) {
