@@ -45,3 +45,10 @@ def sample_candidates(rng: np.random.Generator, hand: dict, n: int, radius: floa
     lo, hi = hand["q_low"].astype(np.float64), hand["q_up"].astype(np.float64)
     th = lo[None, :] + (hi - lo)[None, :] * rng.random((n, hand["J"]))
     return np.concatenate([t, w, th], axis=1).astype(np.float32)
+
+
+def unit_directions(n: int, dim: int = 6, seed: int = 2306081320) -> np.ndarray:
+    """n seeded directions uniform on the unit sphere of R^dim (normalised Gaussians), float32."""
+    rng = np.random.default_rng(seed)
+    g = rng.normal(size=(n, dim))
+    return (g / np.linalg.norm(g, axis=1, keepdims=True)).astype(np.float32)

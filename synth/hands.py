@@ -108,6 +108,26 @@ def box_points(half, n: int) -> np.ndarray:
     return np.array(pts, dtype=np.float64)
 
 
+def box_point_areas(half, n: int) -> np.ndarray:
+    """Area each sample of ``box_points(half, n)`` stands for (its face's area over
+    the face's sample count), in the same order."""
+    hx, hy, hz = half
+    areas = []
+    for u_half, v_half in ((hy, hz), (hx, hz), (hx, hy)):
+        areas += [4.0 * u_half * v_half] * 2
+    areas = np.array(areas)
+    raw = areas / areas.sum() * n
+    counts = np.floor(raw).astype(int)
+    rem = n - counts.sum()
+    for idx in np.argsort(-(raw - counts), kind="stable")[:rem]:
+        counts[idx] += 1
+    return np.concatenate([np.full(k, a / k) for a, k in zip(areas, counts) if k > 0])
+
+
+def capsule_area(length: float, radius: float) -> float:
+    return 2.0 * math.pi * radius * length + 4.0 * math.pi * radius * radius
+
+
 def _morton_order(pts: np.ndarray) -> np.ndarray:
     """Order of points along a Morton (Z-order) curve of their 10-bit quantised
     coordinates, so that consecutive points are spatially close."""
@@ -193,14 +213,18 @@ def make_hand(kind: int, points_per_link: int) -> dict:
     q_low = np.array([specs[l][6][0] for l in range(1, L)], dtype=np.float32)
     q_up = np.array([specs[l][6][1] for l in range(1, L)], dtype=np.float32)
 
-    local, link_of_point, link_start = [], [], [0]
+    local, link_of_point, link_start, areas = [], [], [0], []
     for l, s in enumerate(specs):
         shape = s[5]
         if shape[0] == "box":
             pts = box_points(shape[1], points_per_link)
+            w = box_point_areas(shape[1], points_per_link)
         else:
             pts = capsule_points(shape[1], CAPSULE_RADIUS, points_per_link)
-        pts = pts[_morton_order(pts)]          # spatially coherent runs of 32 points
+            w = np.full(len(pts), capsule_area(shape[1], CAPSULE_RADIUS) / len(pts))
+        order = _morton_order(pts)             # spatially coherent runs of 32 points
+        pts = pts[order]
+        areas.append(w[order])
         local.append(pts)
         link_of_point.extend([l] * len(pts))
         link_start.append(link_start[-1] + len(pts))
@@ -222,4 +246,42 @@ def make_hand(kind: int, points_per_link: int) -> dict:
         "link_of_point": lop,
         "link_start": np.array(link_start, dtype=np.int32),
         "rest_R": rest_R, "rest_o": rest_o, "rest_pts": rest_pts,
+        "point_area": np.concatenate(areas).astype(np.float32),     # m^2 each surface sample stands for
     }
+
+
+def interior_hand(kind: int, spacing: float) -> dict:
+    """The same hand with its links' interiors sampled instead of their surfaces: a
+    cubic lattice of the given spacing (metres) in each link frame, the nodes inside
+    the capsule (or palm box), each standing for spacing^3 of volume (``point_volume``).
+    Links overlap at the joints; each link keeps its own samples."""
+    base = make_hand(kind, 8)
+    specs = _layout(kind)
+    local, lop, vol = [], [], []
+    for l, s in enumerate(specs):
+        shape = s[5]
+        if shape[0] == "box":
+            h = np.asarray(shape[1])
+            axes = [np.arange(-h[k] + 0.5 * spacing, h[k], spacing) for k in range(3)]
+            X, Y, Z = np.meshgrid(*axes, indexing="ij")
+            pts = np.stack([X.ravel(), Y.ravel(), Z.ravel()], -1)
+        else:
+            ln, r = shape[1], CAPSULE_RADIUS
+            ax = np.arange(-r + 0.5 * spacing, r, spacing)
+            ay = np.arange(-r + 0.5 * spacing, ln + r, spacing)
+            X, Y, Z = np.meshgrid(ax, ay, ax, indexing="ij")
+            pts = np.stack([X.ravel(), Y.ravel(), Z.ravel()], -1)
+            yc = np.clip(pts[:, 1], 0.0, ln)
+            inside = (pts[:, 0] ** 2 + (pts[:, 1] - yc) ** 2 + pts[:, 2] ** 2) <= r * r
+            pts = pts[inside]
+        pts = pts[_morton_order(pts)]
+        local.append(pts)
+        lop.extend([l] * len(pts))
+        vol.append(np.full(len(pts), spacing ** 3))
+    out = dict(base)
+    pts_local = np.concatenate(local).astype(np.float32)
+    out.update({"P": int(len(lop)), "pts_local": pts_local, "link_of_point": np.array(lop, dtype=np.int32),
+                "point_volume": np.concatenate(vol).astype(np.float32)})
+    for key in ("point_area", "rest_pts", "link_start"):
+        out.pop(key, None)
+    return out
