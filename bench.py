@@ -255,6 +255,9 @@ def main():
                     help="comma-separated T: also time the T-step metric (SDF re-queried for T steps) on this workload")
     ap.add_argument("--gs", action="store_true",
                     help="also time the Gauss-Seidel form (constraints projected in point order) on this workload")
+    ap.add_argument("--quality", action="store_true",
+                    help="also time the grasp-quality metrics (contact area, epsilon over 1,024 directions) "
+                         "over the workload's candidates")
     ap.add_argument("--mesh", action="store_true",
                     help="also time the fused step on mesh objects (the same superquadrics as watertight meshes, "
                          "queried through the BVH with the Phong SDF)")
@@ -305,6 +308,26 @@ def main():
             for _ in range(3):
                 q.copy_(q0)
                 fg.optimize_step(hand, scene, q, pT, 0, K, S_in, obj_of_cand=oc, loss=loss)
+        elif args.gs:                        # the Gauss-Seidel kernel
+            pG = dict(w.params, gauss_seidel=1)
+            for _ in range(3):
+                q.copy_(q0)
+                fg.optimize_step(hand, scene, q, pG, 0, K, S_in, obj_of_cand=oc, loss=loss)
+        elif args.mesh:                      # the fused kernel on the superquadrics as meshes
+            from synth import meshes as SM
+            n_lat, n_lon = [int(x) for x in args.mesh_res.split(",")]
+            mobjs = [SM.superquadric_mesh(o["params"]["semi_axes"], float(np.clip(o["params"]["eps1"], 0.5, 1.5)),
+                                          float(np.clip(o["params"]["eps2"], 0.5, 1.5)), n_lat, n_lon)
+                     for o in w.objects]
+            mscene = fg.Scene([fg.Sdf.from_synth(m) for m in mobjs])
+            for _ in range(3):
+                q.copy_(q0)
+                fg.optimize_step(hand, mscene, q, w.params, 0, K, S_in, obj_of_cand=oc, loss=loss)
+        elif args.quality:                   # the epsilon kernel over 1,024 directions
+            import synth as _synth
+            dirs = torch.tensor(_synth.unit_directions(1024), device=dev)
+            for _ in range(3):
+                fg.grasp_epsilon(hand, scene, q0, 0.005, 0.5, 8, 1.0 / 0.08, dirs, obj_of_cand=oc)
         else:
             for _ in range(5):
                 fused_step()
@@ -453,6 +476,29 @@ def main():
               "flops_per_point_step": GS_FLOPS_PER_POINT_STEP,
               "achieved_tflops": GS_FLOPS_PER_POINT_STEP * w.B * w.hand["P"] * S_in / (g_ms / 1000.0) / 1e12}
 
+    quality = None
+    if args.quality:
+        import synth as _synth
+        areas = torch.tensor(w.hand["point_area"], device=dev)
+        dirs = torch.tensor(_synth.unit_directions(1024), device=dev)
+        qeps = torch.empty(w.B, device=dev)
+
+        def ca_step():
+            fg.contact_measure(hand, scene, q0, areas, 0.005, obj_of_cand=oc)
+
+        def eps_step():
+            e, _ = fg.grasp_epsilon(hand, scene, q0, 0.005, 0.5, 8, 1.0 / 0.08, dirs, obj_of_cand=oc)
+            qeps.copy_(e)
+
+        cms = timed(ca_step, max(3, args.steps // 4), 3)
+        ems_ = timed(eps_step, max(3, args.steps // 4), 3)
+        e, nc = fg.grasp_epsilon(hand, scene, q0, 0.005, 0.5, 8, 1.0 / 0.08, dirs, obj_of_cand=oc)
+        ncm = float(nc.float().mean())
+        quality = {"contact_area_ms": float(np.mean(cms)), "epsilon_ms": float(np.mean(ems_)),
+                   "candidates": w.B, "threshold_m": 0.005, "directions": 1024, "cone_edges": 8,
+                   "mean_contacts": ncm,
+                   "epsilon_direction_contact_pairs_per_s": 1024 * ncm * w.B / (float(np.mean(ems_)) / 1000.0)}
+
     mesh = None
     if args.mesh:
         from synth import meshes as SM
@@ -512,6 +558,7 @@ def main():
                 "plain": plain, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
                 "latency": None if serving is None else {"p50_s": serving["p50_s"], "p99_s": serving["p99_s"]},
                 "serving": serving, "serving_sweep": sweep, "tstep": tstep, "gauss_seidel": gs, "mesh": mesh,
+                "quality": quality,
                 "gpu_launches": args.steps * 1, "clocks": clocks, "wall_s_timed_region": wall,
                 "per_step_ms": {"min": float(np.min(ms)), "median": float(np.median(ms)), "max": float(np.max(ms))}}
         print(json.dumps(line))

@@ -323,6 +323,43 @@ fg_status fg_optimize_step_plain_noalloc(const fg_hand* hand, const fg_scene* sc
                                          float* q, int B, const fg_params* host_params, int step,
                                          int total_steps, int nsteps, float* loss, void* stream);
 
+/* ------------------------------------------------------------ grasp quality */
+
+/* Grasp-quality metrics of the evaluation (Sec. V, "Metrics": contact area,
+ * intersection volume and epsilon depend on the distance threshold tau used to
+ * generate contacts; 5 mm for the paper's Table II).  A contact is a hand point
+ * p with phi(p) < tau, phi the undilated SDF of the candidate's object at its
+ * canonical pose (grid or mesh).  Both calls are asynchronous on `stream` and
+ * write NaN (and -1 contacts) for a candidate whose obj_of_cand index is outside
+ * the scene. */
+
+/* Weighted contact measure: out[b] = sum of weights[i] over the hand points i
+ * with phi(p_i(q_b)) < tau.  With the surface samples, the area each stands for
+ * and tau the contact threshold this is the contact area CA; with a hand whose
+ * points sample the links' interiors, their volumes and tau = 0 it is the
+ * intersection volume IV.  weights: device [P] in the hand's point order;
+ * out: device [B].  Errors: FG_ERR_INVALID (NULL buffer, B < 0, non-finite tau). */
+fg_status fg_contact_measure(const fg_hand* hand, const fg_scene* scene, const int* obj_of_cand,
+                             const float* q, int B, const float* weights, float tau, float* out,
+                             void* stream);
+
+/* Epsilon quality over a set of wrench-space directions.  Each contact, with
+ * outward normal n = grad phi / |grad phi|, contributes the cone_edges edges of
+ * its Coulomb cone f_e = -n + mu (cos(2 pi e / k) t1 + sin(2 pi e / k) t2),
+ * (t1, t2) the tangent basis of n by Duff et al. (2017), as the wrenches
+ * w = (f_e, torque_scale * (p - c) x f_e), c the object's origin (its centre of
+ * mass).  eps[b] = min over the K unit directions u of max over all wrenches of
+ * u . w: an upper bound of the Ferrari-Canny epsilon (the distance from the
+ * origin to the boundary of the wrenches' convex hull), equal to it when the
+ * set holds the normal of the hull facet nearest the origin; -infinity without
+ * contacts.  n_contacts (nullable): device [B] contacts found.  dirs: device
+ * [K][6], 1 <= K <= FG_MAX_DIRS; 1 <= cone_edges <= 32; mu >= 0;
+ * torque_scale >= 0 (1 / the object's radius).  Errors: FG_ERR_INVALID. */
+#define FG_MAX_DIRS 8192
+fg_status fg_grasp_epsilon(const fg_hand* hand, const fg_scene* scene, const int* obj_of_cand,
+                           const float* q, int B, float tau, float mu, int cone_edges, float torque_scale,
+                           const float* dirs, int K, float* eps, int* n_contacts, void* stream);
+
 /* ------------------------------------------------------------------ tuning */
 
 /* The fused kernels are compiled in several configurations: warps per

@@ -78,6 +78,8 @@ SIGNATURES = {
     "fg_contact_wrench": [_vp, _vp, _vp, _vp, _i, C.POINTER(Params), _f, _vp, _vp, _vp, _vp],
     "fg_loss_and_grad": [_vp, _vp, _vp, _vp, _i, C.POINTER(Params), _f, _vp, _vp, _vp],
     "fg_optimize_step": [_vp, _vp, _vp, _vp, _i, C.POINTER(Params), _i, _i, _i, _vp, _vp],
+    "fg_contact_measure": [_vp, _vp, _vp, _vp, _i, _vp, _f, _vp, _vp],
+    "fg_grasp_epsilon": [_vp, _vp, _vp, _vp, _i, _f, _f, _i, _f, _vp, _i, _vp, _vp, _vp],
     "fg_plain_workspace_size": [_vp, _i, C.POINTER(C.c_size_t)],
     "fg_optimize_step_plain": [_vp, _vp, _vp, _vp, _i, C.POINTER(Params), _i, _i, _i, _vp, _vp, C.c_size_t, _vp],
     "fg_optimize_step_plain_noalloc": [_vp, _vp, _vp, _vp, _i, C.POINTER(Params), _i, _i, _i, _vp, _vp],

@@ -214,6 +214,36 @@ def optimize_step(hand: Hand, scene: Scene, q: torch.Tensor, params: dict, step:
     return loss
 
 
+def contact_measure(hand: Hand, scene: Scene, q: torch.Tensor, weights: torch.Tensor, tau: float,
+                    obj_of_cand: torch.Tensor | None = None) -> torch.Tensor:
+    """fg_contact_measure: per candidate, the sum of weights[i] over the points with phi < tau
+    (contact area with area weights; intersection volume with interior samples and tau = 0)."""
+    B = q.shape[0]
+    _dptr(q, "q", shape=(B, hand.D))
+    _dptr(weights, "weights", shape=(hand.P,))
+    out = torch.empty(B, device=q.device, dtype=_F32)
+    check(_lib.load().fg_contact_measure(hand.handle, scene.handle, _oc(obj_of_cand, B), _dptr(q, "q"), B,
+                                         _dptr(weights, "weights"), float(tau), _dptr(out, "out"), _stream()),
+          "fg_contact_measure")
+    return out
+
+
+def grasp_epsilon(hand: Hand, scene: Scene, q: torch.Tensor, tau: float, mu: float, cone_edges: int,
+                  torque_scale: float, dirs: torch.Tensor, obj_of_cand: torch.Tensor | None = None):
+    """fg_grasp_epsilon: (eps [B], n_contacts [B] int32) over the unit directions dirs [K, 6]."""
+    B = q.shape[0]
+    _dptr(q, "q", shape=(B, hand.D))
+    K = dirs.shape[0]
+    _dptr(dirs, "dirs", shape=(K, 6))
+    eps = torch.empty(B, device=q.device, dtype=_F32)
+    nc = torch.empty(B, device=q.device, dtype=torch.int32)
+    check(_lib.load().fg_grasp_epsilon(hand.handle, scene.handle, _oc(obj_of_cand, B), _dptr(q, "q"), B,
+                                       float(tau), float(mu), int(cone_edges), float(torque_scale),
+                                       _dptr(dirs, "dirs"), K, _dptr(eps, "eps"),
+                                       _dptr(nc, "n_contacts", dtype=torch.int32), _stream()), "fg_grasp_epsilon")
+    return eps, nc
+
+
 def plain_workspace_size(hand: Hand, B: int) -> int:
     n = C.c_size_t()
     check(_lib.load().fg_plain_workspace_size(hand.handle, B, C.byref(n)), "fg_plain_workspace_size")

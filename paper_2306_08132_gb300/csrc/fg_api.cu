@@ -517,6 +517,52 @@ fg_status fg_optimize_step(const fg_hand* h, const fg_scene* sc, const int* oc, 
   return cuda_status(launch_fused(kModeOptimize, a, h, (cudaStream_t)stream), "fg_optimize_step");
 }
 
+fg_status fg_contact_measure(const fg_hand* h, const fg_scene* sc, const int* oc, const float* q, int B,
+                             const float* weights, float tau, float* out, void* stream) {
+  if (!h || !sc) return invalid("fg_contact_measure: NULL hand or scene");
+  if (B < 0) return invalid("fg_contact_measure: B < 0");
+  if (!std::isfinite(tau)) return invalid("fg_contact_measure: non-finite tau");
+  if (B == 0) return FG_OK;
+  if (!q || !weights || !out) return invalid("fg_contact_measure: NULL buffer");
+  FusedArgs a{};
+  a.hand = h->dev;
+  a.hand_D = h->host.D;
+  a.objs = sc->dev;
+  a.n_obj = sc->n;
+  a.any_mesh = sc->has_mesh;
+  a.obj_of_cand = oc;
+  a.q = const_cast<float*>(q);
+  a.B = B;
+  return cuda_status(launch_contact_measure(a, weights, tau, out, (cudaStream_t)stream), "fg_contact_measure");
+}
+
+fg_status fg_grasp_epsilon(const fg_hand* h, const fg_scene* sc, const int* oc, const float* q, int B, float tau,
+                           float mu, int cone_edges, float torque_scale, const float* dirs, int K, float* eps,
+                           int* n_contacts, void* stream) {
+  if (!h || !sc) return invalid("fg_grasp_epsilon: NULL hand or scene");
+  if (B < 0) return invalid("fg_grasp_epsilon: B < 0");
+  if (!std::isfinite(tau)) return invalid("fg_grasp_epsilon: non-finite tau");
+  if (!(mu >= 0.0f) || !std::isfinite(mu)) return invalid("fg_grasp_epsilon: mu must be >= 0");
+  if (!(torque_scale >= 0.0f) || !std::isfinite(torque_scale))
+    return invalid("fg_grasp_epsilon: torque_scale must be >= 0");
+  if (cone_edges < 1 || cone_edges > 32) return invalid("fg_grasp_epsilon: cone_edges must be in [1, 32]");
+  if (K < 1 || K > FG_MAX_DIRS) return invalid("fg_grasp_epsilon: K must be in [1, FG_MAX_DIRS]");
+  if (B == 0) return FG_OK;
+  if (!q || !dirs || !eps) return invalid("fg_grasp_epsilon: NULL buffer");
+  FusedArgs a{};
+  a.hand = h->dev;
+  a.hand_D = h->host.D;
+  a.objs = sc->dev;
+  a.n_obj = sc->n;
+  a.any_mesh = sc->has_mesh;
+  a.obj_of_cand = oc;
+  a.q = const_cast<float*>(q);
+  a.B = B;
+  return cuda_status(launch_grasp_epsilon(a, tau, mu, cone_edges, torque_scale, dirs, K, eps, n_contacts,
+                                          (cudaStream_t)stream),
+                     "fg_grasp_epsilon");
+}
+
 fg_status fg_plain_workspace_size(const fg_hand* h, int B, size_t* bytes) {
   if (!h || !bytes || B < 0) return invalid("fg_plain_workspace_size: bad argument");
   *bytes = plain_workspace_bytes(h, B);

@@ -94,6 +94,11 @@ void fused_config_select(int i);
 cudaError_t autotune_fused(const FusedArgs& base, int reps, float* times_ms, int* best, cudaStream_t st);
 cudaError_t launch_queue_round(const FusedArgs& a, cudaStream_t st);
 
+// grasp-quality metrics (fg_quality.cu)
+cudaError_t launch_contact_measure(const FusedArgs& a, const float* weights, float tau, float* out, cudaStream_t st);
+cudaError_t launch_grasp_epsilon(const FusedArgs& a, float tau, float mu, int k_edges, float tscale,
+                                 const float* dirs, int K, float* eps, int* ncontact, cudaStream_t st);
+
 // per-stage kernels (fg_plain.cu)
 size_t plain_workspace_bytes(const fg_hand* h, int B);
 cudaError_t launch_plain_step(const fg_hand* h, const fg_scene* sc, const int* obj_of_cand, float* q, int B,
