@@ -63,6 +63,7 @@ struct ObjDev {
   int kind;                      // 0 grid, 1 mesh
   int n_faces;
   float phong_alpha;
+  float phong_shift;             // bound on |r*_rho - r*| (the Phong point's distance from the flat closest point)
   const float4* bvh;             // 2 per node: (min, right child | first face), (max, face count; 0 = inner)
   const float4* tri;             // 3 per face (BVH order): vertices a, b, c
   const float4* face_nrm;        // 7 per face: vertex normals n_a, n_b, n_c, face normal, edge
@@ -506,10 +507,92 @@ __device__ inline int mesh_closest(const ObjDev& O, const float p[3], float bary
   return best;
 }
 
-__device__ inline void mesh_lookup(const ObjDev& O, const float p[3], SdfSample& s) {
+// The same search for the 32 points of a warp at once (every lane must call it):
+// the warp walks one path through the BVH, descending into a node while some
+// lane's box distance is below that lane's best, and every lane tests every
+// triangle of a visited leaf against its own point.  The points of a warp lie
+// close together, so the union of the lanes' paths is short, and the walk does
+// not diverge.  The result per lane is the closest face, as in mesh_closest
+// (up to the choice among faces at exactly equal distance, which share the
+// closest edge or vertex).
+__device__ inline int mesh_closest_warp(const ObjDev& O, const float p[3], float bary[3], int& feature) {
+  int stack[kBvhStack];
+  int sp = 0, node = 0, best = -1;
+  float best_d2 = 3.0e38f;
+  for (;;) {
+    const float4 lo = __ldg(O.bvh + 2 * node), hi = __ldg(O.bvh + 2 * node + 1);
+    const int count = __float_as_int(hi.w);
+    if (count > 0) {
+      const int first = __float_as_int(lo.w);
+      for (int f = first; f < first + count; ++f) {
+        const float4 A = __ldg(O.tri + 3 * f), B = __ldg(O.tri + 3 * f + 1), C = __ldg(O.tri + 3 * f + 2);
+        const float a[3] = {A.x, A.y, A.z}, b[3] = {B.x, B.y, B.z}, c[3] = {C.x, C.y, C.z};
+        float bb[3];
+        int ft;
+        const float d2 = closest_on_triangle(p, a, b, c, bb, ft);
+        if (d2 < best_d2) {
+          best_d2 = d2;
+          best = f;
+          bary[0] = bb[0]; bary[1] = bb[1]; bary[2] = bb[2];
+          feature = ft;
+        }
+      }
+    } else {
+      const int l = node + 1, r = __float_as_int(lo.w);
+      const float dl = box_dist2(p, __ldg(O.bvh + 2 * l), __ldg(O.bvh + 2 * l + 1));
+      const float dr = box_dist2(p, __ldg(O.bvh + 2 * r), __ldg(O.bvh + 2 * r + 1));
+      const bool need_l = __any_sync(0xffffffffu, dl < best_d2);
+      const bool need_r = __any_sync(0xffffffffu, dr < best_d2);
+      // nearer child first: the one nearer for most lanes
+      const bool left_first = __popc(__ballot_sync(0xffffffffu, dl <= dr)) >= 16;
+      const int nearc = left_first ? l : r, farc = left_first ? r : l;
+      const bool need_near = left_first ? need_l : need_r, need_far = left_first ? need_r : need_l;
+      if (need_near && need_far && sp < kBvhStack) stack[sp++] = farc;
+      if (need_near) {
+        node = nearc;
+        continue;
+      }
+      if (need_far) {
+        node = farc;
+        continue;
+      }
+    }
+    bool found = false;
+    while (sp > 0) {
+      const int cand = stack[--sp];
+      if (__any_sync(0xffffffffu, box_dist2(p, __ldg(O.bvh + 2 * cand), __ldg(O.bvh + 2 * cand + 1)) < best_d2)) {
+        node = cand;
+        found = true;
+        break;
+      }
+    }
+    if (!found) break;
+  }
+  return best;
+}
+
+// Signed distance from p to the flat mesh (sign by the closest feature's
+// pseudonormal, as in mesh_lookup); +inf when p is not finite.
+__device__ inline float mesh_flat_distance(const ObjDev& O, const float p[3]) {
   float bary[3];
   int feature = 0;
   const int f = mesh_closest(O, p, bary, feature);
+  if (f < 0) return 3.0e38f;
+  const float4 A = __ldg(O.tri + 3 * f), B = __ldg(O.tri + 3 * f + 1), C = __ldg(O.tri + 3 * f + 2);
+  const float q[3] = {bary[0] * A.x + bary[1] * B.x + bary[2] * C.x, bary[0] * A.y + bary[1] * B.y + bary[2] * C.y,
+                      bary[0] * A.z + bary[1] * B.z + bary[2] * C.z};
+  const int slot = feature == 0 ? 3 : (feature <= 3 ? 3 + feature : feature - 4);
+  const float4 N = __ldg(O.face_nrm + 7 * f + slot);
+  const float dq[3] = {p[0] - q[0], p[1] - q[1], p[2] - q[2]};
+  const float dist = sqrtf(dq[0] * dq[0] + dq[1] * dq[1] + dq[2] * dq[2]);
+  return dq[0] * N.x + dq[1] * N.y + dq[2] * N.z < 0.0f ? -dist : dist;
+}
+
+// Phong SDF at p for the 32 points of a warp (every lane must call it).
+__device__ inline void mesh_lookup(const ObjDev& O, const float p[3], SdfSample& s) {
+  float bary[3];
+  int feature = 0;
+  const int f = mesh_closest_warp(O, p, bary, feature);
   if (f < 0) {                                  // p not finite: no face compares closer
     const float nan = __int_as_float(0x7fc00000);
     s.phi = s.curv = s.e = nan;
@@ -559,6 +642,7 @@ __device__ inline void mesh_lookup(const ObjDev& O, const float p[3], SdfSample&
 }
 
 // kAnyObj = false compiles the grid lookup alone (callers that only see grids).
+// With kAnyObj every lane of the warp must call it (the mesh search is warp-wide).
 template <bool kHess, bool kAnyObj = true>
 __device__ __forceinline__ void sdf_lookup(const ObjDev& O, const float p[3], SdfSample& s) {
   if constexpr (kAnyObj) {

@@ -343,7 +343,10 @@ __global__ void __launch_bounds__(NW * 32, MINB) fused_step_kernel(FusedArgs a) 
       // so a chunk with  min - r - dt V (1 + 1e-5) - slack > 0  has no contact in
       // any simulation; the slack covers float32 rounding of positions and values.
       // Its contact flags are all zero and its forces are not computed.
-      const bool cull = H.nchunks <= kMaxCullChunks && O.kind == kObjGrid;   // meshes have no min-pyramid
+      // Mesh objects: the Phong point lies within phong_shift of the flat closest
+      // point, so if the chunk's centre c is outside the mesh at flat distance
+      // d > R, every point of the chunk has rho >= d - R - phong_shift.
+      const bool cull = H.nchunks <= kMaxCullChunks;
       if (cull) {
         for (int j0 = warp * 32; j0 < H.nchunks; j0 += NW * 32) {
           const int j = j0 + lane;
@@ -351,7 +354,16 @@ __global__ void __launch_bounds__(NW * 32, MINB) fused_step_kernel(FusedArgs a) 
           if (j < H.nchunks) {
             active = true;
             const int l = H.chunk_link[j];
-            if (l >= 0) {
+            if (l >= 0 && ANY && O.kind == kObjMesh) {
+              const float4 cs = __ldg(H.chunk_sphere + j);
+              float cw[3];
+              world_point(S.frame4[l], cs, cw);
+              const float slack = 1e-6f + 1e-5f * (fabsf(cw[0]) + fabsf(cw[1]) + fabsf(cw[2]));
+              const float dc = mesh_flat_distance(O, cw);
+              const float R = cs.w + slack;
+              const float lbm = dc - R - O.phong_shift;
+              active = !(dc > R && lbm - r - dtV * (1.0f + 1e-5f) - (1e-6f + 1e-5f * fabsf(dc)) > 0.0f);
+            } else if (l >= 0) {
               const float4 cs = __ldg(H.chunk_sphere + j);
               float cw[3];
               world_point(S.frame4[l], cs, cw);

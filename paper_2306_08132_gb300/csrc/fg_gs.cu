@@ -25,13 +25,14 @@
 //   loss       L_stable (Eq. 2) from the final states, its adjoint per
 //              simulation, the joint terms
 //   reverse    warp m carries the state adjoint backwards over the chunks with
-//              events (re-running each such chunk from its start state) and
-//              keeps the adjoint at every chunk's start.
+//              events (re-running each such chunk from its start state: per lane
+//              state and adjoint, the general contact adjoint for the projected
+//              lanes, the leaky one for the rest, through the lookup's adjoint
+//              into the warp's link sums) and keeps the adjoint at every chunk's start.
 //   adjoint    warps take chunks in a fixed pattern; per point one lookup with
-//              second derivatives serves all 7 simulations: the leaky adjoint at
-//              the chunk's (state, state adjoint), or, in a chunk with events,
-//              per lane state and adjoint from a re-run and the general contact
-//              adjoint for the projected lanes.  dL/dp -> per-link sums.
+//              second derivatives serves the simulations without events in the
+//              chunk: the leaky adjoint at the chunk's (state, state adjoint).
+//              dL/dp -> per-link sums.
 //   tree, update  as in the one-step kernel
 //
 // The decision arithmetic (constraint value, tangential displacement, friction
@@ -165,10 +166,17 @@ __device__ __forceinline__ void gs_leaky(const PointState& ps, const float xt[3]
   float un[3];
   cross3(d, ps.n, un);
   const float rwn = rcp_fast(fma_(O.inv_inertia, dot3(un, un), O.inv_mass));
-  float t[3], sn;
-  const float sig = gs_tangent(ps.n, D, t, sn);
+  // tangential direction of D (no branch depends on its rounding: only s2 > 0 does)
+  const float sn = dot3(D, ps.n);
+  float t[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) t[k] = fmaf(-sn, ps.n[k], D[k]);
+  const float s2 = dot3(t, t);
   float c = rwn * (O.inv_mass * dot3(a, ps.n) + O.inv_inertia * dot3(a + 3, un));
-  if (sig > 0.0f) {
+  if (s2 > 0.0f) {
+    const float rs = rsqrtf(s2);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) t[k] *= rs;
     float ut[3];
     cross3(d, t, ut);
     const float rwt = rcp_fast(fma_(O.inv_inertia, dot3(ut, ut), O.inv_mass));
@@ -540,6 +548,13 @@ __global__ void __launch_bounds__(kGW * 32, 2) gs_kernel(FusedArgs a) {
       }
 
       // ------------------------------------- reverse: state adjoint per chunk
+      // A chunk with events of simulation m is finished here: its lanes' states
+      // and adjoints come out of the re-run, so their contribution of simulation m
+      // goes through the lookup's adjoint and into the warp's link sums now, and
+      // the sweep over all points below leaves simulation m of that chunk out.
+      int cur = -1;
+      float acc[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+      const float t0[3] = {S.q[0], S.q[1], S.q[2]};
       {
         const int m = warp;
         float xt[3];
@@ -552,17 +567,33 @@ __global__ void __launch_bounds__(kGW * 32, 2) gs_kernel(FusedArgs a) {
           const unsigned mask = __float_as_uint(sn[12]);
           if (mask) {
             const int i = 32 * j + lane;
-            const float4 sp = __ldg(H.pts + (i < P ? i : 32 * j));
+            const bool valid = i < P;
+            const float4 sp = __ldg(H.pts + (valid ? i : 32 * j));
+            const int link = (int)sp.w;
             float p[3];
-            world_point(S.frame4[(int)sp.w], sp, p);
+            world_point(S.frame4[link], sp, p);
             SdfSample smp;
-            sdf_lookup<false, false>(O, p, smp);
+            sdf_lookup<true, false>(O, p, smp);
             PointState ps;
             point_state(smp, p, r, ps);
             float st0[6], smine[6], amine[6], dphi = 0.0f, dn[3] = {0.0f, 0.0f, 0.0f}, dp[3] = {0.0f, 0.0f, 0.0f};
 #pragma unroll
             for (int k = 0; k < 6; ++k) st0[k] = sn[k];
             gs_chunk_reverse(ps, xt, st0, av, mask, m, lane, Pm, O, smine, amine, dphi, dn, dp);
+            if (!((mask >> lane) & 1u)) gs_leaky(ps, xt, smine, amine, m == 0 ? Pm.w_pen : 0.0f, Pm, O, dphi, dn, dp);
+            sdf_adjoint(smp, ps, dphi, dn, dp);
+            float v[6];
+            if (valid) {
+              const float rel[3] = {p[0] - t0[0], p[1] - t0[1], p[2] - t0[2]};
+              float tq[3];
+              cross3(rel, dp, tq);
+              v[0] = dp[0]; v[1] = dp[1]; v[2] = dp[2];
+              v[3] = tq[0]; v[4] = tq[1]; v[5] = tq[2];
+            } else {
+#pragma unroll
+              for (int k = 0; k < 6; ++k) v[k] = 0.0f;
+            }
+            link_accumulate(S.lacc[warp], lane, link, valid, v, cur, acc);
           }
           if (lane < 6) sn[6 + lane] = pick6(av, lane);
         }
@@ -571,9 +602,6 @@ __global__ void __launch_bounds__(kGW * 32, 2) gs_kernel(FusedArgs a) {
 
       // ----------------------------------------------- adjoint of every point
       {
-        const float t0[3] = {S.q[0], S.q[1], S.q[2]};
-        int cur = -1;
-        float acc[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
         for (int j = warp; j < nch; j += kGW) {
           const int i = 32 * j + lane;
           const bool valid = i < P;
@@ -599,14 +627,7 @@ __global__ void __launch_bounds__(kGW * 32, 2) gs_kernel(FusedArgs a) {
               ae[k] = an[k];
             }
             const unsigned mask = __float_as_uint(sn[12]);
-            const float extra = m == 0 ? Pm.w_pen : 0.0f;
-            if (mask == 0u) {
-              gs_leaky(ps, xt, st0, ae, extra, Pm, O, dphi, dn, dp);
-            } else {
-              float smine[6], amine[6];
-              gs_chunk_reverse(ps, xt, st0, ae, mask, m, lane, Pm, O, smine, amine, dphi, dn, dp);
-              if (!((mask >> lane) & 1u)) gs_leaky(ps, xt, smine, amine, extra, Pm, O, dphi, dn, dp);
-            }
+            if (mask == 0u) gs_leaky(ps, xt, st0, ae, m == 0 ? Pm.w_pen : 0.0f, Pm, O, dphi, dn, dp);
           }
           sdf_adjoint(smp, ps, dphi, dn, dp);
           float v[6];

@@ -175,6 +175,15 @@ extern "C" fg_status fg_sdf_create_mesh(const float* vertices, int nv, const int
   }
   for (int i = 0; i < nv; ++i)
     if (norm(vn[i]) > 0.0) vn[i] = unit(vn[i]);     // vertices used by no face keep a zero normal
+  // Bound on the Phong point's shift from the flat closest point r* on face f:
+  // r*_rho - r* = -a sum_x b_x ((r* - v_x) . n_x) n_x, so |.| <= a max over vertices x, y
+  // of the face of |(v_y - v_x) . n_x| (linear in r*, extreme at the vertices).
+  double shift = 0.0;
+  for (int f = 0; f < nf; ++f)
+    for (int x = 0; x < 3; ++x)
+      for (int y = 0; y < 3; ++y)
+        shift = std::max(shift, std::fabs(dot(sub(V[F[3 * f + y]], V[F[3 * f + x]]), vn[F[3 * f + x]])));
+  shift *= phong_alpha;
   // BVH over faces
   Builder bld(V, F);
   bld.build(0, nf, 0);
@@ -220,6 +229,7 @@ extern "C" fg_status fg_sdf_create_mesh(const float* vertices, int nv, const int
   o.kind = kObjMesh;
   o.n_faces = nf;
   o.phong_alpha = phong_alpha;
+  o.phong_shift = (float)(shift * (1.0 + 1e-5)) + 1e-7f;
   o.bvh = dev;
   o.tri = dev + 2 * nn;
   o.face_nrm = dev + 2 * nn + 3 * (size_t)nf;

@@ -371,10 +371,16 @@ __global__ void fk_points_kernel(const HandDev* __restrict__ Hp, const float* __
 
 __global__ void sdf_query_kernel(ObjDev O, const float* __restrict__ pts, int n, float r, float* __restrict__ phi,
                                  float* __restrict__ grad) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    float p[3] = {pts[i], pts[(size_t)n + i], pts[2 * (size_t)n + i]};
+  // whole warps stay in the loop (the mesh search is warp-wide); lanes past n
+  // look up the last point and write nothing
+  const int lane = threadIdx.x & 31;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i - lane < n; i += gridDim.x * blockDim.x) {
+    const bool valid = i < n;
+    const int k = valid ? i : n - 1;
+    float p[3] = {pts[k], pts[(size_t)n + k], pts[2 * (size_t)n + k]};
     SdfSample s;
     sdf_lookup<false>(O, p, s);
+    if (!valid) continue;
     phi[i] = s.phi - r;
     if (grad) {
       grad[i] = s.g[0];

@@ -31,6 +31,7 @@ namespace {
 constexpr int kQW = 8;                       // warps per candidate
 constexpr int kQBatchChunks = 32;            // chunks per contact batch (<= 1024 contacts)
 constexpr int kQBatch = 32 * kQBatchChunks;
+constexpr int kQD = 4;                       // directions per thread per pass over the contacts
 
 struct QualitySmem {
   HandDev H;
@@ -174,25 +175,40 @@ __global__ void __launch_bounds__(kQW * 32) epsilon_kernel(FusedArgs a, float ta
       }
       __syncthreads();
       const int nc = S.count;
-      for (int k = tid; k < K; k += NT) {
-        const float* u = dirs + (size_t)k * 6;
-        const float uf[3] = {__ldg(u), __ldg(u + 1), __ldg(u + 2)};
-        const float ut[3] = {__ldg(u + 3) * tscale, __ldg(u + 4) * tscale, __ldg(u + 5) * tscale};
-        float h = hmax[k];
+      // kQD directions per thread per pass: each contact record read from shared
+      // memory serves all of them
+      for (int k0 = tid; k0 < K; k0 += NT * kQD) {
+        float uf[kQD][3], ut[kQD][3], h[kQD];
+#pragma unroll
+        for (int d = 0; d < kQD; ++d) {
+          const int k = min(k0 + d * NT, K - 1);              // repeats the last direction past K
+          const float* u = dirs + (size_t)k * 6;
+#pragma unroll
+          for (int c3 = 0; c3 < 3; ++c3) {
+            uf[d][c3] = __ldg(u + c3);
+            ut[d][c3] = __ldg(u + 3 + c3) * tscale;
+          }
+          h[d] = k0 + d * NT < K ? hmax[k] : -INFINITY;       // each thread keeps to its own entries
+        }
         for (int jc = 0; jc < nc; ++jc) {
           const float4 ra = rec[jc].a, rb = rec[jc].b, rc = rec[jc].c;
-          // a = u_f + s (u_t x p)
-          const float ax = uf[0] + (ut[1] * ra.z - ut[2] * ra.y);
-          const float ay = uf[1] + (ut[2] * ra.x - ut[0] * ra.z);
-          const float az = uf[2] + (ut[0] * ra.y - ut[1] * ra.x);
-          const float an = ax * ra.w + ay * rb.x + az * rb.y;
-          const float a1 = ax * rb.z + ay * rb.w + az * rc.x;
-          const float a2 = ax * rc.y + ay * rc.z + az * rc.w;
-          float best = -INFINITY;
-          for (int e = 0; e < k_edges; ++e) best = fmaxf(best, S.ce[e] * a1 + S.se[e] * a2);
-          h = fmaxf(h, mu * best - an);
+#pragma unroll
+          for (int d = 0; d < kQD; ++d) {
+            // a = u_f + s (u_t x p)
+            const float ax = uf[d][0] + (ut[d][1] * ra.z - ut[d][2] * ra.y);
+            const float ay = uf[d][1] + (ut[d][2] * ra.x - ut[d][0] * ra.z);
+            const float az = uf[d][2] + (ut[d][0] * ra.y - ut[d][1] * ra.x);
+            const float an = ax * ra.w + ay * rb.x + az * rb.y;
+            const float a1 = ax * rb.z + ay * rb.w + az * rc.x;
+            const float a2 = ax * rc.y + ay * rc.z + az * rc.w;
+            float best = -INFINITY;
+            for (int e = 0; e < k_edges; ++e) best = fmaxf(best, S.ce[e] * a1 + S.se[e] * a2);
+            h[d] = fmaxf(h[d], mu * best - an);
+          }
         }
-        hmax[k] = h;
+#pragma unroll
+        for (int d = 0; d < kQD; ++d)
+          if (k0 + d * NT < K) hmax[k0 + d * NT] = h[d];
       }
       if (tid == 0) S.total += nc;
       __syncthreads();
