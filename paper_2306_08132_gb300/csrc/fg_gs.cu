@@ -347,7 +347,7 @@ __device__ __forceinline__ void gs_chunk_reverse(const PointState& ps, const flo
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kGW * 32, 2) gs_kernel(FusedArgs a) {
+__global__ void __launch_bounds__(kGW * 32, 3) gs_kernel(FusedArgs a) {
   __shared__ GsSmem S;
   extern __shared__ float dyn[];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
