@@ -520,6 +520,17 @@ def main():
         mesh = {"ms_per_step": m_ms, "value": cand_steps / (m_ms / 1000.0), "unit": "candidate-steps/s",
                 "objects": "%d superquadric meshes, %d faces each, Phong SDF" % (len(mobjs), len(mobjs[0]["faces"])),
                 "fused_config": "%dw/%d/%dp" % fg.fused_configs()[fg.fused_config_current()]}
+        if args.gs:                          # the paper's combination: Phong SDF of a mesh, Gauss-Seidel
+            pGm = dict(w.params, gauss_seidel=1)
+
+            def mesh_gs_step():
+                q.copy_(q0)
+                fg.optimize_step(hand, mscene, q, pGm, 0, K, S_in, obj_of_cand=oc, loss=loss)
+
+            gms2 = timed(graphed(mesh_gs_step), max(3, args.steps // 4), 3)
+            mg_ms = max_over_ranks(float(np.mean(gms2)), world, dev)
+            mesh["gauss_seidel"] = {"ms_per_step": mg_ms, "value": cand_steps / (mg_ms / 1000.0),
+                                    "unit": "candidate-steps/s"}
 
     serving, sweep = None, None
     if args.serving > 0:

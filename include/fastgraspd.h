@@ -106,8 +106,8 @@ typedef struct {
  * 1 = they are projected one after another in point order, each seeing the
  * object displaced by the corrections before it (Sec. III-C: "a Gauss-Seidel
  * step" over the constraints of Eq. 1), and applied in full.  Gauss-Seidel is
- * accepted by fg_loss_and_grad and fg_optimize_step on grid objects, for hands
- * of at most 8,192 points (FG_ERR_INVALID elsewhere). */
+ * accepted by fg_loss_and_grad and fg_optimize_step on grid and mesh objects,
+ * for hands of at most 8,192 points (FG_ERR_INVALID elsewhere). */
 typedef struct {
   float alpha_leak;
   float dt;

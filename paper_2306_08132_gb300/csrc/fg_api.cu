@@ -413,9 +413,9 @@ static fg_status check_one_step(const char* fn, const fg_params* p) {
   return FG_OK;
 }
 
-// The Gauss-Seidel form: grid objects, hands whose chunks fit the kernel's tables.
+// The Gauss-Seidel form: hands whose chunks fit the kernel's tables.
 static fg_status check_gs(const char* fn, const fg_hand* h, const fg_scene* sc) {
-  if (sc->has_mesh) return invalid(std::string(fn) + ": the Gauss-Seidel form takes grid objects only");
+  (void)sc;
   if (h->host.nchunks > kMaxCullChunks)
     return invalid(std::string(fn) + ": the Gauss-Seidel form takes hands of at most 8,192 points");
   return FG_OK;

@@ -346,7 +346,8 @@ __device__ __forceinline__ void gs_chunk_reverse(const PointState& ps, const flo
   }
 }
 
-template <int MODE>
+// ANY = false: grid objects only; true: grids and meshes (the lookup dispatches on the kind).
+template <int MODE, bool ANY>
 __global__ void __launch_bounds__(kGW * 32, 3) gs_kernel(FusedArgs a) {
   __shared__ GsSmem S;
   extern __shared__ float dyn[];
@@ -396,12 +397,24 @@ __global__ void __launch_bounds__(kGW * 32, 3) gs_kernel(FusedArgs a) {
       // ------------------------------------------------- chunk bounds (culling)
       // Every point of chunk j lies in its bounding sphere (centre cw, radius R);
       // the interpolated field over the sphere's box is bounded below by the
-      // min-pyramid, so phi_hat >= lb = min - r over the chunk.
+      // min-pyramid, so phi_hat >= lb = min - r over the chunk.  For a mesh: if the
+      // centre is outside at flat distance d > R, rho >= d - R - (the Phong shift bound).
       for (int j = tid; j < nch; j += kGW * 32) {
         const int l = H.chunk_link[j];
         float lbj = -3.0e38f;
         float4 cwj = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        if (l >= 0) {
+        if (ANY && O.kind == kObjMesh) {
+          if (l >= 0) {
+            const float4 cs = __ldg(H.chunk_sphere + j);
+            float cw[3];
+            world_point(S.frame4[l], cs, cw);
+            const float slack = 1e-6f + 1e-5f * (fabsf(cw[0]) + fabsf(cw[1]) + fabsf(cw[2]));
+            const float R = cs.w + slack;
+            const float dc = mesh_flat_distance(O, cw);
+            if (dc > R) lbj = dc - R - O.phong_shift - r - 1e-5f * fabsf(dc);
+            cwj = make_float4(cw[0], cw[1], cw[2], R);
+          }
+        } else if (l >= 0) {
           const float4 cs = __ldg(H.chunk_sphere + j);
           float cw[3];
           world_point(S.frame4[l], cs, cw);
@@ -451,7 +464,7 @@ __global__ void __launch_bounds__(kGW * 32, 3) gs_kernel(FusedArgs a) {
             float p[3];
             world_point(S.frame4[(int)sp.w], sp, p);
             SdfSample smp;
-            sdf_lookup<false, false>(O, p, smp);
+            sdf_lookup<false, ANY>(O, p, smp);
             PointState ps;
             point_state(smp, p, r, ps);
             int last = -1;
@@ -573,7 +586,7 @@ __global__ void __launch_bounds__(kGW * 32, 3) gs_kernel(FusedArgs a) {
             float p[3];
             world_point(S.frame4[link], sp, p);
             SdfSample smp;
-            sdf_lookup<true, false>(O, p, smp);
+            sdf_lookup<true, ANY>(O, p, smp);
             PointState ps;
             point_state(smp, p, r, ps);
             float st0[6], smine[6], amine[6], dphi = 0.0f, dn[3] = {0.0f, 0.0f, 0.0f}, dp[3] = {0.0f, 0.0f, 0.0f};
@@ -610,7 +623,7 @@ __global__ void __launch_bounds__(kGW * 32, 3) gs_kernel(FusedArgs a) {
           float p[3];
           world_point(S.frame4[link], sp, p);
           SdfSample smp;
-          sdf_lookup<true, false>(O, p, smp);
+          sdf_lookup<true, ANY>(O, p, smp);
           PointState ps;
           point_state(smp, p, r, ps);
           float dphi = 0.0f, dn[3] = {0.0f, 0.0f, 0.0f}, dp[3] = {0.0f, 0.0f, 0.0f};
@@ -718,25 +731,25 @@ __global__ void __launch_bounds__(kGW * 32, 3) gs_kernel(FusedArgs a) {
   }
 }
 
-template <int MODE>
+template <int MODE, bool ANY>
 cudaError_t launch_gs_mode(const FusedArgs& a, int nchunks, cudaStream_t st) {
   const size_t dyn = sizeof(float) * (size_t)nchunks * kSims * kSnapWords;
   static size_t attr_set[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dyn > attr_set[dev & 63]) {
-    cudaError_t e = cudaFuncSetAttribute(gs_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    cudaError_t e = cudaFuncSetAttribute(gs_kernel<MODE, ANY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
     if (e != cudaSuccess) return e;
     attr_set[dev & 63] = dyn;
   }
   int bps = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, gs_kernel<MODE>, kGW * 32, dyn);
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, gs_kernel<MODE, ANY>, kGW * 32, dyn);
   if (e != cudaSuccess) return e;
   if (bps < 1) bps = 1;
   long long grid = (long long)device_sm_count() * bps;
   if (grid > a.B) grid = a.B;
   if (grid < 1) return cudaSuccess;
-  gs_kernel<MODE><<<(int)grid, kGW * 32, dyn, st>>>(a);
+  gs_kernel<MODE, ANY><<<(int)grid, kGW * 32, dyn, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -745,8 +758,11 @@ cudaError_t launch_gs_mode(const FusedArgs& a, int nchunks, cudaStream_t st) {
 cudaError_t launch_gs(int mode, const FusedArgs& a, int nchunks, cudaStream_t st) {
   if (a.B <= 0) return cudaSuccess;
   if (nchunks < 1 || nchunks > kMaxCullChunks) return cudaErrorInvalidValue;
-  if (mode == kModeLossGrad) return launch_gs_mode<kModeLossGrad>(a, nchunks, st);
-  return launch_gs_mode<kModeOptimize>(a, nchunks, st);
+  if (a.any_mesh)
+    return mode == kModeLossGrad ? launch_gs_mode<kModeLossGrad, true>(a, nchunks, st)
+                                 : launch_gs_mode<kModeOptimize, true>(a, nchunks, st);
+  return mode == kModeLossGrad ? launch_gs_mode<kModeLossGrad, false>(a, nchunks, st)
+                               : launch_gs_mode<kModeOptimize, false>(a, nchunks, st);
 }
 
 }  // namespace fg

@@ -167,7 +167,6 @@ def test_gs_single_contact_equals_jacobi_on_the_gpu(fg, tiny):
 
 def test_gs_is_refused_where_unsupported(fg, tiny):
     from paper_2306_08132_gb300 import _lib
-    from synth import meshes as SM
     w = tiny.w
     q = torch.tensor(w.q0[:4], device=_dev())
     params = dict(w.params, gauss_seidel=1)
@@ -186,7 +185,80 @@ def test_gs_is_refused_where_unsupported(fg, tiny):
             qu.submit(tiny.hand, tiny.sdfs[0], w.q0[:4], 10, params)
     finally:
         qu.close()
-    m = SM.icosphere(0.04, 2)
-    mscene = fg.Scene([fg.Sdf.from_mesh(m["vertices"], m["faces"], m["mass"], m["inertia"])])
-    with pytest.raises(_lib.FgError):
-        fg.loss_and_grad(tiny.hand, mscene, q, params, 0.004)
+
+
+def test_gs_full_size_sampled_parity(fg):
+    """The benchmark workload at full size (8 superquadrics on 128^3 grids, 4-finger hand
+    with 4,352 points, 8,192 candidates) in the launch the benchmark times: loss and
+    update of 6 sampled candidates against the oracle's Gauss-Seidel form."""
+    w = synth.batched_superquadric_workload(device="cuda")
+    case = Case(fg, w)
+    params = dict(w.params, gauss_seidel=1)
+    S = case.oracle(params)
+    q = torch.tensor(w.q0, device=_dev())
+    q1 = q.clone()
+    loss = fg.optimize_step(case.hand, case.scene, q1, params, 0, w.steps, 1, obj_of_cand=case.oc)
+    torch.cuda.synchronize()
+    assert torch.isfinite(loss).all() and torch.isfinite(q1).all()
+    r = O.dilation_radius(S.prm, 0, w.steps)
+    sample = np.sort(np.random.default_rng(12).choice(w.B, size=6, replace=False))
+    ref = O.batch_loss_and_grad(S, w.q0[sample], w.obj_of_cand[sample], r)
+    clean = np.array([O.clean_candidates(S.hand, S.objs[int(w.obj_of_cand[b])], w.q0[b:b + 1], r, S.prm)[0]
+                      for b in sample])
+    assert clean.sum() >= 3
+    step = ((q1 - q).cpu().numpy()[sample]).astype(np.float64) / -params["lr"]
+    _compare(loss.cpu().numpy()[sample], step, ref, clean)
+
+
+def test_gs_ragged_hand_and_edge_cases(fg):
+    """Links whose point ranges are not 32-aligned (chunks straddle links and are never
+    culled), a last chunk of 18 points; an empty batch, a hand far from the object
+    (6V/7 exactly), object indices outside the scene (NaN, q left alone)."""
+    w = synth.tiny_sphere_workload(n_cand=24)
+    h = synth.make_hand(3, 21)                          # P = 210
+    qs = synth.sample_candidates(np.random.default_rng(7), h, 24, 0.095)
+    w2 = synth.Workload("ragged", h, w.objects, qs, np.zeros(24, dtype=np.int32), w.params, 10)
+    case = Case(fg, w2)
+    params = dict(w.params, gauss_seidel=1)
+    S = case.oracle(params)
+    loss, grad = fg.loss_and_grad(case.hand, case.scene, torch.tensor(qs, device=_dev()), params, 0.004)
+    ref = O.batch_loss_and_grad(S, qs, w2.obj_of_cand, 0.004)
+    clean = case.clean(S, qs, 0.004)
+    assert clean.sum() >= 12 and (ref["N"][clean] > 0).any()
+    _compare(loss.cpu().numpy(), grad.cpu().numpy(), ref, clean)
+    e = torch.zeros(0, h["D"], device=_dev())
+    l0, _ = fg.loss_and_grad(case.hand, case.scene, e, params, 0.004)
+    assert l0.numel() == 0
+    far = np.zeros((3, h["D"]), dtype=np.float32)
+    far[:, 0] = [0.5, -0.4, 0.3]
+    far[:, 6:] = 0.5 * (h["q_low"] + h["q_up"])
+    lf, gf = fg.loss_and_grad(case.hand, case.scene, torch.tensor(far, device=_dev()), params, 0.004)
+    assert np.allclose(lf.cpu().numpy(), 6.0 / 7.0, rtol=1e-6)
+    bad = torch.tensor([0, 3, -1], device=_dev(), dtype=torch.int32)
+    qq = torch.tensor(qs[:3], device=_dev())
+    lb, _ = fg.loss_and_grad(case.hand, case.scene, qq, params, 0.004, obj_of_cand=bad)
+    lb = lb.cpu().numpy()
+    assert np.isfinite(lb[0]) and np.isnan(lb[1]) and np.isnan(lb[2])
+    q2 = qq.clone()
+    fg.optimize_step(case.hand, case.scene, q2, params, 0, 10, 2, obj_of_cand=bad)
+    assert torch.equal(q2[1:], qq[1:])
+
+
+def test_gs_on_mesh_objects(fg):
+    """The paper's own combination: the Phong SDF of a mesh (an icosphere and a
+    superquadric mesh in one batch) with the Gauss-Seidel projection."""
+    from synth import meshes as SM
+    w = synth.tiny_sphere_workload(n_cand=32)
+    rng = np.random.default_rng(5)
+    objects = [SM.icosphere(0.04, 3), SM.random_superquadric_mesh(rng, 16, 32)]
+    oc = np.repeat(np.arange(2, dtype=np.int32), 16)
+    w2 = synth.Workload("gs-mesh", w.hand, objects, w.q0, oc, w.params, 10)
+    case = Case(fg, w2)
+    params = dict(w.params, gauss_seidel=1)
+    S = case.oracle(params)
+    loss, grad = fg.loss_and_grad(case.hand, case.scene, torch.tensor(w.q0, device=_dev()), params, 0.004,
+                                  obj_of_cand=case.oc)
+    ref = O.batch_loss_and_grad(S, w.q0, oc, 0.004)
+    clean = case.clean(S, w.q0, 0.004)
+    assert clean.sum() >= 12 and (ref["N"][clean] >= 2).any()
+    _compare(loss.cpu().numpy(), grad.cpu().numpy(), ref, clean)

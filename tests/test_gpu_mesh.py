@@ -169,3 +169,29 @@ def test_mesh_scenes_refused_where_unsupported(fg, sphere_case):
         fg.loss_and_grad(c.hand, c.scene, q, dict(c.params, sim_steps=1), 0.004)
     with pytest.raises(_lib.FgError):
         fg.optimize_step_plain(c.hand, c.scene, q.clone(), c.params, 0, 10, 1)
+
+
+def test_mesh_full_size_sampled_parity(fg):
+    """The benchmark's mesh workload at full size (the 8 superquadrics as meshes of 2,208
+    faces, 4-finger hand with 4,352 points, 8,192 candidates) in the launch the benchmark
+    times: loss and update of 3 sampled candidates against the oracle."""
+    w = synth.batched_superquadric_workload(device="cuda")
+    meshes = []
+    for o in w.objects:
+        pr = o["params"]
+        meshes.append(SM.superquadric_mesh(pr["semi_axes"], float(np.clip(pr["eps1"], 0.5, 1.5)),
+                                           float(np.clip(pr["eps2"], 0.5, 1.5)), 24, 48))
+    c = Case(fg, w.hand, meshes, w.obj_of_cand, w.q0, w.params)
+    q = torch.tensor(w.q0, device=_dev())
+    q1 = q.clone()
+    loss = fg.optimize_step(c.hand, c.scene, q1, w.params, 0, w.steps, 1, obj_of_cand=c.oc)
+    torch.cuda.synchronize()
+    assert torch.isfinite(loss).all() and torch.isfinite(q1).all()
+    r = O.dilation_radius(c.S.prm, 0, w.steps)
+    sample = np.sort(np.random.default_rng(14).choice(w.B, size=8, replace=False))
+    ref = O.batch_loss_and_grad(c.S, w.q0[sample], w.obj_of_cand[sample], r)
+    clean = np.array([O.clean_candidates(c.S.hand, c.S.objs[int(w.obj_of_cand[b])], w.q0[b:b + 1], r, c.S.prm)[0]
+                      for b in sample])
+    assert clean.sum() >= 2
+    step = ((q1 - q).cpu().numpy()[sample]).astype(np.float64) / -w.params["lr"]
+    _compare(loss.cpu().numpy()[sample], step, ref, clean)

@@ -163,3 +163,74 @@ def test_quality_arguments_are_checked(fg, batch):
             fg.grasp_epsilon(hand, scene, q, args["tau"], args["mu"], args["cone_edges"], args["torque_scale"], dirs)
     with pytest.raises(_lib.FgError):
         fg.contact_measure(hand, scene, q, torch.ones(hand.P, device=_dev()), float("nan"))
+
+
+def test_quality_full_size_sampled(fg):
+    """Contact area and epsilon over the benchmark workload's 8,192 candidates (8
+    superquadrics on 128^3 grids, 4-finger hand) in one launch each; 12 sampled
+    candidates against the oracle."""
+    w = synth.batched_superquadric_workload(device="cuda")
+    hand = fg.Hand.from_synth(w.hand)
+    scene = fg.Scene([fg.Sdf.from_synth(o) for o in w.objects])
+    S = O.Setup(w.hand, w.objects, w.params)
+    q = torch.tensor(w.q0, device=_dev())
+    oc = torch.tensor(w.obj_of_cand, device=_dev(), dtype=torch.int32)
+    U = synth.unit_directions(1024)
+    ca = fg.contact_measure(hand, scene, q, torch.tensor(w.hand["point_area"], device=_dev()), TAU, obj_of_cand=oc)
+    eps, nc = fg.grasp_epsilon(hand, scene, q, TAU, MU, EDGES, 1.0 / 0.08, torch.tensor(U, device=_dev()),
+                               obj_of_cand=oc)
+    ca, eps, nc = ca.cpu().numpy().astype(np.float64), eps.cpu().numpy().astype(np.float64), nc.cpu().numpy()
+    sample = np.sort(np.random.default_rng(13).choice(w.B, size=12, replace=False))
+    checked = 0
+    for b in sample:
+        obj = S.objs[int(w.obj_of_cand[b])]
+        if not Q.guard_ok(S.hand, obj, w.q0[b], TAU):
+            continue
+        p, n, phi, idx = Q.contacts(S.hand, obj, w.q0[b], TAU)
+        assert nc[b] == len(p)
+        ref_ca = Q.measure(S.hand, obj, w.q0[b], w.hand["point_area"], TAU)
+        assert abs(ca[b] - ref_ca) <= 1e-5 * max(ref_ca, 1e-6)
+        ref_e = Q.support_min(Q.cone_wrenches(p, n, MU, EDGES, 0.08), U.astype(np.float64))
+        assert _eps_close(np.array([eps[b]]), np.array([ref_e]))[0], (b, eps[b], ref_e)
+        checked += 1
+    assert checked >= 8
+
+
+def test_quality_ragged_hand(fg):
+    """Links not 32-aligned (P = 210, a last chunk of 18 points): contact area, contact
+    counts and epsilon against the oracle; an empty batch; a hand far from the object
+    (no contact: CA = 0, eps = -inf); object indices outside the scene (NaN, -1)."""
+    w = synth.tiny_sphere_workload(n_cand=20)
+    h = synth.make_hand(3, 21)
+    qs = synth.sample_candidates(np.random.default_rng(7), h, 20, 0.095)
+    hand = fg.Hand.from_synth(h)
+    scene = fg.Scene([fg.Sdf.from_synth(o) for o in w.objects])
+    S = O.Setup(h, w.objects, w.params)
+    q = torch.tensor(qs, device=_dev())
+    U = synth.unit_directions(64)
+    ca = fg.contact_measure(hand, scene, q, torch.tensor(h["point_area"], device=_dev()), TAU).cpu().numpy()
+    eps, nc = fg.grasp_epsilon(hand, scene, q, TAU, MU, EDGES, 20.0, torch.tensor(U, device=_dev()))
+    eps, nc = eps.cpu().numpy().astype(np.float64), nc.cpu().numpy()
+    checked = 0
+    for b in range(len(qs)):
+        if not Q.guard_ok(S.hand, S.objs[0], qs[b], TAU):
+            continue
+        p, n, phi, idx = Q.contacts(S.hand, S.objs[0], qs[b], TAU)
+        assert nc[b] == len(p)
+        ref_ca = Q.measure(S.hand, S.objs[0], qs[b], h["point_area"], TAU)
+        assert abs(float(ca[b]) - ref_ca) <= 1e-5 * max(ref_ca, 1e-6)
+        ref_e = Q.support_min(Q.cone_wrenches(p, n, MU, EDGES, 0.05), U.astype(np.float64))
+        assert _eps_close(np.array([eps[b]]), np.array([ref_e]))[0]
+        checked += 1
+    assert checked >= 10 and (nc > 0).sum() >= 3
+    e0, n0 = fg.grasp_epsilon(hand, scene, q[:0], TAU, MU, EDGES, 20.0, torch.tensor(U, device=_dev()))
+    assert e0.numel() == 0
+    far = np.zeros((2, h["D"]), dtype=np.float32)
+    far[:, 0] = [0.5, -0.4]
+    qf = torch.tensor(far, device=_dev())
+    assert float(fg.contact_measure(hand, scene, qf, torch.tensor(h["point_area"], device=_dev()), TAU).abs().max()) == 0
+    ef, nf = fg.grasp_epsilon(hand, scene, qf, TAU, MU, EDGES, 20.0, torch.tensor(U, device=_dev()))
+    assert np.isneginf(ef.cpu().numpy()).all() and (nf.cpu().numpy() == 0).all()
+    bad = torch.tensor([0, 5], device=_dev(), dtype=torch.int32)
+    eb, nb = fg.grasp_epsilon(hand, scene, q[:2], TAU, MU, EDGES, 20.0, torch.tensor(U, device=_dev()), obj_of_cand=bad)
+    assert np.isnan(eb.cpu().numpy()[1]) and nb.cpu().numpy()[1] == -1

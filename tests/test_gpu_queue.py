@@ -158,3 +158,32 @@ def test_queue_errors_and_destroy(fg, requests):
     t0 = time.time()
     queue.close()                                # drops waiting work, finishes the round in flight
     assert time.time() - t0 < 30
+
+
+def test_mesh_request_in_the_mix(fg, requests):
+    """A request on a mesh object (Phong SDF) and a grid request: each result alone and
+    in the mix.  The mix runs in the kernel that dispatches per object kind; the mesh
+    request runs in it either way (identical results), the grid request's result may
+    differ from its grid-only run by float32 rounding only."""
+    from synth import meshes as SM
+    w = synth.tiny_sphere_workload(n_cand=20)
+    mesh_req = (fg.Hand.from_synth(w.hand), fg.Sdf.from_synth(SM.icosphere(0.04, 3)), w.q0, w.params, 9)
+    h, s, q0, p, _ = requests[1]
+    reqs = [mesh_req, (h, s, q0, p, 1)]        # one step: the two kernels start from the same state
+    alone = []
+    for r in reqs:
+        queue = fg.Queue(1 << 30, steps_per_launch=4)
+        try:
+            alone.append(_run(fg, queue, [r])[0])
+        finally:
+            queue.close()
+    queue = fg.Queue(1 << 30, steps_per_launch=4)
+    try:
+        mixed = _run(fg, queue, reqs)
+    finally:
+        queue.close()
+    np.testing.assert_array_equal(alone[0][0], mixed[0][0])
+    np.testing.assert_array_equal(alone[0][1], mixed[0][1])
+    np.testing.assert_allclose(mixed[1][0], alone[1][0], rtol=1e-5, atol=1e-5)
+    np.testing.assert_allclose(mixed[1][1], alone[1][1], rtol=1e-4)
+    assert np.isfinite(mixed[0][0]).all() and np.isfinite(mixed[0][1]).all()
