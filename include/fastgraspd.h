@@ -97,9 +97,10 @@ typedef struct {
  * the object's velocity after T steps; the paper's experiments use T = 1).
  *   0: one step, each simulation's constraint on the plane through the single
  *      SDF query of the point (the default path of every entry point);
- *   1..FG_MAX_SIM_STEPS: T steps, every point re-queried in the SDF at each
- *      simulation's predicted object pose of every step (Sec. III-C); accepted
- *      by fg_loss_and_grad and fg_optimize_step only (FG_ERR_INVALID elsewhere). */
+ *   1..FG_MAX_SIM_STEPS: T steps, every point re-queried in the SDF (grid or
+ *      mesh) at each simulation's predicted object pose of every step (Sec. III-C);
+ *      accepted by fg_loss_and_grad and fg_optimize_step only (FG_ERR_INVALID
+ *      elsewhere). */
 #define FG_MAX_SIM_STEPS 8
 /* gauss_seidel (with sim_steps = 0): 0 = the corrections of all contacts are
  * taken at the predicted pose and averaged over the active contacts (Jacobi);

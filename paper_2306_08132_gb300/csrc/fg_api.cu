@@ -470,7 +470,6 @@ fg_status fg_loss_and_grad(const fg_hand* h, const fg_scene* sc, const int* oc, 
   a.loss = loss;
   a.grad = grad;
   if (a.P.sim_steps >= 1) {
-    if (sc->has_mesh) return invalid("fg_loss_and_grad: the T-step metric takes grid objects only");
     return cuda_status(launch_tstep(kModeLossGrad, a, (cudaStream_t)stream), "fg_loss_and_grad (T-step)");
   }
   if (a.P.gauss_seidel) {
@@ -505,7 +504,6 @@ fg_status fg_optimize_step(const fg_hand* h, const fg_scene* sc, const int* oc, 
   a.nsteps = nsteps;
   a.loss = loss;
   if (a.P.sim_steps >= 1) {
-    if (sc->has_mesh) return invalid("fg_optimize_step: the T-step metric takes grid objects only");
     return cuda_status(launch_tstep(kModeOptimize, a, (cudaStream_t)stream), "fg_optimize_step (T-step)");
   }
   if (a.P.gauss_seidel) {

@@ -238,6 +238,14 @@ __device__ __forceinline__ bool chunk_may_touch(const ObjDev& O, const SimStep& 
                                                 float rdil) {
   float d[3], c[3];
   step_query(st, cw, d, c);
+  if (O.kind == kObjMesh) {
+    // the centre outside the mesh at flat distance dc > R: rho >= dc - R - (Phong shift bound)
+    const float slack = 1e-6f + 1e-5f * (fabsf(cw[0]) + fabsf(cw[1]) + fabsf(cw[2]) + fabsf(d[0]) + fabsf(d[1]) +
+                                         fabsf(d[2]));
+    const float dc = mesh_flat_distance(O, c);
+    const float Rs = R + slack;
+    return !(dc > Rs && dc - Rs - O.phong_shift - rdil - (1e-6f + 1e-5f * fabsf(dc)) > 0.0f);
+  }
   const float slack = 1e-6f + 1e-5f * (fabsf(cw[0]) + fabsf(cw[1]) + fabsf(cw[2]) + fabsf(d[0]) + fabsf(d[1]) +
                                        fabsf(d[2]));
   const float Ru = (R + slack) * O.inv_h;
@@ -284,7 +292,8 @@ __device__ __forceinline__ float leaky_adjoint(const float d[3], const float n[3
   return -P.alpha * dC;
 }
 
-template <int MODE>
+// ANY = false: grid objects only; true: grids and meshes (the lookup dispatches on the kind).
+template <int MODE, bool ANY>
 __global__ void __launch_bounds__(kTW * 32, 4) tstep_kernel(FusedArgs a) {
   __shared__ TstepSmem S;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -389,7 +398,7 @@ __global__ void __launch_bounds__(kTW * 32, 4) tstep_kernel(FusedArgs a) {
             world_point(S.frame4[(int)sp.w], sp, p);
             step_query(st, p, d, r);
             SdfSample smp;
-            sdf_lookup<false, false>(O, r, smp);   // grid objects only
+            sdf_lookup<false, ANY>(O, r, smp);
             PointState ps;
             point_state(smp, r, rdil, ps);
             const bool kap = valid && ps.phi_hat < 0.0f;
@@ -532,13 +541,24 @@ __global__ void __launch_bounds__(kTW * 32, 4) tstep_kernel(FusedArgs a) {
             // tangent) carries no gradient and only dphi_hat = -alpha dC reaches
             // the query, through the gradient of the SDF (no curvature term).
             SdfIndex ix;
-            sdf_index(O, r, ix);
             float corner[8];
-            sdf_gather(O, ix.cell, corner);
+            SdfSample msmp;              // mesh objects: the whole lookup (value, gradient, curvature) at once
+            bool touch;
+            if (ANY && O.kind == kObjMesh) {
+              mesh_lookup(O, r, msmp);
+              touch = sub_(msmp.phi, rdil) < 0.0f;
+            } else {
+              sdf_index(O, r, ix);
+              sdf_gather(O, ix.cell, corner);
+              touch = query_in_contact(O, ix, corner, rdil);
+            }
             float pb[3];
-            if (!__any_sync(kFull, valid && query_in_contact(O, ix, corner, rdil))) {
+            if (!__any_sync(kFull, valid && touch)) {
               SdfSample smp;
-              sdf_finish<false>(O, ix, corner, smp);
+              if (ANY && O.kind == kObjMesh)
+                smp = msmp;
+              else
+                sdf_finish<false>(O, ix, corner, smp);
               PointState ps;
               point_state(smp, r, rdil, ps);
               float n[3], sr[3];
@@ -561,7 +581,10 @@ __global__ void __launch_bounds__(kTW * 32, 4) tstep_kernel(FusedArgs a) {
               }
             } else {
               SdfSample smp;
-              sdf_finish<true>(O, ix, corner, smp);
+              if (ANY && O.kind == kObjMesh)
+                smp = msmp;
+              else
+                sdf_finish<true>(O, ix, corner, smp);
               PointState ps;
               point_state(smp, r, rdil, ps);
               const bool kap = ps.phi_hat < 0.0f;
@@ -730,21 +753,21 @@ __global__ void __launch_bounds__(kTW * 32, 4) tstep_kernel(FusedArgs a) {
   }
 }
 
-template <int MODE>
+template <int MODE, bool ANY>
 cudaError_t launch_tstep_mode(const FusedArgs& a, cudaStream_t st) {
   static int blocks_per_sm[64] = {0};
   int dev = 0;
   cudaGetDevice(&dev);
   int& bps = blocks_per_sm[dev & 63];
   if (bps <= 0) {
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, tstep_kernel<MODE>, kTW * 32, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, tstep_kernel<MODE, ANY>, kTW * 32, 0);
     if (e != cudaSuccess) return e;
     if (bps < 1) bps = 1;
   }
   long long grid = (long long)device_sm_count() * bps;
   if (grid > a.B) grid = a.B;
   if (grid < 1) return cudaSuccess;
-  tstep_kernel<MODE><<<(int)grid, kTW * 32, 0, st>>>(a);
+  tstep_kernel<MODE, ANY><<<(int)grid, kTW * 32, 0, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -753,8 +776,11 @@ cudaError_t launch_tstep_mode(const FusedArgs& a, cudaStream_t st) {
 cudaError_t launch_tstep(int mode, const FusedArgs& a, cudaStream_t st) {
   if (a.B <= 0) return cudaSuccess;
   if (a.P.sim_steps < 1 || a.P.sim_steps > kTSteps) return cudaErrorInvalidValue;
-  if (mode == kModeLossGrad) return launch_tstep_mode<kModeLossGrad>(a, st);
-  return launch_tstep_mode<kModeOptimize>(a, st);
+  if (a.any_mesh)
+    return mode == kModeLossGrad ? launch_tstep_mode<kModeLossGrad, true>(a, st)
+                                 : launch_tstep_mode<kModeOptimize, true>(a, st);
+  return mode == kModeLossGrad ? launch_tstep_mode<kModeLossGrad, false>(a, st)
+                               : launch_tstep_mode<kModeOptimize, false>(a, st);
 }
 
 }  // namespace fg

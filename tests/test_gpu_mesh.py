@@ -166,9 +166,25 @@ def test_mesh_scenes_refused_where_unsupported(fg, sphere_case):
     c = sphere_case
     q = torch.tensor(c.q0[:4], device=_dev())
     with pytest.raises(_lib.FgError):
-        fg.loss_and_grad(c.hand, c.scene, q, dict(c.params, sim_steps=1), 0.004)
-    with pytest.raises(_lib.FgError):
         fg.optimize_step_plain(c.hand, c.scene, q.clone(), c.params, 0, 10, 1)
+
+
+@pytest.mark.parametrize("T", [1, 2])
+def test_mesh_tstep_matches_oracle(fg, T):
+    """The T-step metric on a mesh object (an icosphere of 320 faces): every point
+    re-queried (BVH, Phong SDF) at each simulation's predicted pose for T steps, against
+    the oracle's evaluate_tstep."""
+    w = synth.tiny_sphere_workload(n_cand=12)
+    c = Case(fg, w.hand, [SM.icosphere(0.04, 2)], w.obj_of_cand, w.q0, w.params)
+    params = dict(w.params, sim_steps=T)
+    S = O.Setup(w.hand, c.objects, params)
+    loss, grad = fg.loss_and_grad(c.hand, c.scene, torch.tensor(w.q0, device=_dev()), params, 0.004,
+                                  obj_of_cand=c.oc)
+    ref = O.batch_loss_and_grad(S, w.q0, w.obj_of_cand, 0.004)
+    clean = O.clean_candidates(S.hand, S.objs[0], w.q0, 0.004, S.prm)
+    assert clean.sum() >= 8
+    assert (ref["N"].sum(axis=1) > 0).sum() >= 3
+    _compare(loss.cpu().numpy(), grad.cpu().numpy(), ref, clean)
 
 
 def test_mesh_full_size_sampled_parity(fg):
