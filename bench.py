@@ -114,16 +114,27 @@ def load_traffic(kernel_tag: str):
     return None
 
 
-def build_workload(device, rank, n_obj=8, per_obj=1024, grid_n=128):
-    """The benchmark workload for one rank.  Weak scaling: every rank holds the same
-    objects and its own share of the global candidate set (rank 0 the recipe's
-    candidates, rank k > 0 candidates drawn from seed base + 100 + k), so ranks
-    never exchange data."""
+WORKLOADS = ("superquadric8", "polyhedra32", "sweep256")
+
+
+def build_workload(device, rank, kind="superquadric8"):
+    """The benchmark workload for one rank: by default the 8 superquadrics (128^3), the
+    4-finger hand and 8,192 candidates; "polyhedra32" the 32 polyhedra (128^3) with the
+    5-finger hand and 131,072 candidates; "sweep256" the 256 objects (192^3) with the
+    5-finger hand and 65,536 candidates.  Weak scaling: every rank holds the same objects
+    and its own share of the global candidate set (rank 0 the recipe's candidates, rank
+    k > 0 candidates drawn from seed base + 100 + k), so ranks never exchange data."""
     import synth
-    w = synth.batched_superquadric_workload(n_obj=n_obj, per_obj=per_obj, grid_n=grid_n, device=device)
+    if kind == "polyhedra32":
+        w = synth.polyhedra_workload(device=device)
+    elif kind == "sweep256":
+        w = synth.sweep_workload(device=device)
+    else:
+        w = synth.batched_superquadric_workload(device=device)
     if rank:
         rng = np.random.default_rng(synth.workloads.SEED_BASE + 100 + rank)
         from synth.candidates import sample_candidates
+        per_obj = w.B // len(w.objects)
         q = [sample_candidates(rng, w.hand, per_obj, o["bound_radius"] + 0.06) for o in w.objects]
         w.q0 = np.concatenate(q)
     return w
@@ -253,6 +264,8 @@ def main():
     ap.add_argument("--serving-rate", type=float, default=200.0)
     ap.add_argument("--tstep", default="",
                     help="comma-separated T: also time the T-step metric (SDF re-queried for T steps) on this workload")
+    ap.add_argument("--workload", default="superquadric8", choices=WORKLOADS,
+                    help="superquadric8 (the benchmark configuration), polyhedra32 or sweep256 (larger configurations)")
     ap.add_argument("--gs", action="store_true",
                     help="also time the Gauss-Seidel form (constraints projected in point order) on this workload")
     ap.add_argument("--quality", action="store_true",
@@ -283,7 +296,7 @@ def main():
     import paper_2306_08132_gb300 as fg
     from oracle import fastgraspd_oracle as O   # rank 0 cpu_baseline leg only
 
-    w = build_workload(dev, rank)
+    w = build_workload(dev, rank, args.workload)
     hand = fg.Hand.from_synth(w.hand)
     sdfs = [fg.Sdf.from_synth(o) for o in w.objects]
     scene = fg.Scene(sdfs)
@@ -557,8 +570,10 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": "candidate-steps/s", "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": w.name, "objects": len(w.objects), "grid": "128^3 f32",
-                           "hand": "4-finger, 17 links, %d points" % w.hand["P"], "candidates": w.B * world,
+                "config": {"workload": w.name, "objects": len(w.objects),
+                           "grid": "%d^3 f32" % w.objects[0]["grid"].shape[0],
+                           "hand": "%d-finger, %d links, %d points" % (w.hand["kind"], w.hand["L"], w.hand["P"]),
+                           "candidates": w.B * world,
                            "inner_steps_per_launch": S_in, "state": "q reset to the initial candidates each step",
                            "l2": "flushed between timed steps (256 MiB write)", "parallelism": "dp%d" % world,
                            "fused_config": {"warps_per_candidate": cfgs[best_cfg][0],
