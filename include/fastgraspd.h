@@ -214,7 +214,9 @@ fg_status fg_contact_wrench(const fg_hand* hand, const fg_scene* scene, const in
 /* Loss and gradient (Eqs. 2-4, Sec. III-C leaky rule) at dilation r_dil,
  * forward and adjoint fused in one kernel (the adjoint recomputes the forward
  * per point; nothing per point is stored).  loss: [B]; grad: [B][D] nullable
- * (NULL: the loss alone, without the adjoint sweep). */
+ * (NULL: the loss alone, without the adjoint sweep).  params.sim_steps >= 1
+ * selects the T-step form and params.gauss_seidel = 1 the Gauss-Seidel form
+ * (each its own kernel, same arguments); grid and mesh objects. */
 fg_status fg_loss_and_grad(const fg_hand* hand, const fg_scene* scene, const int* obj_of_cand,
                            const float* q, int B, const fg_params* host_params, float r_dil,
                            float* loss, float* grad, void* stream);
@@ -223,7 +225,7 @@ fg_status fg_loss_and_grad(const fg_hand* hand, const fg_scene* scene, const int
  * forward + adjoint + update kernel.  q: [B][D] in/out.  The dilation of global
  * step k = step + s is r0 (schedule 0) or r0 * max(0, 1 - k / (total_steps - 1))
  * (schedule 1).  loss (nullable, [B]): loss at the last step, evaluated before
- * its update. */
+ * its update.  The T-step and Gauss-Seidel forms as for fg_loss_and_grad. */
 fg_status fg_optimize_step(const fg_hand* hand, const fg_scene* scene, const int* obj_of_cand,
                            float* q, int B, const fg_params* host_params, int step, int total_steps,
                            int nsteps, float* loss, void* stream);
@@ -232,7 +234,9 @@ fg_status fg_optimize_step(const fg_hand* hand, const fg_scene* scene, const int
  * form: FK links -> point transform -> SDF query -> contact forward -> loss ->
  * contact adjoint -> link reduction -> FK adjoint + update, with the per-point
  * intermediates in `workspace` (device memory, >= fg_plain_workspace_size
- * bytes, 256-byte aligned).  Comparison baseline for the fused kernel. */
+ * bytes, 256-byte aligned).  Comparison baseline for the fused kernel: the
+ * one-step Jacobi form on grid objects (FG_ERR_INVALID for the other forms and
+ * for mesh objects). */
 fg_status fg_plain_workspace_size(const fg_hand* hand, int B, size_t* bytes);
 fg_status fg_optimize_step_plain(const fg_hand* hand, const fg_scene* scene, const int* obj_of_cand,
                                  float* q, int B, const fg_params* host_params, int step,

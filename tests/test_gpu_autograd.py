@@ -132,3 +132,46 @@ def test_autograd_tstep_gradient_matches_oracle_finite_differences(fg):
         assert rel < 1e-3, (b, rel)
         compared += 1
     assert compared >= 16, compared
+
+
+def test_autograd_gauss_seidel_gradient_matches_oracle_finite_differences(fg):
+    """The Gauss-Seidel form through GraspLoss against central finite differences of the
+    oracle's branch-frozen Gauss-Seidel loss (non-contact constraints as the leaky
+    surrogate with the state frozen at the decision point), on a mesh object."""
+    from synth import meshes as SM
+    w = synth.tiny_sphere_workload(n_cand=16)
+    objs = [SM.icosphere(0.04, 2)]
+    params = dict(w.params, gauss_seidel=1)
+    S = O.Setup(w.hand, objs, params)
+    hand = fg.Hand.from_synth(w.hand)
+    scene = fg.Scene([fg.Sdf.from_synth(objs[0])])
+    q = torch.tensor(w.q0, device="cuda", requires_grad=True)
+    fg.grasp_loss(q, hand, scene, params, 0.004).sum().backward()
+    g_gpu = q.grad.cpu().numpy().astype(np.float64)
+    compared = 0
+    for b in range(w.B):
+        if not O.clean_candidates(S.hand, S.objs[0], w.q0[b:b + 1], 0.004, S.prm)[0]:
+            continue
+        qb = torch.tensor(w.q0[b:b + 1].astype(np.float64))
+        base = O.evaluate_gs(S.hand, S.objs[0], qb, 0.004, S.prm)
+        if compared < 2 and base["N"].sum() == 0:
+            continue                                   # compare the touching candidates first
+        h = 1e-8
+        D = qb.shape[1]
+        E = torch.eye(D, dtype=torch.float64) * h
+        rep = lambda t: t.repeat((2 * D,) + (1,) * (t.dim() - 1))
+        dec = O.GSDecisions()
+        for k, v in base["dec"].__dict__.items():
+            if isinstance(v, dict):
+                setattr(dec, k, {kk: rep(vv) for kk, vv in v.items()})
+            elif isinstance(v, torch.Tensor):
+                setattr(dec, k, rep(v))
+        L = O.evaluate_gs(S.hand, S.objs[0], torch.cat([qb + E, qb - E]), 0.004, S.prm, dec=dec,
+                          anchor_mode=True)["L"]
+        fd = ((L[:D] - L[D:]) / (2 * h)).numpy()
+        rel = np.linalg.norm(g_gpu[b] - fd) / max(np.linalg.norm(fd), 1e-6)
+        assert rel < 1e-3, (b, rel)
+        compared += 1
+        if compared == 4:
+            break
+    assert compared >= 3, compared
