@@ -59,8 +59,8 @@ struct GsSmem {
   float4 frame4[kMaxLinks][3];
   float q[64];
   float grad[64];
-  float4 cw[kMaxCullChunks];       // chunk bounding sphere in world coordinates (centre, radius)
   float lb[kMaxCullChunks];        // lower bound of phi_hat over the chunk (-inf: never culled)
+  float reach[kMaxCullChunks][kSims];   // |c - x~_m| + R: lever bound of the chunk's points in simulation m
   float sfin[kSims][6];            // final state per simulation
   float afin[kSims][6];            // dL/d(final state)
   float red[kSims][8];             // per simulation: sum f (3), sum d x f (3), contacts, penetration
@@ -432,7 +432,13 @@ __global__ void __launch_bounds__(kGW * 32, 3) gs_kernel(FusedArgs a) {
           cwj = make_float4(cw[0], cw[1], cw[2], cs.w + slack);
         }
         S.lb[j] = lbj;
-        S.cw[j] = cwj;
+#pragma unroll
+        for (int m = 0; m < kSims; ++m) {
+          float xt[3];
+          sim_pred(m, dtV, xt);
+          const float rel[3] = {cwj.x - xt[0], cwj.y - xt[1], cwj.z - xt[2]};
+          S.reach[j][m] = sqrtf(rel[0] * rel[0] + rel[1] * rel[1] + rel[2] * rel[2]) + cwj.w;
+        }
       }
       __syncthreads();
 
@@ -444,16 +450,13 @@ __global__ void __launch_bounds__(kGW * 32, 3) gs_kernel(FusedArgs a) {
         float st[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
         float Wl[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f}, pen = 0.0f;
         int cnt = 0;
+        // |x~ + dx| and |dth| of the current state (recomputed when a projection changes it)
+        float ex = sqrtf(xt[0] * xt[0] + xt[1] * xt[1] + xt[2] * xt[2]), en = 0.0f;
         for (int j = 0; j < nch; ++j) {
           float* sn = snap(dyn, j, m);
           if (lane < 6) sn[lane] = pick6(st, lane);
           // largest |n . D| over the chunk: |x~ + dx| + |dth| (|c - x~| + R)
-          const float4 cw = S.cw[j];
-          const float e[3] = {xt[0] + st[0], xt[1] + st[1], xt[2] + st[2]};
-          const float rel[3] = {cw.x - xt[0], cw.y - xt[1], cw.z - xt[2]};
-          const float bound = sqrtf(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]) +
-                              sqrtf(st[3] * st[3] + st[4] * st[4] + st[5] * st[5]) *
-                                  (sqrtf(rel[0] * rel[0] + rel[1] * rel[1] + rel[2] * rel[2]) + cw.w);
+          const float bound = fmaf(en, S.reach[j][m], ex);
           const float lbj = S.lb[j];
           unsigned mask = 0u;
           const bool culled = lbj - bound * (1.0f + 1e-5f) - (1e-6f + 1e-5f * fabsf(lbj)) > 0.0f;
@@ -491,6 +494,11 @@ __global__ void __launch_bounds__(kGW * 32, 3) gs_kernel(FusedArgs a) {
           }
           if (lane == 0) sn[12] = __uint_as_float(mask);
           cnt += __popc(mask);
+          if (mask) {
+            const float e[3] = {xt[0] + st[0], xt[1] + st[1], xt[2] + st[2]};
+            ex = sqrtf(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+            en = sqrtf(st[3] * st[3] + st[4] * st[4] + st[5] * st[5]);
+          }
         }
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
