@@ -13,7 +13,8 @@
 // One CTA of 7 warps per candidate (persistent over candidates and steps):
 //
 //   FK, cull   warp 0 frames; per 32-point chunk a lower bound of phi_hat over
-//              its bounding sphere (min-pyramid)
+//              its bounding sphere (min-pyramid; for a mesh the flat distance of
+//              its centre) and, per simulation, a bound on its points' levers
 //   forward    warp m runs simulation m over the chunks in order.  A chunk whose
 //              bound exceeds the largest displacement the state can give any
 //              of its points holds no contact and is skipped.  Otherwise the
