@@ -117,9 +117,9 @@ def load_traffic(kernel_tag: str):
 WORKLOADS = ("superquadric8", "polyhedra32", "sweep256")
 
 
-def build_workload(device, rank, kind="superquadric8"):
+def build_workload(device, rank, kind="superquadric8", n_obj=8, per_obj=1024, grid_n=128):
     """The benchmark workload for one rank: by default the 8 superquadrics (128^3), the
-    4-finger hand and 8,192 candidates; "polyhedra32" the 32 polyhedra (128^3) with the
+    4-finger hand and 8,192 candidates (sizes adjustable for tests); "polyhedra32" the 32 polyhedra (128^3) with the
     5-finger hand and 131,072 candidates; "sweep256" the 256 objects (192^3) with the
     5-finger hand and 65,536 candidates.  Weak scaling: every rank holds the same objects
     and its own share of the global candidate set (rank 0 the recipe's candidates, rank
@@ -130,7 +130,7 @@ def build_workload(device, rank, kind="superquadric8"):
     elif kind == "sweep256":
         w = synth.sweep_workload(device=device)
     else:
-        w = synth.batched_superquadric_workload(device=device)
+        w = synth.batched_superquadric_workload(n_obj=n_obj, per_obj=per_obj, grid_n=grid_n, device=device)
     if rank:
         rng = np.random.default_rng(synth.workloads.SEED_BASE + 100 + rank)
         from synth.candidates import sample_candidates

@@ -107,8 +107,8 @@ typedef struct {
  * 1 = they are projected one after another in point order, each seeing the
  * object displaced by the corrections before it (Sec. III-C: "a Gauss-Seidel
  * step" over the constraints of Eq. 1), and applied in full.  Gauss-Seidel is
- * accepted by fg_loss_and_grad and fg_optimize_step on grid and mesh objects,
- * for hands of at most 8,192 points (FG_ERR_INVALID elsewhere). */
+ * accepted by fg_contact_wrench, fg_loss_and_grad and fg_optimize_step on grid
+ * and mesh objects, for hands of at most 8,192 points (FG_ERR_INVALID elsewhere). */
 typedef struct {
   float alpha_leak;
   float dt;
@@ -206,7 +206,9 @@ fg_status fg_sdf_query(const fg_sdf* sdf, const float* pts, int n, float r_dil, 
  * wrench[B][7][6] = sum over contacts of (f, d x f), the summed position
  * corrections times mass (before averaging); ncontact[B][7] = number of points
  * with phi_m < 0; contact_bits (nullable) [B][7][ceil(P/32)], bit (i % 32) of
- * word i / 32 set when point i is in contact. */
+ * word i / 32 set when point i is in contact.  With params.gauss_seidel = 1: the
+ * sums of the corrections the sweep applied (m dx, I dth), the points it
+ * projected and their bits. */
 fg_status fg_contact_wrench(const fg_hand* hand, const fg_scene* scene, const int* obj_of_cand,
                             const float* q, int B, const fg_params* host_params, float r_dil,
                             float* wrench, int* ncontact, uint32_t* contact_bits, void* stream);

@@ -425,7 +425,10 @@ fg_status fg_contact_wrench(const fg_hand* h, const fg_scene* sc, const int* oc,
                             const fg_params* p, float r, float* wrench, int* ncontact, uint32_t* bits,
                             void* stream) {
   fg_status st = check_common("fg_contact_wrench", h, sc, B, p);
-  if (st == FG_OK) st = check_one_step("fg_contact_wrench", p);
+  if (st == FG_OK && p->sim_steps != 0)
+    st = invalid("fg_contact_wrench: params.sim_steps must be 0 here (the T-step metric: fg_loss_and_grad, "
+                 "fg_optimize_step)");
+  if (st == FG_OK && p->gauss_seidel) st = check_gs("fg_contact_wrench", h, sc);
   if (st != FG_OK) return st;
   if (B == 0) return FG_OK;
   if (!q || !wrench || !ncontact) return invalid("fg_contact_wrench: NULL buffer");
@@ -445,6 +448,9 @@ fg_status fg_contact_wrench(const fg_hand* h, const fg_scene* sc, const int* oc,
   a.wrench = wrench;
   a.ncontact = ncontact;
   a.bits = bits;
+  if (a.P.gauss_seidel)
+    return cuda_status(launch_gs(kModeWrench, a, h->host.nchunks, (cudaStream_t)stream),
+                       "fg_contact_wrench (Gauss-Seidel)");
   return cuda_status(launch_fused(kModeWrench, a, h, (cudaStream_t)stream), "fg_contact_wrench");
 }
 

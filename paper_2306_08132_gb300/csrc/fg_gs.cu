@@ -377,7 +377,10 @@ __global__ void __launch_bounds__(kGW * 32, 3) gs_kernel(FusedArgs a) {
     __syncthreads();
     if (S.bad_object) {
       const float nan = __int_as_float(0x7fc00000);
-      if (MODE == kModeLossGrad) {
+      if (MODE == kModeWrench) {
+        for (int idx = tid; idx < kSims * 6; idx += kGW * 32) a.wrench[(size_t)c * kSims * 6 + idx] = nan;
+        if (tid < kSims) a.ncontact[(size_t)c * kSims + tid] = -1;
+      } else if (MODE == kModeLossGrad) {
         if (tid == 0) a.loss[c] = nan;
         if (a.grad && tid < D) a.grad[(size_t)c * D + tid] = nan;
       } else if (a.loss && tid == 0) {
@@ -516,6 +519,18 @@ __global__ void __launch_bounds__(kGW * 32, 3) gs_kernel(FusedArgs a) {
         }
       }
       __syncthreads();
+      if (MODE == kModeWrench) {
+        // the sums of the corrections applied, the points projected, and their lanes per chunk
+        for (int idx = tid; idx < kSims * 6; idx += kGW * 32)
+          a.wrench[(size_t)c * kSims * 6 + idx] = S.red[idx / 6][idx % 6];
+        if (tid < kSims) a.ncontact[(size_t)c * kSims + tid] = (int)S.red[tid][6];
+        if (a.bits)
+          for (int idx = tid; idx < kSims * nch; idx += kGW * 32) {
+            const int m = idx / nch, j = idx - m * nch;
+            a.bits[((size_t)c * kSims + m) * nch + j] = __float_as_uint(snap(dyn, j, m)[12]);
+          }
+        continue;
+      }
 
       // ---------------------------------------------------------------- loss
       if (warp == 0) {
@@ -767,9 +782,12 @@ cudaError_t launch_gs_mode(const FusedArgs& a, int nchunks, cudaStream_t st) {
 cudaError_t launch_gs(int mode, const FusedArgs& a, int nchunks, cudaStream_t st) {
   if (a.B <= 0) return cudaSuccess;
   if (nchunks < 1 || nchunks > kMaxCullChunks) return cudaErrorInvalidValue;
-  if (a.any_mesh)
+  if (a.any_mesh) {
+    if (mode == kModeWrench) return launch_gs_mode<kModeWrench, true>(a, nchunks, st);
     return mode == kModeLossGrad ? launch_gs_mode<kModeLossGrad, true>(a, nchunks, st)
                                  : launch_gs_mode<kModeOptimize, true>(a, nchunks, st);
+  }
+  if (mode == kModeWrench) return launch_gs_mode<kModeWrench, false>(a, nchunks, st);
   return mode == kModeLossGrad ? launch_gs_mode<kModeLossGrad, false>(a, nchunks, st)
                                : launch_gs_mode<kModeOptimize, false>(a, nchunks, st);
 }

@@ -171,10 +171,10 @@ def test_gs_is_refused_where_unsupported(fg, tiny):
     q = torch.tensor(w.q0[:4], device=_dev())
     params = dict(w.params, gauss_seidel=1)
     with pytest.raises(_lib.FgError) as e:
-        fg.contact_wrench(tiny.hand, tiny.scene, q, params, 0.004)
+        fg.optimize_step_plain(tiny.hand, tiny.scene, q.clone(), params, 0, 10, 1)
     assert e.value.name == "FG_ERR_INVALID"
     with pytest.raises(_lib.FgError):
-        fg.optimize_step_plain(tiny.hand, tiny.scene, q.clone(), params, 0, 10, 1)
+        fg.contact_wrench(tiny.hand, tiny.scene, q, dict(params, sim_steps=1), 0.004)
     with pytest.raises(_lib.FgError):
         fg.loss_and_grad(tiny.hand, tiny.scene, q, dict(params, sim_steps=2), 0.004)
     with pytest.raises(_lib.FgError):
@@ -262,3 +262,27 @@ def test_gs_on_mesh_objects(fg):
     clean = case.clean(S, w.q0, 0.004)
     assert clean.sum() >= 12 and (ref["N"][clean] >= 2).any()
     _compare(loss.cpu().numpy(), grad.cpu().numpy(), ref, clean)
+
+
+def test_gs_contact_wrench_matches_oracle(fg, tiny):
+    """fg_contact_wrench in the Gauss-Seidel form: per simulation the sums of the applied
+    corrections (f, d x f), the number of points projected and their bits, against the
+    oracle's sweep (counts and bits bit-exact on clean candidates)."""
+    w, r = tiny.w, 0.004
+    params = dict(w.params, gauss_seidel=1)
+    S = tiny.oracle(params)
+    W, N, bits = fg.contact_wrench(tiny.hand, tiny.scene, torch.tensor(w.q0, device=_dev()), params, r,
+                                   obj_of_cand=tiny.oc, want_bits=True)
+    torch.cuda.synchronize()
+    ref = O.batch_loss_and_grad(S, w.q0, w.obj_of_cand, r)
+    clean = tiny.clean(S, w.q0, r)
+    assert clean.sum() >= 0.5 * len(clean) and (ref["N"][clean] >= 2).any()
+    Wg, Ng, bw = W.cpu().numpy().astype(np.float64), N.cpu().numpy(), bits.cpu().numpy().view(np.uint32)
+    P = w.hand["P"]
+    for b in np.nonzero(clean)[0]:
+        assert np.array_equal(Ng[b], ref["N"][b].astype(np.int32)), b
+        for m in range(7):
+            got = np.unpackbits(bw[b, m].view(np.uint8), bitorder="little")[:P].astype(bool)
+            assert np.array_equal(got, ref["kappa"][b][:, m]), (b, m)
+        nrm = np.linalg.norm(ref["W"][b])
+        assert nrm == 0 or np.linalg.norm(Wg[b] - ref["W"][b]) / nrm < GRAD_TOL, b
