@@ -45,9 +45,17 @@ FUSED_SOURCES = ("fg_device.cuh", "fg_vec.cuh", "fg_fused_kernel.cuh", "fg_fused
                  "fastgraspd.h")
 
 
+def _code_only(text: str) -> str:
+    """C/C++/CUDA source without its comments and blank lines (string literals kept)."""
+    import re
+    pattern = re.compile(r'//[^\n]*|/\*.*?\*/|"(?:\\.|[^"\\])*"', re.S)
+    text = pattern.sub(lambda m: m.group(0) if m.group(0).startswith('"') else "", text)
+    return "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+
+
 def source_hash(names=None) -> str:
-    """Short hash of the sources and headers the library is built from (or of the
-    named files only)."""
+    """Short hash of the code (comments left out) of the sources and headers the
+    library is built from (or of the named files only)."""
     import hashlib
     h = hashlib.sha256()
     for f in sorted(_inputs()):
@@ -55,8 +63,8 @@ def source_hash(names=None) -> str:
             continue
         if f.endswith((".cu", ".cuh", ".h")):
             h.update(os.path.basename(f).encode())
-            with open(f, "rb") as fh:
-                h.update(fh.read())
+            with open(f, "r", encoding="utf-8") as fh:
+                h.update(_code_only(fh.read()).encode())
     return h.hexdigest()[:12]
 
 
