@@ -62,7 +62,6 @@ struct Builder {
     const int idx = (int)nodes.size();
     nodes.push_back(Node{});
     double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
-    double clo[3] = {1e300, 1e300, 1e300}, chi[3] = {-1e300, -1e300, -1e300};
     for (int i = begin; i < end; ++i) {
       const int f = order[i];
       for (int k = 0; k < 3; ++k) {
@@ -72,11 +71,6 @@ struct Builder {
           lo[a] = std::min(lo[a], c[a]);
           hi[a] = std::max(hi[a], c[a]);
         }
-      }
-      const double cc[3] = {centroid[f].x, centroid[f].y, centroid[f].z};
-      for (int a = 0; a < 3; ++a) {
-        clo[a] = std::min(clo[a], cc[a]);
-        chi[a] = std::max(chi[a], cc[a]);
       }
     }
     for (int a = 0; a < 3; ++a) {
@@ -89,13 +83,58 @@ struct Builder {
       nodes[idx].count = end - begin;
       return idx;
     }
-    int axis = 0;
-    for (int a = 1; a < 3; ++a)
-      if (chi[a] - clo[a] > chi[axis] - clo[axis]) axis = a;
-    const int mid = (begin + end) / 2;
-    auto key = [&](int f) { return axis == 0 ? centroid[f].x : (axis == 1 ? centroid[f].y : centroid[f].z); };
-    std::nth_element(order.begin() + begin, order.begin() + mid, order.begin() + end,
-                     [&](int a, int b) { return key(a) < key(b) || (key(a) == key(b) && a < b); });
+    // Split by the surface-area heuristic: over each axis, faces sorted by
+    // centroid, the split k minimising area(left box) k + area(right box) (n - k)
+    // (the expected number of faces a query visits is proportional to it).
+    const int n = end - begin;
+    int best_axis = 0, best_k = n / 2;
+    double best_cost = 1e300;
+    std::vector<int> sorted(n);
+    std::vector<double> right_area(n + 1);
+    auto box_area = [](const double lo[3], const double hi[3]) {
+      const double dx = hi[0] - lo[0], dy = hi[1] - lo[1], dz = hi[2] - lo[2];
+      return 2.0 * (dx * dy + dy * dz + dz * dx);
+    };
+    for (int axis = 0; axis < 3; ++axis) {
+      auto key = [&](int f) { return axis == 0 ? centroid[f].x : (axis == 1 ? centroid[f].y : centroid[f].z); };
+      std::copy(order.begin() + begin, order.begin() + end, sorted.begin());
+      std::sort(sorted.begin(), sorted.end(), [&](int a, int b) { return key(a) < key(b) || (key(a) == key(b) && a < b); });
+      double rlo[3] = {1e300, 1e300, 1e300}, rhi[3] = {-1e300, -1e300, -1e300};
+      for (int i = n - 1; i >= 1; --i) {             // right_area[i]: box of sorted[i..n)
+        for (int k = 0; k < 3; ++k) {
+          const Vec& p = V[F[3 * sorted[i] + k]];
+          const double c[3] = {p.x, p.y, p.z};
+          for (int a = 0; a < 3; ++a) {
+            rlo[a] = std::min(rlo[a], c[a]);
+            rhi[a] = std::max(rhi[a], c[a]);
+          }
+        }
+        right_area[i] = box_area(rlo, rhi);
+      }
+      double llo[3] = {1e300, 1e300, 1e300}, lhi[3] = {-1e300, -1e300, -1e300};
+      for (int i = 0; i < n - 1; ++i) {              // left box of sorted[0..i]
+        for (int k = 0; k < 3; ++k) {
+          const Vec& p = V[F[3 * sorted[i] + k]];
+          const double c[3] = {p.x, p.y, p.z};
+          for (int a = 0; a < 3; ++a) {
+            llo[a] = std::min(llo[a], c[a]);
+            lhi[a] = std::max(lhi[a], c[a]);
+          }
+        }
+        const double cost = box_area(llo, lhi) * (i + 1) + right_area[i + 1] * (n - i - 1);
+        if (cost < best_cost) {
+          best_cost = cost;
+          best_axis = axis;
+          best_k = i + 1;
+        }
+      }
+    }
+    auto best_key = [&](int f) {
+      return best_axis == 0 ? centroid[f].x : (best_axis == 1 ? centroid[f].y : centroid[f].z);
+    };
+    std::sort(order.begin() + begin, order.begin() + end,
+              [&](int a, int b) { return best_key(a) < best_key(b) || (best_key(a) == best_key(b) && a < b); });
+    const int mid = begin + best_k;
     build(begin, mid, depth + 1);                 // left child is idx + 1
     const int right = build(mid, end, depth + 1);
     nodes[idx].link = right;
