@@ -12,6 +12,13 @@ Lines: the fused path (value), the plain per-stage GPU form (plain), the same
 step end to end through host buffers (e2e), the roofline of the fused kernel,
 sampled SM clocks, and the FP64 oracle on the host cores (cpu_baseline).
 `--impl reference` times the oracle alone on the same workload.
+
+Optional legs on the same candidates: --gs (Gauss-Seidel projection), --tstep T
+(the T-step metric), --mesh (the objects as meshes with the Phong SDF; with --gs
+also that combination), --quality (contact area and epsilon), --serving N and
+--serving-sweep (request latency against offered load); --workload selects the
+larger polyhedra32 / sweep256 configurations; --profile-kernel runs a few
+launches of the selected kernel for ncu and exits.
 """
 
 from __future__ import annotations
