@@ -15,7 +15,9 @@ sampled SM clocks, and the FP64 oracle on the host cores (cpu_baseline).
 
 Optional legs on the same candidates: --gs (Gauss-Seidel projection), --tstep T
 (the T-step metric), --mesh (the objects as meshes with the Phong SDF; with --gs
-also that combination), --quality (contact area and epsilon), --serving N and
+also that combination), --quality (contact area and epsilon), --order-quality (the
+grasps of a whole optimisation in the Jacobi and the Gauss-Seidel order, compared
+by their quality metrics), --serving N and
 --serving-sweep (request latency against offered load); --workload selects the
 larger polyhedra32 / sweep256 configurations; --profile-kernel runs a few
 launches of the selected kernel for ncu and exits.
@@ -224,6 +226,70 @@ def run_serving(fg, n_requests: int, rates_hz, device, budget_bytes: int, steps_
     return out
 
 
+def run_order_quality(fg, w, hand, scene, oc, q0, device, lrs, steps_per_launch: int = 10):
+    """Jacobi against Gauss-Seidel projection, judged by the grasps they produce: the
+    same initial candidates optimised over the workload's whole schedule (w.steps
+    steps, dilation from r0 down to 0) in each order and at each learning rate of lrs
+    (the paper's 1e-3 moves a candidate by decimetres per step in SI units, so smaller
+    rates are swept beside it), then the quality metrics of the final grasps at the
+    5 mm contact threshold: contact area (area-weighted surface samples), intersection
+    volume (3 mm interior lattice, phi < 0), epsilon over 1,024 unit directions (8-edge
+    cones, mu = 0.5, torque scaled by 1/rho of each object), contacts, and the loss of
+    the last step."""
+    import torch
+    import synth as _synth
+    areas = torch.tensor(w.hand["point_area"], device=device)
+    ih = _synth.interior_hand(w.hand["kind"], 0.003)
+    ihand = fg.Hand.from_synth(ih)
+    vols = torch.tensor(ih["point_volume"], device=device)
+    dirs = torch.tensor(_synth.unit_directions(1024), device=device)
+    oc_np = np.asarray(w.obj_of_cand)
+    groups = [torch.tensor(np.nonzero(oc_np == k)[0], device=device) for k in range(len(w.objects))]
+
+    def med(x):
+        return float(x.double().median())
+
+    def mean(x):
+        return float(x.double().mean())
+
+    runs = []
+    for lr in lrs:
+        eps_of = {}
+        for name, gs in (("jacobi", 0), ("gauss_seidel", 1)):
+            prm = dict(w.params, gauss_seidel=gs, lr=lr)
+            q = q0.clone()
+            loss = torch.empty(w.B, device=device)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for k in range(0, w.steps, steps_per_launch):
+                fg.optimize_step(hand, scene, q, prm, k, w.steps, min(steps_per_launch, w.steps - k),
+                                 obj_of_cand=oc, loss=loss)
+            e1.record()
+            torch.cuda.synchronize()
+            ca = fg.contact_measure(hand, scene, q, areas, 0.005, obj_of_cand=oc)
+            iv = fg.contact_measure(ihand, scene, q, vols, 0.0, obj_of_cand=oc)
+            eps = torch.empty(w.B, device=device)
+            nc = torch.empty(w.B, device=device, dtype=torch.int32)
+            for k, sel in enumerate(groups):
+                e, n = fg.grasp_epsilon(hand, scene, q[sel].contiguous(), 0.005, 0.5, 8,
+                                        1.0 / float(w.objects[k]["bound_radius"]), dirs,
+                                        obj_of_cand=oc[sel].contiguous())
+                eps[sel] = e
+                nc[sel] = n
+            torch.cuda.synchronize()
+            eps_of[name] = eps
+            touching = nc > 0
+            runs.append({"lr": lr, "order": name, "optimise_s": e0.elapsed_time(e1) / 1000.0,
+                         "loss_median": med(loss), "with_contact_frac": mean(touching),
+                         "contacts_mean": mean(nc), "contact_area_cm2_mean": mean(ca * 1e4),
+                         "intersection_volume_cm3_mean": mean(iv * 1e6),
+                         "force_closure_frac": mean(eps > 0),
+                         "epsilon_median_of_force_closure": med(eps[eps > 0]) if bool((eps > 0).any()) else None})
+        runs.append({"lr": lr, "gs_epsilon_above_jacobi_frac": mean(eps_of["gauss_seidel"] > eps_of["jacobi"])})
+    setup = ("%d candidates, %d steps (dilation %.0f mm -> 0), threshold 5 mm, 1,024 directions, 8-edge cones, "
+             "mu 0.5, interior lattice 3 mm (%d samples)" % (w.B, w.steps, 1000.0 * w.params["r0"], ih["P"]))
+    return {"setup": setup, "runs": runs}
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -278,6 +344,11 @@ def main():
     ap.add_argument("--quality", action="store_true",
                     help="also time the grasp-quality metrics (contact area, epsilon over 1,024 directions) "
                          "over the workload's candidates")
+    ap.add_argument("--order-quality", action="store_true",
+                    help="also optimise the candidates over the whole schedule in the Jacobi and the Gauss-Seidel "
+                         "order and compare the quality metrics of the final grasps")
+    ap.add_argument("--order-quality-lr", default="1e-3,1e-5,1e-6,1e-7",
+                    help="learning rates of the --order-quality runs")
     ap.add_argument("--mesh", action="store_true",
                     help="also time the fused step on mesh objects (the same superquadrics as watertight meshes, "
                          "queried through the BVH with the Phong SDF)")
@@ -552,6 +623,11 @@ def main():
             mesh["gauss_seidel"] = {"ms_per_step": mg_ms, "value": cand_steps / (mg_ms / 1000.0),
                                     "unit": "candidate-steps/s"}
 
+    order_quality = None
+    if args.order_quality:
+        order_quality = run_order_quality(fg, w, hand, scene, oc, q0, dev,
+                                          [float(x) for x in args.order_quality_lr.split(",")])
+
     serving, sweep = None, None
     if args.serving > 0:
         free, _ = torch.cuda.mem_get_info()
@@ -591,7 +667,7 @@ def main():
                 "plain": plain, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
                 "latency": None if serving is None else {"p50_s": serving["p50_s"], "p99_s": serving["p99_s"]},
                 "serving": serving, "serving_sweep": sweep, "tstep": tstep, "gauss_seidel": gs, "mesh": mesh,
-                "quality": quality,
+                "quality": quality, "order_quality": order_quality,
                 "gpu_launches": args.steps * 1, "clocks": clocks, "wall_s_timed_region": wall,
                 "per_step_ms": {"min": float(np.min(ms)), "median": float(np.median(ms)), "max": float(np.max(ms))}}
         print(json.dumps(line))
