@@ -29,6 +29,11 @@
  *  - Handles (fg_hand, fg_sdf, fg_scene) own device copies of their data and are
  *    immutable after creation; they may be shared by concurrent streams.  Destroy
  *    a handle only after the work that uses it has completed.
+ *  - The persistent kernels take candidates from a counter that each launch
+ *    draws from a pool of 1,024 and leaves at zero when it ends.  Calls may run on
+ *    concurrent streams (fewer than 1,024 launches of one kind in flight at once).
+ *    A call captured in a CUDA graph keeps the counter it drew at capture, so one
+ *    graph must not be replayed on two streams at once (capture one per stream).
  *  - Configuration vector layout, per candidate (row-major [B][D]):
  *      q = (t_x, t_y, t_z, w_x, w_y, w_z, theta_0 .. theta_{J-1}),  D = 6 + J,
  *    t the palm origin (metres), w the palm rotation vector (R_b = Exp(w)),

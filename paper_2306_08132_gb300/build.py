@@ -41,8 +41,8 @@ def _inputs() -> list[str]:
 
 
 # Sources that define the fused kernel (its profile stays valid while they are unchanged).
-FUSED_SOURCES = ("fg_device.cuh", "fg_vec.cuh", "fg_fused_kernel.cuh", "fg_fused.cu", "fg_fused_opt.cu", "fg_internal.h",
-                 "fastgraspd.h")
+FUSED_SOURCES = ("fg_device.cuh", "fg_vec.cuh", "fg_fused_kernel.cuh", "fg_work.cuh", "fg_fused.cu", "fg_fused_opt.cu",
+                 "fg_internal.h", "fastgraspd.h")
 
 
 def _code_only(text: str) -> str:

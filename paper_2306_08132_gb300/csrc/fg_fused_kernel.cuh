@@ -1,5 +1,5 @@
 // Fused grasp-search step: one CTA of NW warps per candidate, persistent over
-// candidates and steps.  Per step:
+// candidates (claimed from a counter, fg_work.cuh) and steps.  Per step:
 //
 //   FK       warp 0, one lane per link, level by level -> link frames (smem)
 //   sweep 1  point -> SDF -> 7 plane-linearised contacts; a warp that has a
@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include "fg_internal.h"
+#include "fg_work.cuh"
 
 namespace fg {
 
@@ -47,6 +48,7 @@ struct FusedSmem {
   float uacc[kMaxUnits][6];        // per work unit: sum g, sum (p - t) x g
   float Wtot[kSims][8];
   float loss;
+  int cand;                        // the candidate claimed by this CTA
   int bad_object;
   int n_active;
   int next_unit;                   // adjoint sweep: next unclaimed work unit
@@ -265,8 +267,9 @@ __global__ void __launch_bounds__(NW * 32, MINB) fused_step_kernel(FusedArgs a) 
   const HandDev& H = S.H;
   const ParamsDev& Pm = S.Pm;
 
-  for (int c = blockIdx.x; c < a.B; c += gridDim.x) {
-    __syncthreads();
+  for (;;) {
+    const int c = next_candidate(a.work, &S.cand);
+    if (c >= a.B) break;
     if (tid == 0) {
       if (MODE == kModeQueue) {
         // candidate c of the round belongs to the slot whose range holds it
@@ -664,6 +667,7 @@ __global__ void __launch_bounds__(NW * 32, MINB) fused_step_kernel(FusedArgs a) 
       if (tid < D) S.qout[(size_t)cl * D + tid] = S.q[tid];
     }
   }
+  work_done(a.work);
 }
 
 // Launch of one compiled configuration: a persistent grid of (SMs x resident
@@ -682,7 +686,10 @@ cudaError_t launch_fused_cfg(const FusedArgs& a, cudaStream_t st) {
   long long grid = (long long)device_sm_count() * bps;
   if (grid > a.B) grid = a.B;
   if (grid < 1) return cudaSuccess;
-  fused_step_kernel<MODE, NW, MINB, PPT, ANY><<<(int)grid, NW * 32, 0, st>>>(a);
+  FusedArgs b = a;
+  cudaError_t e = work_pair(&b.work);
+  if (e != cudaSuccess) return e;
+  fused_step_kernel<MODE, NW, MINB, PPT, ANY><<<(int)grid, NW * 32, 0, st>>>(b);
   return cudaGetLastError();
 }
 

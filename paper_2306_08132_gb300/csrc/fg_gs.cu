@@ -67,6 +67,7 @@ struct GsSmem {
   float red[kSims][8];             // per simulation: sum f (3), sum d x f (3), contacts, penetration
   float lacc[kGW][kMaxLinks][6];   // per warp, per link: sum g, sum (p - t) x g
   float loss;
+  int cand;                        // the candidate claimed by this CTA
   int bad_object;
   const HandDev* hand_loaded;
 };
@@ -357,8 +358,9 @@ __global__ void __launch_bounds__(kGW * 32, 3) gs_kernel(FusedArgs a) {
   const HandDev& H = S.H;
   const ParamsDev& Pm = S.Pm;
 
-  for (int c = blockIdx.x; c < a.B; c += gridDim.x) {
-    __syncthreads();
+  for (;;) {
+    const int c = next_candidate(a.work, &S.cand);
+    if (c >= a.B) break;
     if (tid == 0) {
       S.Pm = a.P;
       const int oi = a.obj_of_cand ? a.obj_of_cand[c] : 0;
@@ -753,6 +755,7 @@ __global__ void __launch_bounds__(kGW * 32, 3) gs_kernel(FusedArgs a) {
       if (tid < D) a.q[(size_t)c * D + tid] = S.q[tid];
     }
   }
+  work_done(a.work);
 }
 
 template <int MODE, bool ANY>
@@ -773,7 +776,10 @@ cudaError_t launch_gs_mode(const FusedArgs& a, int nchunks, cudaStream_t st) {
   long long grid = (long long)device_sm_count() * bps;
   if (grid > a.B) grid = a.B;
   if (grid < 1) return cudaSuccess;
-  gs_kernel<MODE, ANY><<<(int)grid, kGW * 32, dyn, st>>>(a);
+  FusedArgs b = a;
+  e = work_pair(&b.work);
+  if (e != cudaSuccess) return e;
+  gs_kernel<MODE, ANY><<<(int)grid, kGW * 32, dyn, st>>>(b);
   return cudaGetLastError();
 }
 

@@ -74,6 +74,7 @@ struct FusedArgs {
   const QueueSlotDev* slots;   // queue mode: slot table (device), sorted by cand_start
   int nslots;
   int any_mesh;                // some object is a mesh: the kernels with the mesh lookup
+  unsigned* work;              // fused kernels: candidate counter pair (set by the launcher)
 };
 typedef cudaError_t (*FusedLaunchFn)(const FusedArgs&, cudaStream_t);
 // Compiled configurations: grid objects only, and any object (grids and meshes).

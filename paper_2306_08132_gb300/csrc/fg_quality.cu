@@ -12,8 +12,8 @@
 //   max_e u . w_e = -a . n + mu max_e (cos_e a . t1 + sin_e a . t2),
 // and eps_U = min over the directions of the maximum over all contacts.
 //
-// Both kernels: one CTA per candidate (persistent), FK by warp 0, warps over
-// 32-point chunks.  Epsilon collects the contacts of 32 chunks at a time in
+// Both kernels: one CTA per candidate (persistent, candidates claimed from a
+// counter), FK by warp 0, warps over 32-point chunks.  Epsilon collects the contacts of 32 chunks at a time in
 // shared memory (point, normal, tangent basis) and every thread folds them into
 // the running maxima of its directions; max and min do not depend on order, so
 // the result is exact with respect to the order of the contacts.
@@ -43,6 +43,7 @@ struct QualitySmem {
   int total;
   ObjDev O;
   int bad_object;
+  int cand;                                  // the candidate claimed by this CTA
   const HandDev* hand_loaded;
 };
 
@@ -76,7 +77,9 @@ __global__ void __launch_bounds__(kQW * 32) measure_kernel(FusedArgs a, const fl
   __shared__ QualitySmem S;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) S.hand_loaded = nullptr;
-  for (int c = blockIdx.x; c < a.B; c += gridDim.x) {
+  for (;;) {
+    const int c = next_candidate(a.work, &S.cand);
+    if (c >= a.B) break;
     if (!quality_setup(S, a, c, tid, kQW * 32)) {
       if (tid == 0) out[c] = __int_as_float(0x7fc00000);
       continue;
@@ -103,6 +106,7 @@ __global__ void __launch_bounds__(kQW * 32) measure_kernel(FusedArgs a, const fl
       out[c] = t;
     }
   }
+  work_done(a.work);
 }
 
 // Contact record in the batch: point p, outward normal n, tangent basis t1, t2.
@@ -129,7 +133,9 @@ __global__ void __launch_bounds__(kQW * 32) epsilon_kernel(FusedArgs a, float ta
     S.ce[tid] = co;
     S.se[tid] = s;
   }
-  for (int c = blockIdx.x; c < a.B; c += gridDim.x) {
+  for (;;) {
+    const int c = next_candidate(a.work, &S.cand);
+    if (c >= a.B) break;
     if (!quality_setup(S, a, c, tid, NT)) {
       if (tid == 0) {
         eps[c] = __int_as_float(0x7fc00000);
@@ -227,6 +233,7 @@ __global__ void __launch_bounds__(kQW * 32) epsilon_kernel(FusedArgs a, float ta
       if (ncontact) ncontact[c] = S.total;
     }
   }
+  work_done(a.work);
 }
 
 template <class Kern>
@@ -243,8 +250,11 @@ cudaError_t grid_for_kernel(Kern k, size_t dyn, int B, int* grid) {
 
 }  // namespace
 
-cudaError_t launch_contact_measure(const FusedArgs& a, const float* weights, float tau, float* out, cudaStream_t st) {
-  if (a.B <= 0) return cudaSuccess;
+cudaError_t launch_contact_measure(const FusedArgs& a0, const float* weights, float tau, float* out, cudaStream_t st) {
+  if (a0.B <= 0) return cudaSuccess;
+  FusedArgs a = a0;
+  cudaError_t ew = work_pair(&a.work);
+  if (ew != cudaSuccess) return ew;
   int grid = 0;
   if (a.any_mesh) {
     cudaError_t e = grid_for_kernel(measure_kernel<true>, 0, a.B, &grid);
@@ -260,9 +270,12 @@ cudaError_t launch_contact_measure(const FusedArgs& a, const float* weights, flo
 
 size_t epsilon_smem_bytes(int K) { return sizeof(ContactRec) * kQBatch + sizeof(float) * (size_t)K; }
 
-cudaError_t launch_grasp_epsilon(const FusedArgs& a, float tau, float mu, int k_edges, float tscale,
+cudaError_t launch_grasp_epsilon(const FusedArgs& a0, float tau, float mu, int k_edges, float tscale,
                                  const float* dirs, int K, float* eps, int* ncontact, cudaStream_t st) {
-  if (a.B <= 0) return cudaSuccess;
+  if (a0.B <= 0) return cudaSuccess;
+  FusedArgs a = a0;
+  cudaError_t ew = work_pair(&a.work);
+  if (ew != cudaSuccess) return ew;
   const size_t dyn = epsilon_smem_bytes(K);
   static size_t attr_set[2][64] = {{0}, {0}};
   int dev = 0;

@@ -58,6 +58,7 @@ struct TstepSmem {
   float lacc[kTW][kMaxLinks][6];
   unsigned act[kSims][kMaxCullChunks / 32];   // forward: chunks that may touch the object, per simulation
   float loss;
+  int cand;                        // the candidate claimed by this CTA
   int bad_object;
   const HandDev* hand_loaded;
 };
@@ -301,8 +302,9 @@ __global__ void __launch_bounds__(kTW * 32, 4) tstep_kernel(FusedArgs a) {
   const HandDev& H = S.H;
   const ParamsDev& Pm = S.Pm;
 
-  for (int c = blockIdx.x; c < a.B; c += gridDim.x) {
-    __syncthreads();
+  for (;;) {
+    const int c = next_candidate(a.work, &S.cand);
+    if (c >= a.B) break;
     if (tid == 0) {
       S.Pm = a.P;
       const int oi = a.obj_of_cand ? a.obj_of_cand[c] : 0;
@@ -751,6 +753,7 @@ __global__ void __launch_bounds__(kTW * 32, 4) tstep_kernel(FusedArgs a) {
       if (tid < D) a.q[(size_t)c * D + tid] = S.q[tid];
     }
   }
+  work_done(a.work);
 }
 
 template <int MODE, bool ANY>
@@ -767,7 +770,10 @@ cudaError_t launch_tstep_mode(const FusedArgs& a, cudaStream_t st) {
   long long grid = (long long)device_sm_count() * bps;
   if (grid > a.B) grid = a.B;
   if (grid < 1) return cudaSuccess;
-  tstep_kernel<MODE, ANY><<<(int)grid, kTW * 32, 0, st>>>(a);
+  FusedArgs b = a;
+  cudaError_t e = work_pair(&b.work);
+  if (e != cudaSuccess) return e;
+  tstep_kernel<MODE, ANY><<<(int)grid, kTW * 32, 0, st>>>(b);
   return cudaGetLastError();
 }
 
