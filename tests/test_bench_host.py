@@ -1,0 +1,93 @@
+"""Host logic of bench.py's order-quality leg (no GPU): the schedule of launches
+that covers the whole optimisation, the parameters each order and learning rate
+runs with, the per-object torque scale, and the summary statistics, with a fake
+binding standing in for the library."""
+
+import os
+import sys
+import types
+
+import numpy as np
+import torch
+
+import synth
+
+sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+
+
+class _Event:
+    def __init__(self, **_):
+        pass
+
+    def record(self):
+        pass
+
+    def elapsed_time(self, other):
+        return 250.0
+
+
+def _fake_fg(calls, B):
+    fg = types.SimpleNamespace()
+    fg.Hand = types.SimpleNamespace(from_synth=lambda h: types.SimpleNamespace(P=h["P"]))
+
+    def optimize_step(hand, scene, q, prm, k, total, n, obj_of_cand=None, loss=None):
+        calls.append(("opt", prm["gauss_seidel"], prm["lr"], k, total, n))
+        loss.fill_(1.0 + prm["gauss_seidel"])
+
+    def contact_measure(hand, scene, q, weights, tau, obj_of_cand=None):
+        calls.append(("measure", tau, hand.P))
+        return torch.full((q.shape[0],), 2e-4)          # 2 cm^2 (CA) or 200 cm^3 (IV)
+
+    def grasp_epsilon(hand, scene, q, tau, mu, k, ts, dirs, obj_of_cand=None):
+        calls.append(("eps", q.shape[0], ts, int(obj_of_cand[0])))
+        n = q.shape[0]
+        # the first half of each object's candidates in force closure
+        e = torch.where(torch.arange(n) < n // 2, torch.tensor(0.1), torch.tensor(-0.2))
+        return e, torch.full((n,), 7, dtype=torch.int32)
+
+    fg.optimize_step = optimize_step
+    fg.contact_measure = contact_measure
+    fg.grasp_epsilon = grasp_epsilon
+    return fg
+
+
+def test_order_quality_schedule_and_summary(monkeypatch):
+    import bench
+    monkeypatch.setattr(torch.cuda, "Event", _Event)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a: None)
+    w = synth.batched_superquadric_workload(n_obj=2, per_obj=6, grid_n=12)
+    calls = []
+    fg = _fake_fg(calls, w.B)
+    hand = types.SimpleNamespace(P=w.hand["P"])
+    out = bench.run_order_quality(fg, w, hand, None, torch.tensor(w.obj_of_cand), torch.tensor(w.q0), "cpu",
+                                  [1e-3, 1e-6], steps_per_launch=30)
+    opt = [c for c in calls if c[0] == "opt"]
+    # 2 rates x 2 orders, each covering steps 0..w.steps-1 in launches of <= 30 steps
+    assert len(opt) == 4 * -(-w.steps // 30)
+    for lr in (1e-3, 1e-6):
+        for gs in (0, 1):
+            run = [c for c in opt if c[1] == gs and c[2] == lr]
+            assert [c[3] for c in run] == list(range(0, w.steps, 30))
+            assert sum(c[5] for c in run) == w.steps
+            assert all(c[4] == w.steps for c in run)
+    # one epsilon call per object, torque scaled by 1/rho of that object
+    eps = [c for c in calls if c[0] == "eps"]
+    assert len(eps) == 4 * len(w.objects)
+    for c in eps[:len(w.objects)]:
+        assert np.isclose(c[2], 1.0 / w.objects[c[3]]["bound_radius"])
+    # contact area on the surface samples at 5 mm, intersection volume on the interior lattice at 0
+    meas = [c for c in calls if c[0] == "measure"]
+    assert meas[0][1] == 0.005 and meas[1][1] == 0.0 and meas[0][2] == w.hand["P"] and meas[1][2] != w.hand["P"]
+    runs = [r for r in out["runs"] if "order" in r]
+    assert [(r["lr"], r["order"]) for r in runs] == [(1e-3, "jacobi"), (1e-3, "gauss_seidel"),
+                                                     (1e-6, "jacobi"), (1e-6, "gauss_seidel")]
+    for r in runs:
+        assert r["force_closure_frac"] == 0.5
+        assert np.isclose(r["epsilon_median_of_force_closure"], 0.1)
+        assert np.isclose(r["contact_area_cm2_mean"], 2.0)
+        assert np.isclose(r["intersection_volume_cm3_mean"], 200.0)
+        assert r["with_contact_frac"] == 1.0 and r["contacts_mean"] == 7.0
+        assert r["optimise_s"] == 0.25
+        assert r["loss_median"] == (1.0 if r["order"] == "jacobi" else 2.0)
+    cmp_ = [r for r in out["runs"] if "gs_epsilon_above_jacobi_frac" in r]
+    assert [r["gs_epsilon_above_jacobi_frac"] for r in cmp_] == [0.0, 0.0]
