@@ -227,7 +227,7 @@ def run_serving(fg, n_requests: int, rates_hz, device, budget_bytes: int, steps_
 
 
 def run_order_quality(fg, w, hand, scene, oc, q0, device, lrs, steps_per_launch: int = 10):
-    """Jacobi against Gauss-Seidel projection, judged by the grasps they produce: the
+    """Jacobi against Gauss-Seidel projection, compared by the grasps they produce: the
     same initial candidates optimised over the workload's whole schedule (w.steps
     steps, dilation from r0 down to 0) in each order and at each learning rate of lrs
     (the paper's 1e-3 moves a candidate by decimetres per step in SI units, so smaller
