@@ -286,6 +286,28 @@ def _fd_jacobian(C, h=1e-7):
     return np.array([(C(np.eye(6)[k] * h) - C(-np.eye(6)[k] * h)) / (2 * h) for k in range(6)])
 
 
+@pytest.mark.parametrize("seed", range(4))
+def test_single_contact_on_a_sphere(seed):
+    """One hand point at depth delta inside a sphere centred at the object's origin, in
+    the zero-velocity simulation (Eq. 1 and Sec. IV-A): the lever d = p is parallel to
+    the outward normal u, so the projection is a pure push along -u of size delta m
+    (lambda_n = C / w_n with w_n = 1/m, since d x n = 0), no torque, and no friction
+    (the test velocity is 0, so sigma = 0).  The sphere is sampled on a 2 mm grid: the
+    value errs by at most (3/8) h^2 / R (2.5% of delta here) and the normal's direction
+    by O(h / R) = 0.05, which set the tolerances."""
+    R, h, delta = 0.04, 0.002, 0.0015
+    ob = obj_from(synth.sphere_grid(R, 64, h), 1.0)
+    u = np.random.default_rng(seed).normal(size=3)
+    u /= np.linalg.norm(u)
+    p = (R - delta) * u
+    out = O.evaluate(multi_point_hand([p]), ob, torch.zeros(1, 6, dtype=F64), 0.0, O.Params(mu=0.5))
+    W = out["W"][0, 0].numpy()
+    assert int(out["N"][0, 0]) == 1
+    assert np.linalg.norm(W[:3] + u * delta) <= (0.025 + 0.05) * delta
+    assert np.linalg.norm(W[3:]) <= 0.05 * np.linalg.norm(p) * delta
+    assert float(out["sigma"][0, 0, 0]) == 0.0
+
+
 @pytest.mark.parametrize("m", range(7))
 @pytest.mark.parametrize("inv_mass,inv_inertia", [(1.0, 0.0), (0.0, 30.0), (1.0, 25.0)])
 def test_single_contact_projection_satisfies_eq1(plane, inv_mass, inv_inertia, m):
