@@ -115,6 +115,32 @@ def hull_mesh(points: np.ndarray):
     return _pack("hull", V, _orient_outward(V, F), {"n_points": int(len(P))})
 
 
+
+def torus_mesh(R: float, r: float, n_major: int, n_minor: int):
+    """Torus about the z axis (tube centre radius R, tube radius r): a non-convex,
+    genus-1 watertight mesh of 2 n_major n_minor triangles, each oriented by the
+    torus's analytic outward normal at its centroid (the star-shaped orientation
+    rule does not hold here)."""
+    th = 2.0 * np.pi * np.arange(n_major) / n_major
+    ph = 2.0 * np.pi * np.arange(n_minor) / n_minor
+    T, P = np.meshgrid(th, ph, indexing="ij")
+    V = np.stack([(R + r * np.cos(P)) * np.cos(T), (R + r * np.cos(P)) * np.sin(T), r * np.sin(P)], -1).reshape(-1, 3)
+    idx = lambda i, j: (i % n_major) * n_minor + (j % n_minor)
+    F = []
+    for i in range(n_major):
+        for j in range(n_minor):
+            a, b, c, d = idx(i, j), idx(i + 1, j), idx(i + 1, j + 1), idx(i, j + 1)
+            F += [(a, b, c), (a, c, d)]
+    F = np.array(F)
+    A, B, C = V[F[:, 0]], V[F[:, 1]], V[F[:, 2]]
+    n = np.cross(B - A, C - A)
+    g = (A + B + C) / 3.0
+    ring = g[:, :2] * (R / np.linalg.norm(g[:, :2], axis=1))[:, None]     # nearest point of the tube's centre circle
+    out = g - np.concatenate([ring, np.zeros((len(g), 1))], axis=1)
+    flip = (n * out).sum(-1) < 0
+    F[flip] = F[flip][:, [0, 2, 1]]
+    return _pack("torus", V, F, {"R": R, "r": r, "n_major": n_major, "n_minor": n_minor})
+
 def random_superquadric_mesh(rng: np.random.Generator, n_lat: int = 24, n_lon: int = 48):
     """Superquadric mesh with exponents U(0.5, 1.5) (the grid objects use U(0.3, 2);
     sharper exponents fold the pole triangles of a latitude/longitude mesh) and

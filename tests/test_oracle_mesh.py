@@ -155,3 +155,54 @@ def test_mesh_object_in_the_grasp_metric():
     ref = O.evaluate(grid.hand, grid.objs[0], torch.tensor(q), 0.004, grid.prm)
     free = (ref["N"].sum(1) == 0).numpy()
     assert np.allclose(out["L"].detach().numpy()[free], ref["L"].numpy()[free], rtol=1e-3)
+
+
+def _winding_number(V, F, p):
+    """Generalised winding number of a closed triangle mesh at points p: the solid
+    angles of its faces seen from p (Van Oosterom and Strackee, 1983) summed over the
+    faces and divided by 4 pi; 1 inside a watertight outward-oriented mesh, 0 outside."""
+    w = np.zeros(len(p))
+    for f in F:
+        a, b, c = V[f[0]] - p, V[f[1]] - p, V[f[2]] - p
+        la, lb, lc = (np.linalg.norm(x, axis=1) for x in (a, b, c))
+        num = (a * np.cross(b, c)).sum(-1)
+        den = la * lb * lc + (a * b).sum(-1) * lc + (b * c).sum(-1) * la + (c * a).sum(-1) * lb
+        w += 2.0 * np.arctan2(num, den)
+    return w / (4.0 * np.pi)
+
+
+@pytest.mark.parametrize("n_major,n_minor", [(24, 12), (8, 4), (6, 3)])
+def test_sign_on_a_non_convex_mesh_matches_the_winding_number(n_major, n_minor):
+    """The pseudonormal sign (the closest face, edge or vertex decides) on tori, whose
+    inner half is saddle-shaped, against an independent inside test: the generalised
+    winding number.  Points fill the bounding box (the hole included), lie within
+    0.2-3 mm of the smooth torus on both sides, and cluster around the vertices and
+    edges of the mesh.  The coarse tori (tubes of 3 or 4 faces, 60-90 degree bends
+    along the ring) have sharp convex and concave features, where a sign taken from
+    the closest face's normal alone, or from its vertices' normals, is wrong."""
+    R, r = 0.04, 0.015
+    m = SM.torus_mesh(R, r, n_major, n_minor)
+    mesh = MS.MeshObj.from_synth(m, alpha=0.0)
+    V = m["vertices"].astype(np.float64)
+    F = mesh.F
+    rng = np.random.default_rng(6)
+    box = rng.uniform(-1.0, 1.0, size=(1500, 3)) * np.array([R + 1.5 * r, R + 1.5 * r, 1.5 * r])
+    th, ph = rng.uniform(0, 2 * np.pi, size=(2, 1500))
+    n = np.stack([np.cos(ph) * np.cos(th), np.cos(ph) * np.sin(th), np.sin(ph)], -1)
+    s = np.stack([(R + r * np.cos(ph)) * np.cos(th), (R + r * np.cos(ph)) * np.sin(th), r * np.sin(ph)], -1)
+    near = s + n * (rng.choice([-1.0, 1.0], size=1500) * rng.uniform(0.0002, 0.003, size=1500))[:, None]
+    at_vertices = V[rng.integers(0, len(V), 1500)] + rng.normal(size=(1500, 3)) * 0.003
+    e = rng.integers(0, len(F), 1500)
+    t = rng.uniform(size=(1500, 1))
+    at_edges = V[F[e, 0]] * t + V[F[e, 1]] * (1 - t) + rng.normal(size=(1500, 3)) * 0.003
+    p = np.concatenate([box, near, at_vertices, at_edges])
+    res = MS.mesh_query(mesh, p)
+    w = _winding_number(V, F, p)
+    assert np.abs(w - np.round(w)).max() < 1e-9            # closed and consistently oriented
+    keep = res["dist"] > 1e-7
+    inside = np.round(w[keep]) == 1
+    assert inside.sum() > 500 and (~inside).sum() > 500
+    assert np.array_equal(res["sign"][keep] < 0, inside)
+    # the hole: points on the axis are outside
+    axis = np.stack([np.zeros(20), np.zeros(20), np.linspace(-r, r, 20)], -1)
+    assert (MS.mesh_query(mesh, axis)["sign"] > 0).all()
