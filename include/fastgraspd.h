@@ -34,6 +34,8 @@
  *    concurrent streams (fewer than 1,024 launches of one kind in flight at once).
  *    A call captured in a CUDA graph keeps the counter it drew at capture, so one
  *    graph must not be replayed on two streams at once (capture one per stream).
+ *    Run each kind of call once before capturing it: its first launch on a device
+ *    sets kernel attributes and looks up the counter pool.
  *  - Configuration vector layout, per candidate (row-major [B][D]):
  *      q = (t_x, t_y, t_z, w_x, w_y, w_z, theta_0 .. theta_{J-1}),  D = 6 + J,
  *    t the palm origin (metres), w the palm rotation vector (R_b = Exp(w)),
