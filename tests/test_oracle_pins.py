@@ -580,3 +580,42 @@ def test_dilation_schedule_linear_to_zero():
     assert r[0] == 0.01 and r[-1] == 0.0
     assert np.allclose(np.diff(r), -0.001, atol=1e-15)
     assert O.dilation_radius(O.Params(r0=0.004), 50, 100) == 0.004
+
+
+# ----------------------------------------------------------------------------- guard band
+
+def test_guard_band_excludes_near_ties():
+    """clean_candidates keeps a candidate only if every decision sits outside its guard
+    band.  On the tilted plane phi = c . x (|c| = 1, no test velocity parallel to c)
+    with r = 0, the +z simulation's constraint is phi_m = phi - dt V c_z: a point
+    0.5 micrometres from that threshold is excluded on either side, one 0.3 mm away is
+    kept; a point on a grid node plane (a tie in the cell choice) is excluded; in the
+    +x simulation the friction regime flips at sigma = mu C with sigma = dt V
+    sqrt(1 - c_x^2) and C = dt V c_x - phi, and a contact 0.5 micrometres from that
+    boundary is excluded.  On an axis-aligned plane every candidate is excluded: the
+    normal is parallel to two test velocities, where the friction direction is 0/0."""
+    c = np.array([0.3, 0.2, 1.0])
+    c /= np.linalg.norm(c)
+    ob = obj_from(synth.linear_grid(tuple(c), 0.0, 32, 0.005), 1.0, 0.0)
+    prm = O.Params(mu=0.5)
+    dtv = prm.dt * prm.v_test
+    h = ob.pitch
+    org = ob.origin.numpy()
+    x, y = org[0] + 7.31 * h, org[1] + 9.47 * h          # off the node planes
+    q = np.zeros((1, 6))
+
+    def at(phi, px=x):
+        return [px, y, (phi - c[0] * px - c[1] * y) / c[2]]
+
+    def clean(pt, o=ob):
+        return bool(O.clean_candidates(multi_point_hand([pt]), o, q, 0.0, prm)[0])
+
+    assert clean(at(dtv * c[2] + 3e-4))
+    assert not clean(at(dtv * c[2] + 5e-7))
+    assert not clean(at(dtv * c[2] - 5e-7))
+    assert not clean(at(dtv * c[2] + 3e-4, px=org[0] + 7.0 * h))
+    boundary = dtv * c[0] - dtv * np.sqrt(1.0 - c[0] ** 2) / prm.mu
+    assert clean(at(boundary + 2e-4))
+    assert not clean(at(boundary + 5e-7))
+    flat = obj_from(synth.linear_grid((0.0, 0.0, 1.0), 0.0, 32, 0.005), 1.0, 0.0)
+    assert not clean([x, y, 0.004], flat)
