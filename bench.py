@@ -48,6 +48,8 @@ FLOPS_PER_POINT_STEP = 2092
 KERNEL_MIN_FLOPS_PER_POINT_STEP = 599
 # The same count for the Gauss-Seidel form (oracle counting instantiation, this workload).
 GS_FLOPS_PER_POINT_STEP = 2540
+# The T-step form, by the number of simulation steps T (same counter, same workload).
+TSTEP_FLOPS_PER_POINT_STEP = {1: 6228, 2: 13061, 4: 26729}
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 METRIC = "candidate-steps/sec fused fwd+bwd vs plain GPU form at 1e-3 grad tol; p50/p99 latency"
@@ -550,8 +552,12 @@ def main():
 
             tms = timed(graphed(tstep_step), max(3, args.steps // 4), 3)
             t_ms = max_over_ranks(float(np.mean(tms)), world, dev)
-            tstep.append({"T": T, "ms_per_step": t_ms, "value": cand_steps / (t_ms / 1000.0),
-                          "unit": "candidate-steps/s", "sdf_queries_per_point_step": 2 * 7 * T})
+            rec = {"T": T, "ms_per_step": t_ms, "value": cand_steps / (t_ms / 1000.0),
+                   "unit": "candidate-steps/s", "sdf_queries_per_point_step": 2 * 7 * T}
+            if T in TSTEP_FLOPS_PER_POINT_STEP:
+                rec["flops_per_point_step"] = TSTEP_FLOPS_PER_POINT_STEP[T]
+                rec["achieved_tflops"] = TSTEP_FLOPS_PER_POINT_STEP[T] * w.B * w.hand["P"] * S_in / (t_ms / 1e3) / 1e12
+            tstep.append(rec)
 
     gs = None
     if args.gs:

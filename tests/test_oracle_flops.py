@@ -54,14 +54,16 @@ def test_oracle_count_scales_with_work():
 
 def test_benchmark_constants_are_the_oracle_counts():
     """bench.py's algorithmic work per point-step (the roofline's numerator) is the
-    counter's figure for the benchmark hand (4-finger, 4,352 points), Jacobi and
-    Gauss-Seidel forms; the per-point figure does not depend on the grid size."""
+    counter's figure for the benchmark hand (4-finger, 4,352 points): the Jacobi,
+    Gauss-Seidel and T-step forms; the per-point figure does not depend on the grid size."""
     import os
     import sys
     sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
     import bench
     w = synth.batched_superquadric_workload(n_obj=1, per_obj=8, grid_n=32, device="cpu")
-    for gs, const in ((0, bench.FLOPS_PER_POINT_STEP), (1, bench.GS_FLOPS_PER_POINT_STEP)):
-        S = O.Setup(w.hand, w.objects, dict(w.params, gauss_seidel=gs))
+    forms = [({}, bench.FLOPS_PER_POINT_STEP), ({"gauss_seidel": 1}, bench.GS_FLOPS_PER_POINT_STEP)]
+    forms += [({"sim_steps": T}, n) for T, n in bench.TSTEP_FLOPS_PER_POINT_STEP.items()]
+    for extra, const in forms:
+        S = O.Setup(w.hand, w.objects, dict(w.params, **extra))
         c = count_step(S, w.q0[:2], 0, O.dilation_radius(S.prm, 0, w.steps))
-        assert round(c["flops_per_point_step"]) == const, (gs, c["flops_per_point_step"])
+        assert round(c["flops_per_point_step"]) == const, (extra, c["flops_per_point_step"])
