@@ -120,3 +120,25 @@ def test_invalid_meshes_are_rejected_on_the_host(lib):
     Vd = V.copy(); Vd[1] = Vd[0] + 1e-12
     assert create(Vd, F) == 1 and (b"zero-area" in _last(lib) or b"directed" in _last(lib))
     assert create(V, F, alpha=1.5) == 1 and b"phong_alpha" in _last(lib)
+
+
+def test_valid_meshes_pass_host_validation(lib):
+    """Convex and non-convex watertight meshes (box, icosphere, superquadric, hull, and
+    tori whose tubes have 3 to 12 faces) pass fg_sdf_create_mesh's host validation and
+    BVH build; without a GPU the call then stops at the device copy."""
+    import numpy as np
+    from synth import meshes as SM
+    rng = np.random.default_rng(7)
+    meshes = [SM.box_mesh((0.03, 0.02, 0.05)), SM.icosphere(0.04, 2),
+              SM.superquadric_mesh((0.05, 0.03, 0.04), 0.7, 1.3, 12, 24), SM.hull_mesh(rng.normal(size=(30, 3)) * 0.04),
+              SM.torus_mesh(0.04, 0.015, 24, 12), SM.torus_mesh(0.04, 0.015, 6, 3)]
+    for m in meshes:
+        V = np.ascontiguousarray(m["vertices"], dtype=np.float32)
+        F = np.ascontiguousarray(m["faces"], dtype=np.int32)
+        out = C.c_void_p()
+        st = lib.fg_sdf_create_mesh(V.ctypes.data_as(C.POINTER(C.c_float)), len(V),
+                                    F.ctypes.data_as(C.POINTER(C.c_int)), len(F), 0.75, 1.0, 1.0, C.byref(out))
+        if st == 0:
+            assert lib.fg_sdf_destroy(out) == 0
+        else:
+            assert st == 5 and b"device copy" in _last(lib), (m["kind"], st, _last(lib))
