@@ -91,3 +91,28 @@ def test_order_quality_schedule_and_summary(monkeypatch):
         assert r["loss_median"] == (1.0 if r["order"] == "jacobi" else 2.0)
     cmp_ = [r for r in out["runs"] if "gs_epsilon_above_jacobi_frac" in r]
     assert [r["gs_epsilon_above_jacobi_frac"] for r in cmp_] == [0.0, 0.0]
+
+
+def test_reference_arm_line():
+    """bench.py --impl reference times the FP64 oracle on the host and prints the
+    contract's JSON line (same metric and unit as the GPU arm, the oracle as its
+    cpu_baseline, no host-device bytes); ranks other than 0 print nothing."""
+    import json
+    import subprocess
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cmd = [sys.executable, os.path.join(root, "bench.py"), "--impl", "reference", "--steps", "1", "--warmup", "0"]
+    env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK")}
+    out = subprocess.run(cmd, capture_output=True, text=True, timeout=600, env=env, cwd=root)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    import bench
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "candidate-steps/s"
+    assert d["value"] > 0 and d["higher_is_better"] is True and d["steps"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    out1 = subprocess.run(cmd, capture_output=True, text=True, timeout=120, cwd=root,
+                          env=dict(env, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1"))
+    assert out1.returncode == 0 and out1.stdout.strip() == ""
