@@ -241,6 +241,26 @@ def sdf_query(obj: Obj, p: torch.Tensor, r: float):
 
 # ----------------------------------------------------------------------------- step
 
+def _forced(taken: torch.Tensor, force: dict | None, key: str, i: int | None = None) -> torch.Tensor:
+    """A decision taken from the values, except where ``force[key] = (mask, value)``
+    sets it ([B,P,M] tables; ``i`` selects point i of them)."""
+    if force is None or key not in force:
+        return taken
+    mask, value = force[key]
+    if i is not None:
+        mask, value = mask[:, i], value[:, i]
+    return torch.where(mask, value, taken)
+
+
+def _forced_cells(sdf_dec: dict, force: dict | None) -> dict:
+    """Grid lookup decisions, except at the points where ``force["sdf"] = (mask [B,P],
+    decisions)`` gives them."""
+    if force is None or "sdf" not in force:
+        return sdf_dec
+    mask, alt = force["sdf"]
+    return {k: torch.where(mask[..., None], alt[k], v) for k, v in sdf_dec.items()}
+
+
 @dataclass
 class Decisions:
     sdf: dict = None
@@ -266,13 +286,15 @@ def _dot(a, b):
 
 
 def evaluate(hand: Hand, obj: Obj, q: torch.Tensor, r: float, prm: Params,
-             dec: Decisions | None = None, anchor_mode: bool = False) -> dict:
+             dec: Decisions | None = None, anchor_mode: bool = False, force: dict | None = None) -> dict:
     """One grasp-metric evaluation for a batch of candidates on one object.
 
     With ``dec=None`` every decision is taken from the current values (the method).
     With a frozen ``dec`` the same arithmetic is evaluated on that branch; with
     ``anchor_mode`` non-contact constraints use C = -alpha (phi_m - anchor), whose
     value is 0 at the anchor state and whose slope is the leaky -alpha.
+    ``force`` (with ``dec=None``) sets some decisions while the others are taken
+    from the values (see ``_forced``).
     Returns a dict of per-candidate tensors and the decisions used."""
     take = dec is None
     if take:
@@ -281,7 +303,7 @@ def evaluate(hand: Hand, obj: Obj, q: torch.Tensor, r: float, prm: Params,
     R, o = forward_kinematics(hand, q)
     p = hand_points(hand, R, o)                                      # [B,P,3]
     if take:
-        dec.sdf = sdf_decisions(obj, p)
+        dec.sdf = _forced_cells(sdf_decisions(obj, p), force)
     phi, grad = sdf_eval(obj, p, dec.sdf)
     phi_hat = phi - r
     if take:
@@ -297,7 +319,7 @@ def evaluate(hand: Hand, obj: Obj, q: torch.Tensor, r: float, prm: Params,
     # constraint on the plane through the query: phi(p - x_pred) ~ phi_hat - n . x_pred
     phi_m = phi_hat[..., None] - _dot(n_, x_pred)                     # [B,P,M]
     if take:
-        dec.kappa = phi_m.detach() < 0
+        dec.kappa = _forced(phi_m.detach() < 0, force, "kappa")
     if anchor_mode:
         anchor = dec.anchor
     else:
@@ -319,7 +341,7 @@ def evaluate(hand: Hand, obj: Obj, q: torch.Tensor, r: float, prm: Params,
     u_t = _cross(d, t_hat)
     w_t = obj.inv_mass + obj.inv_inertia * _dot(u_t, u_t)
     if take:
-        dec.static = sig.detach() <= prm.mu * C.detach()
+        dec.static = _forced(sig.detach() <= prm.mu * C.detach(), force, "static")
     lam_t = torch.where(dec.has_t, torch.where(dec.static, sig, prm.mu * C) / w_t, torch.zeros_like(sig))
     f = -(lam_n[..., None] * n_ + lam_t[..., None] * t_hat)          # [B,P,M,3]
     W_lin = f.sum(1)                                                  # [B,M,3]
@@ -513,7 +535,7 @@ class GSDecisions:
 
 
 def evaluate_gs(hand: Hand, obj: Obj, q: torch.Tensor, r: float, prm: Params,
-                dec: GSDecisions | None = None, anchor_mode: bool = False) -> dict:
+                dec: GSDecisions | None = None, anchor_mode: bool = False, force: dict | None = None) -> dict:
     """The one-step grasp metric with the constraints projected by a Gauss-Seidel
     sweep (Sec. III-C: the update of Eq. (1) for each constraint, applied in turn).
 
@@ -536,7 +558,9 @@ def evaluate_gs(hand: Hand, obj: Obj, q: torch.Tensor, r: float, prm: Params,
     non-contact constraint neither moves the state nor passes gradient between
     states (its exact derivative with respect to the state is 0).  With a frozen
     ``dec`` and ``anchor_mode`` that state is the one recorded at the decision point,
-    which makes the leaky gradient the exact gradient of the frozen surrogate."""
+    which makes the leaky gradient the exact gradient of the frozen surrogate.
+    ``force`` (with ``dec=None``) sets some decisions while the others, later ones
+    of the sweep included, are taken from the values (see ``_forced``)."""
     take = dec is None
     if take:
         dec = GSDecisions()
@@ -545,7 +569,7 @@ def evaluate_gs(hand: Hand, obj: Obj, q: torch.Tensor, r: float, prm: Params,
     R, o = forward_kinematics(hand, q)
     p = hand_points(hand, R, o)                                      # [B,P,3]
     if take:
-        dec.sdf = sdf_decisions(obj, p)
+        dec.sdf = _forced_cells(sdf_decisions(obj, p), force)
     phi, grad = sdf_eval(obj, p, dec.sdf)
     phi_hat = phi - r
     if take:
@@ -575,7 +599,7 @@ def evaluate_gs(hand: Hand, obj: Obj, q: torch.Tensor, r: float, prm: Params,
         phi_m = ph_i[i][:, None] - _dot(n_, Dsp)                      # [B,M]
         if take:
             dec.state[:, i] = torch.cat([dx, dth], -1).detach()
-            dec.kappa[:, i] = phi_m.detach() < 0
+            dec.kappa[:, i] = _forced(phi_m.detach() < 0, force, "kappa", i)
         if anchor_mode:
             st = dec.state[:, i].clone()
             dx_c, dth_c = st[..., :3], st[..., 3:]
@@ -599,7 +623,7 @@ def evaluate_gs(hand: Hand, obj: Obj, q: torch.Tensor, r: float, prm: Params,
         u_t = _cross(d, t_hat)
         w_t = obj.inv_mass + obj.inv_inertia * _dot(u_t, u_t)
         if take:
-            dec.static[:, i] = sig.detach() <= prm.mu * C.detach()
+            dec.static[:, i] = _forced(sig.detach() <= prm.mu * C.detach(), force, "static", i)
         stat = dec.static[:, i].clone()
         lam_t = torch.where(ht, torch.where(stat, sig, prm.mu * C) / w_t, torch.zeros_like(sig))
         f = -(lam_n[..., None] * n_ + lam_t[..., None] * t_hat)       # [B,M,3]
@@ -627,14 +651,14 @@ def evaluate_gs(hand: Hand, obj: Obj, q: torch.Tensor, r: float, prm: Params,
 
 
 def evaluate_any(hand: Hand, obj: Obj, q: torch.Tensor, r: float, prm: Params, dec=None,
-                 anchor_mode: bool = False) -> dict:
+                 anchor_mode: bool = False, force: dict | None = None) -> dict:
     """evaluate (sim_steps = 0), evaluate_gs (sim_steps = 0, gauss_seidel = 1) or
     evaluate_tstep (sim_steps = T >= 1)."""
     if prm.sim_steps >= 1:
         return evaluate_tstep(hand, obj, q, r, prm, prm.sim_steps, dec=dec, anchor_mode=anchor_mode)
     if prm.gauss_seidel:
-        return evaluate_gs(hand, obj, q, r, prm, dec=dec, anchor_mode=anchor_mode)
-    return evaluate(hand, obj, q, r, prm, dec=dec, anchor_mode=anchor_mode)
+        return evaluate_gs(hand, obj, q, r, prm, dec=dec, anchor_mode=anchor_mode, force=force)
+    return evaluate(hand, obj, q, r, prm, dec=dec, anchor_mode=anchor_mode, force=force)
 
 
 def loss_and_grad(hand: Hand, obj: Obj, q32, r: float, prm: Params, alpha=None):
@@ -789,3 +813,194 @@ def clean_candidates(hand: Hand, obj: Obj, q32, r: float, prm: Params, face_tol:
         m = guard_margins(hand, obj, q32, r, prm)
     return ((m["face"] > face_tol) & (m["phi"] > phi_tol) & (m["friction"] > fr_tol)
             & (m["parallel"] > par_tol))
+
+
+# ----------------------------------------------------------------------------- guard band per decision
+
+def _alternative_cells(obj: Obj, sdf_dec: dict, pts: torch.Tensor, face_tol: float):
+    """The other side of every cell choice within face_tol voxel of its threshold.
+
+    Per point and axis: inside the grid near an interior node plane k the cell is
+    k - 1 or k, so the other one is 2k - 1 - i0; near the clamp planes u = 0 and
+    u = n - 1 the clamp decision flips (the cell stays 0 or n - 2).  Returns the
+    decisions with every such choice flipped and the per-point, per-axis mask of
+    flipped choices [..., 3].  Mesh objects have no alternative (None)."""
+    if isinstance(obj, _mesh.MeshObj):
+        return None, None
+    n = torch.tensor(obj.dims, dtype=F64)
+    u = (pts - obj.origin) / obj.pitch
+    k = torch.round(u)
+    near = (u - k).abs() <= face_tol
+    near_lo = near & (k == 0)
+    near_hi = near & (k == n - 1)
+    near_node = near & (k >= 1) & (k <= n - 2) & ~sdf_dec["lo"] & ~sdf_dec["hi"]
+    alt = {"lo": torch.where(near_lo, ~sdf_dec["lo"], sdf_dec["lo"]),
+           "hi": torch.where(near_hi, ~sdf_dec["hi"], sdf_dec["hi"]),
+           "i0": torch.where(near_node, 2 * k.long() - 1 - sdf_dec["i0"], sdf_dec["i0"])}
+    return alt, near_lo | near_hi | near_node
+
+
+def _one_candidate(dec, b: int):
+    """Decisions of candidate b alone (every tensor field sliced to [b:b+1])."""
+    out = type(dec)()
+    for name in dec.__dataclass_fields__:
+        v = getattr(dec, name)
+        if isinstance(v, dict):
+            v = {k: t[b:b + 1].clone() for k, t in v.items()}
+        elif isinstance(v, torch.Tensor):
+            v = v[b:b + 1].clone()
+        setattr(out, name, v)
+    return out
+
+
+def _stack_decisions(decs: list):
+    """One decision set holding the candidates of several (concatenated along the batch)."""
+    out = type(decs[0])()
+    for name in out.__dataclass_fields__:
+        v = getattr(decs[0], name)
+        if isinstance(v, dict):
+            v = {k: torch.cat([d_.__dict__[name][k] for d_ in decs]) for k in v}
+        elif isinstance(v, torch.Tensor):
+            v = torch.cat([getattr(d_, name) for d_ in decs])
+        setattr(out, name, v)
+    return out
+
+
+def decision_band(hand: Hand, obj: Obj, q32, r: float, prm: Params, face_tol: float = 1e-5,
+                  phi_tol: float = 1e-6, fr_tol: float = 1e-6, par_tol: float = 1e-3,
+                  max_alternatives: int = 8, chunk: int = 64) -> dict:
+    """Which decisions float32 may take differently from this float64 evaluation, pair
+    by pair, and the oracle's result on every branch they allow.
+
+    The decisions are those of ``clean_candidates`` (the cell choice and clamp within
+    face_tol voxel of a node or clamp plane, the contact flag within phi_tol metres of
+    phi_m = 0, the friction regime within fr_tol of sigma = mu C, the friction
+    direction of a contact with sigma / (dt V) < par_tol), located per (point,
+    simulation) instead of per candidate, and the last only for kinetic contacts (a
+    static contact's friction force is -s / w_t, smooth in s).  For the Jacobi form (Sec. III-C, read as
+    averaged corrections) and the Gauss-Seidel form (point order):
+
+    ``flag`` [B,P,M]: contact flags that are not fixed: |phi_m| <= phi_tol, or on the
+        other side of an ambiguous cell choice phi_m changes sign or comes within
+        phi_tol of 0.  phi_m of the Gauss-Seidel form is taken at the state the sweep
+        reaches the point with.
+    ``masked`` [B,P,M]: the flags a comparison leaves out.  Jacobi: ``flag`` (each
+        flag depends on its own point only).  Gauss-Seidel: in each simulation every
+        pair from the first ambiguous decision of the chain on (an ambiguous flag, the
+        regime or direction of a contact's friction, or an ambiguous cell of a point
+        in contact on either side), since the state that later points see depends on it.
+    ``branches``: per candidate, the loss "L" [K], gradient "grad" [K,D] and wrench
+        "W" [K,M,6] on each of the K branches its ambiguous decisions allow (index 0:
+        the method's own decisions; then every combination of the alternatives).  An
+        alternative sets one decision to its other side: a cell choice, a contact
+        flag within phi_tol of its threshold, or a friction regime; every other
+        decision is taken from the values as the method takes it (the flags and
+        counts of a point looked up in its other cell, and in the Gauss-Seidel form
+        the rest of the sweep from the changed state on).  Where several branches
+        are correct a float32 result must match one of them.
+    ``comparable`` [B]: candidates whose branches are all enumerated: at most
+        max_alternatives ambiguous decisions, no contact with an ill-conditioned
+        friction direction (a conditioning question, not a branch), and for mesh
+        objects no decision in the face band (no alternative is enumerated for them).
+    ``ref``: the float64 forward outputs at the method's own decisions."""
+    if prm.sim_steps >= 1:
+        raise ValueError("decision_band covers the one-step forms (Jacobi, Gauss-Seidel)")
+    gs = bool(prm.gauss_seidel)
+    ref = loss_and_grad(hand, obj, q32, r, prm)
+    dec = ref["dec"]
+    with torch.no_grad():
+        p = ref["points"].detach()
+        phi_m = ref["phi_m"].detach()
+        kap = ref["kappa"]
+        B, P = p.shape[0], p.shape[1]
+        alt, near = _alternative_cells(obj, dec.sdf, p, face_tol)
+        if near is None:
+            face_band = (_face_margin(obj, p)[..., 0] <= face_tol)
+            has_alt = torch.zeros(B, P, dtype=torch.bool)
+        else:
+            has_alt = near.any(-1)
+            face_band = torch.zeros(B, P, dtype=torch.bool)
+        tie = phi_m.abs() <= phi_tol
+        flag = tie.clone()
+        flip_contact = torch.zeros_like(flag)
+        phi_ma = None
+        if has_alt.any():
+            phi_a, g_a = sdf_eval(obj, p, alt)
+            gn = _safe_norm(g_a, (g_a * g_a).sum(-1) > 0)
+            n_a = g_a / torch.where(gn > 0, gn, torch.ones_like(gn))[..., None]
+            V = torch.tensor(TEST_DIRECTIONS, dtype=F64) * prm.v_test
+            x_pred = prm.dt * V                                       # [M,3]
+            if gs:
+                st = dec.state                                        # [B,P,M,6]
+                d = p[:, :, None, :] - x_pred[None, None]
+                D = x_pred[None, None] + st[..., :3] + _cross(st[..., 3:], d)
+            else:
+                D = x_pred[None, None].expand(B, P, M_SIMS, 3)
+            phi_ma = (phi_a - r)[..., None] - _dot(n_a[:, :, None, :], D)
+            alt_pair = has_alt[..., None].expand_as(flag)
+            flag = flag | (alt_pair & (((phi_ma < 0) != kap) | (phi_ma.abs() <= phi_tol)))
+            flip_contact = alt_pair & (kap | (phi_ma < 0))
+        flag = flag | (face_band[..., None] & (phi_m.abs() <= 2.0 * prm.dt * prm.v_test + phi_tol))
+        sig = ref["sigma"].detach()
+        C = ref["C"].detach()
+        fr_band = kap & dec.has_t & ((sig - prm.mu * C).abs() <= fr_tol)
+        # a static contact's friction is -s / w_t, smooth in s; a kinetic one's direction
+        # s / sigma is ill-conditioned when sigma is small against dt V
+        par_band = torch.zeros_like(flag)
+        par_band[..., 1:] = (kap & ~dec.static)[..., 1:] & (sig[..., 1:] / (prm.dt * prm.v_test) <= par_tol)
+        if gs:
+            amb = flag | fr_band | par_band | flip_contact | (face_band[..., None] & kap)
+            masked = torch.cummax(amb.to(torch.int8), dim=1).values.bool()
+        else:
+            masked = flag.clone()
+        comparable = ~(par_band.any(-1).any(-1) | face_band.any(-1))
+        L = ref["L"].detach()
+        G = ref["grad"]
+        W = ref["W"].detach()
+        q64 = np.asarray(q32, dtype=np.float64)
+        static = dec.static
+
+    # the alternatives of each comparable candidate: (table, point, simulation)
+    owner, picks = [], []
+    for b in torch.nonzero(comparable).flatten().tolist():
+        changes = [("sdf", i, -1) for i in torch.nonzero(has_alt[b]).flatten().tolist()]
+        changes += [("kappa", i, m) for i, m in torch.nonzero(tie[b] & ~has_alt[b][:, None]).tolist()]
+        changes += [("static", i, m) for i, m in torch.nonzero(fr_band[b]).tolist()]
+        if len(changes) > max_alternatives:
+            comparable[b] = False
+            continue
+        for subset in range(1, 1 << len(changes)):
+            owner.append(b)
+            picks.append([c_ for j, c_ in enumerate(changes) if subset >> j & 1])
+    branches = [{"L": L[b:b + 1].numpy(), "grad": G[b:b + 1].numpy(), "W": W[b:b + 1].numpy()} for b in range(B)]
+    for s0 in range(0, len(picks), chunk):
+        own = owner[s0:s0 + chunk]
+        n_ = len(own)
+        idx = torch.as_tensor(own)
+        cell_mask = torch.zeros(n_, P, dtype=torch.bool)
+        k_mask = torch.zeros(n_, P, M_SIMS, dtype=torch.bool)
+        s_mask = torch.zeros_like(k_mask)
+        for j, pick in enumerate(picks[s0:s0 + chunk]):
+            for table, i, m in pick:
+                if table == "sdf":
+                    cell_mask[j, i] = True
+                elif table == "kappa":
+                    k_mask[j, i, m] = True
+                else:
+                    s_mask[j, i, m] = True
+        force = {"kappa": (k_mask, ~kap[idx]), "static": (s_mask, ~static[idx])}
+        if alt is not None:
+            force["sdf"] = (cell_mask, {k: v[idx] for k, v in alt.items()})
+        qa = torch.as_tensor(q64[own]).clone().requires_grad_(True)
+        out = evaluate_any(hand, obj, qa, r, prm, force=force)
+        (ga,) = torch.autograd.grad(out["L"].sum(), qa)
+        La, Wa = out["L"].detach().numpy(), out["W"].detach().numpy()
+        for j, b in enumerate(own):
+            br = branches[b]
+            br["L"] = np.concatenate([br["L"], La[j:j + 1]])
+            br["grad"] = np.concatenate([br["grad"], ga[j:j + 1].numpy()])
+            br["W"] = np.concatenate([br["W"], Wa[j:j + 1]])
+    return {"flag": flag.numpy(), "masked": masked.numpy(), "comparable": comparable.numpy(),
+            "branches": branches,
+            "ref": {"L": L.numpy(), "grad": G.numpy(), "W": W.numpy(), "N": ref["N"].numpy(),
+                    "kappa": kap.numpy()}}

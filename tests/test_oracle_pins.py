@@ -619,3 +619,158 @@ def test_guard_band_excludes_near_ties():
     assert not clean(at(boundary + 5e-7))
     flat = obj_from(synth.linear_grid((0.0, 0.0, 1.0), 0.0, 32, 0.005), 1.0, 0.0)
     assert not clean([x, y, 0.004], flat)
+
+
+# ----------------------------------------------------------------------------- guard band per decision
+
+def _tilted():
+    c = np.array([0.3, 0.2, 1.0])
+    c /= np.linalg.norm(c)
+    return c, obj_from(synth.linear_grid(tuple(c), 0.0, 32, 0.005), 1.0, 0.0)
+
+
+def test_decision_band_on_a_linear_field():
+    """decision_band locates each near tie at its (point, simulation).  On the tilted
+    plane phi = c . x the trilinear interpolant is exact in every cell, so a point on a
+    node plane has the same value and normal in both cells: its flags are fixed and the
+    candidate stays comparable (clean_candidates drops it).  A point 0.5 micrometres
+    from the +z simulation's threshold phi_m = phi - dt V c_z = 0 has that one flag
+    ambiguous and its candidate is not robust, while the other six flags of the point
+    and the flags of a second, distant point are fixed."""
+    c, ob = _tilted()
+    prm = O.Params(mu=0.5)
+    dtv = prm.dt * prm.v_test
+    h = ob.pitch
+    org = ob.origin.numpy()
+    x, y = org[0] + 7.31 * h, org[1] + 9.47 * h
+
+    def at(phi, px=x):
+        return [px, y, (phi - c[0] * px - c[1] * y) / c[2]]
+
+    q = np.zeros((1, 6))
+    node = [at(dtv * c[2] + 3e-4, px=org[0] + 7.0 * h)]
+    res = O.decision_band(multi_point_hand(node), ob, q, 0.0, prm)
+    br = res["branches"][0]
+    assert not res["flag"].any() and res["comparable"][0] and len(br["L"]) == 2
+    # equal up to the float32 rounding of the stored grid values (the field is not exactly linear)
+    assert np.abs(br["L"] - br["L"][0]).max() < 1e-12
+    assert np.abs(br["grad"] - br["grad"][0]).max() < 1e-6 * np.abs(br["grad"][0]).max()
+    assert not O.clean_candidates(multi_point_hand(node), ob, q, 0.0, prm)[0]
+    tie = [at(dtv * c[2] + 5e-7), at(dtv * c[2] + 3e-3, px=x + 0.011)]
+    res = O.decision_band(multi_point_hand(tie), ob, q, 0.0, prm)
+    expect = np.zeros((1, 2, 7), dtype=bool)
+    expect[0, 0, 5] = True                               # +z is simulation 5
+    assert np.array_equal(res["flag"], expect) and np.array_equal(res["masked"], expect)
+    # both flags of the tie are branches: with the contact (N = 1, a push of ~0.5 um) and without
+    br = res["branches"][0]
+    assert res["comparable"][0] and len(br["L"]) == 2
+    ref = O.loss_and_grad(multi_point_hand(tie), ob, q, 0.0, prm)
+    assert br["L"][0] == float(ref["L"].detach()[0]) and br["L"][1] != br["L"][0]
+
+
+def test_decision_band_cell_choice_on_a_curved_field():
+    """On a grid-sampled sphere the normal jumps across a node plane.  A flag is
+    ambiguous exactly when phi_m taken just on either side of the plane (the lookup at
+    p -+ 1e-7 voxel along the axis, where the cell choice is each side's own) has
+    different signs or lies within the band.  Checked on points placed on node planes
+    in a shell around the dilated surface, where both outcomes occur."""
+    R = 0.04
+    ob = obj_from(synth.sphere_grid(R, 64, 0.002), 1.0)
+    hgrid = ob.pitch                                      # the float32 pitch of the grid
+    prm = O.Params()
+    rng = np.random.default_rng(4)
+    org = ob.origin.numpy()
+    V = np.array(O.TEST_DIRECTIONS, dtype=np.float64) * prm.v_test
+    seen = {True: 0, False: 0}
+    for _ in range(300):
+        u = rng.normal(size=3)
+        u /= np.linalg.norm(u)
+        p = u * (R + rng.uniform(-2e-4, 2e-3))
+        ax = rng.integers(3)
+        k = np.round((p[ax] - org[ax]) / hgrid)
+        p[ax] = org[ax] + k * hgrid                       # on a node plane
+        res = O.decision_band(one_point_hand(p), ob, np.zeros((1, 6)), 0.0, prm)
+        side = []
+        for s in (-1.0, 1.0):
+            ps = p.copy()
+            ps[ax] += s * 1e-7 * hgrid
+            phi, g = O.sdf_query(ob, torch.tensor(ps[None]), 0.0)
+            n = g[0].numpy() / np.linalg.norm(g[0].numpy())
+            side.append(float(phi[0]) - prm.dt * V @ n)
+        side = np.array(side)                             # [2, 7]
+        slack = 1e-6 + 2e-7 * hgrid
+        if (np.abs(side) <= slack).any() or (np.abs(np.abs(side) - 1e-6) < 1e-8).any():
+            continue                                      # on the band's edge: either answer is right
+        want = (np.sign(side[0]) != np.sign(side[1]))
+        assert np.array_equal(res["flag"][0, 0], want), (p, side)
+        seen[bool(want.any())] += 1
+    assert seen[True] >= 5 and seen[False] >= 50
+
+
+def test_decision_band_friction_regime():
+    """A single contact 0.5 micrometres from the friction boundary sigma = mu C of the
+    +x simulation: the force is continuous there (sigma / w_t on both sides) but its
+    derivative is not (d sigma against mu dC).  With a rotational inertia the static
+    regime does not cancel the tangential velocity of the object's centre, so the two
+    derivatives reach the loss: the flag is fixed, the two branches have nearly the
+    same loss and different gradients; 0.2 mm from the boundary there is one branch."""
+    c, ob = _tilted()
+    ob.inv_inertia = 1.0 / (0.4 * 0.05 ** 2)
+    prm = O.Params(mu=0.5)
+    dtv = prm.dt * prm.v_test
+    h = ob.pitch
+    org = ob.origin.numpy()
+    x, y = org[0] + 7.31 * h, org[1] + 9.47 * h
+    boundary = dtv * c[0] - dtv * np.sqrt(1.0 - c[0] ** 2) / prm.mu
+
+    def pt(phi):
+        return [x, y, (phi - c[0] * x - c[1] * y) / c[2]]
+
+    q = np.zeros((1, 6))
+    near = O.decision_band(one_point_hand(pt(boundary + 5e-7)), ob, q, 0.0, prm)
+    br = near["branches"][0]
+    assert not near["flag"].any() and near["comparable"][0] and len(br["L"]) == 2
+    assert abs(br["L"][1] - br["L"][0]) < 2e-5 * abs(br["L"][0])     # (sigma - mu C) / (w_t dt) apart
+    assert np.linalg.norm(br["grad"][1] - br["grad"][0]) > 1e-3 * np.linalg.norm(br["grad"][0])
+    far = O.decision_band(one_point_hand(pt(boundary + 2e-4)), ob, q, 0.0, prm)
+    assert not far["flag"].any() and far["comparable"][0] and len(far["branches"][0]["L"]) == 1
+
+
+def test_decision_band_gauss_seidel_masks_the_rest_of_a_chain():
+    """Gauss-Seidel form: the state a point sees depends on every earlier projection
+    of its simulation, so the comparison masks a chain from its first ambiguous
+    decision on.  Three points in contact (depths 2, 3 and 4 mm, so that after each
+    projection the next point is still clearly in contact): a near tie at the first
+    point masks all three in that simulation; a tie at the last point, at the state
+    the sweep reaches it with, masks only the last, and its flags are branches."""
+    c, ob = _tilted()
+    prm = O.Params(mu=0.5, gauss_seidel=1)
+    h = ob.pitch
+    org = ob.origin.numpy()
+    x, y = org[0] + 7.31 * h, org[1] + 9.47 * h
+
+    def pt(phi, dx=0.0):
+        px = x + dx
+        return [px, y, (phi - c[0] * px - c[1] * y) / c[2]]
+
+    q = np.zeros((1, 6))
+    m0 = 0                                               # the zero-velocity simulation
+    deep = [pt(-2e-3, 0.0), pt(-3e-3, 0.004), pt(-4e-3, 0.008)]
+    res = O.decision_band(multi_point_hand(deep), ob, q, 0.0, prm)
+    assert not res["masked"][0, :, m0].any()
+    # before any projection phi_m = phi: a tie at the first point
+    first = [pt(5e-7, 0.0), deep[1], deep[2]]
+    res = O.decision_band(multi_point_hand(first), ob, q, 0.0, prm)
+    assert res["flag"][0, 0, m0] and res["masked"][0, :, m0].all()
+    # the state before the last point (no rotation: inv_inertia = 0): phi_m = phi - n . D
+    base = O.evaluate_gs(multi_point_hand(deep), ob, torch.zeros(1, 6, dtype=F64), 0.0, prm)
+    st = base["dec"].state[0, 2, m0].numpy()
+    assert np.all(st[3:] == 0)
+    last = [deep[0], deep[1], pt(float(c @ st[:3]) + 5e-7, 0.008)]
+    res = O.decision_band(multi_point_hand(last), ob, q, 0.0, prm)
+    # static friction cancelled the tangential part of the state in every simulation, so
+    # the last point ties in all seven: each flag is a branch (2^7 combinations)
+    assert res["flag"][0, 2].all() and not res["flag"][0, :2].any()
+    assert (res["masked"][0] == np.array([[False] * 7, [False] * 7, [True] * 7])).all()
+    br = res["branches"][0]
+    assert res["comparable"][0] and len(br["L"]) == 128 and len(np.unique(br["L"])) > 1
