@@ -187,29 +187,6 @@ def test_gs_is_refused_where_unsupported(fg, tiny):
         qu.close()
 
 
-def test_gs_full_size_sampled_parity(fg):
-    """The benchmark workload at full size (8 superquadrics on 128^3 grids, 4-finger hand
-    with 4,352 points, 8,192 candidates) in the launch the benchmark times: loss and
-    update of 6 sampled candidates against the oracle's Gauss-Seidel form."""
-    w = synth.batched_superquadric_workload(device="cuda")
-    case = Case(fg, w)
-    params = dict(w.params, gauss_seidel=1)
-    S = case.oracle(params)
-    q = torch.tensor(w.q0, device=_dev())
-    q1 = q.clone()
-    loss = fg.optimize_step(case.hand, case.scene, q1, params, 0, w.steps, 1, obj_of_cand=case.oc)
-    torch.cuda.synchronize()
-    assert torch.isfinite(loss).all() and torch.isfinite(q1).all()
-    r = O.dilation_radius(S.prm, 0, w.steps)
-    sample = np.sort(np.random.default_rng(12).choice(w.B, size=6, replace=False))
-    ref = O.batch_loss_and_grad(S, w.q0[sample], w.obj_of_cand[sample], r)
-    clean = np.array([O.clean_candidates(S.hand, S.objs[int(w.obj_of_cand[b])], w.q0[b:b + 1], r, S.prm)[0]
-                      for b in sample])
-    assert clean.sum() >= 3
-    step = ((q1 - q).cpu().numpy()[sample]).astype(np.float64) / -params["lr"]
-    _compare(loss.cpu().numpy()[sample], step, ref, clean)
-
-
 def test_gs_ragged_hand_and_edge_cases(fg):
     """Links whose point ranges are not 32-aligned (chunks straddle links and are never
     culled), a last chunk of 18 points; an empty batch, a hand far from the object

@@ -269,70 +269,6 @@ def test_five_finger_polyhedra(fg):
     _compare_loss_grad(loss.cpu().numpy(), grad.cpu().numpy(), ref, case.clean(w.q0, r))
 
 
-def test_full_size_batched_sampled_parity(fg):
-    """The benchmark workload at full size (8 superquadrics on 128^3 grids, 4-finger
-    hand with 4,352 points, 8,192 candidates), in the launch the benchmark times:
-    loss and gradient of 16 sampled candidates against the oracle."""
-    w = synth.batched_superquadric_workload(device="cuda")
-    case = Case(fg, w)
-    q = torch.tensor(w.q0, device=_dev())
-    r = O.dilation_radius(case.S.prm, 0, w.steps)
-    loss, grad = fg.loss_and_grad(case.hand, case.scene, q, w.params, r, obj_of_cand=case.oc)
-    q1 = q.clone()
-    fg.optimize_step(case.hand, case.scene, q1, w.params, 0, w.steps, 1, obj_of_cand=case.oc)
-    torch.cuda.synchronize()
-    assert torch.isfinite(loss).all() and torch.isfinite(grad).all()
-    rng = np.random.default_rng(11)
-    sample = np.sort(rng.choice(w.B, size=16, replace=False))
-    sub = O.batch_loss_and_grad(case.S, w.q0[sample], w.obj_of_cand[sample], r)
-    clean = np.zeros(len(sample), dtype=bool)
-    for j, b in enumerate(sample):
-        k = int(w.obj_of_cand[b])
-        clean[j] = O.clean_candidates(case.S.hand, case.S.objs[k], w.q0[b:b + 1], r, case.S.prm)[0]
-    assert clean.sum() >= 8
-    _compare_loss_grad(loss.cpu().numpy()[sample], grad.cpu().numpy()[sample], sub, clean)
-    step = ((q1 - q).cpu().numpy()[sample]).astype(np.float64) / -w.params["lr"]
-    _compare_loss_grad(loss.cpu().numpy()[sample], step, sub, clean)
-
-
-def _sampled_full_size(fg, w, n_sample, seed):
-    """One loss-and-gradient launch and one optimisation launch over the whole workload,
-    then the oracle on sampled candidates (an oracle set-up holding only their objects)."""
-    hand = fg.Hand.from_synth(w.hand)
-    scene = fg.Scene([fg.Sdf.from_synth(o) for o in w.objects])
-    oc = torch.tensor(w.obj_of_cand, device=_dev(), dtype=torch.int32)
-    q = torch.tensor(w.q0, device=_dev())
-    r = O.dilation_radius(O.Params.from_dict(w.params), 0, w.steps)
-    loss, grad = fg.loss_and_grad(hand, scene, q, w.params, r, obj_of_cand=oc)
-    q1 = q.clone()
-    fg.optimize_step(hand, scene, q1, w.params, 0, w.steps, 1, obj_of_cand=oc)
-    torch.cuda.synchronize()
-    assert torch.isfinite(loss).all() and torch.isfinite(grad).all() and torch.isfinite(q1).all()
-    sample = np.sort(np.random.default_rng(seed).choice(w.B, size=n_sample, replace=False))
-    objs = sorted({int(w.obj_of_cand[b]) for b in sample})
-    S = O.Setup(w.hand, [w.objects[k] for k in objs], w.params)
-    local = np.array([objs.index(int(w.obj_of_cand[b])) for b in sample], dtype=np.int32)
-    ref = O.batch_loss_and_grad(S, w.q0[sample], local, r)
-    clean = np.array([O.clean_candidates(S.hand, S.objs[k], w.q0[b:b + 1], r, S.prm)[0]
-                      for b, k in zip(sample, local)])
-    assert clean.sum() >= n_sample // 2
-    _compare_loss_grad(loss.cpu().numpy()[sample], grad.cpu().numpy()[sample], ref, clean)
-    step = ((q1 - q).cpu().numpy()[sample]).astype(np.float64) / -w.params["lr"]
-    _compare_loss_grad(loss.cpu().numpy()[sample], step, ref, clean)
-
-
-def test_full_size_polyhedra_sampled_parity(fg):
-    """32 convex polyhedra (12-40 faces) on 128^3 grids, the 5-finger hand (5,888 points),
-    4,096 candidates per object (131,072) in one launch: 8 sampled candidates."""
-    _sampled_full_size(fg, synth.polyhedra_workload(device="cuda"), 8, 21)
-
-
-def test_full_size_sweep_sampled_parity(fg):
-    """256 objects (128 superquadrics, 128 polyhedra) on 192^3 grids (7.1 GB), the 5-finger
-    hand, 65,536 candidates in one launch: 8 sampled candidates."""
-    _sampled_full_size(fg, synth.sweep_workload(device="cuda"), 8, 22)
-
-
 def test_every_fused_configuration_matches_oracle(fg, tiny):
     """Each compiled (warps per candidate, register budget) configuration gives the
     oracle's loss and gradient; the autotuner selects one of them."""
