@@ -1,26 +1,36 @@
 """Benchmark of the grasp-search step (candidate-steps per second).
 
-Workload: 8 random superquadrics on 128^3 float32 SDF grids, the 4-finger
-synthetic hand (17 links, 4,352 points), 1,024 candidates per object (8,192),
-paper constants (alpha = 0.1, dt = 1 ms, lr = 1e-3), dilation 10 mm at step 0 of
-a 500-step linear schedule.  One timed step = one fused forward + adjoint +
-update launch over all candidates, starting from the initial candidates (q is
-reset by a device copy inside the timed region, so every step sees the same
-contact state).  The L2 is flushed (256 MiB write) between timed steps.
+Workload (default): the 256-object throughput sweep, 128 superquadrics and 128
+convex polyhedra on 192^3 float32 SDF grids (7.1 GB), the 5-finger synthetic hand
+(23 links, 5,888 points), 65,536 candidates (256 per object), paper constants
+(alpha = 0.1, dt = 1 ms, lr = 1e-3), dilation 10 mm at step 0 of a 1,000-step
+linear schedule.  One timed step = one fused forward + adjoint + update launch
+over all candidates, starting from the initial candidates (q is reset by a device
+copy inside the timed region, so every step sees the same contact state).  The
+L2 is flushed (256 MiB write) between timed steps.  `--workload` selects the
+8-superquadric batch (128^3, 4-finger hand, 8,192 candidates) or the 32 polyhedra
+instead; the 8-superquadric batch is also measured beside the sweep as a
+sub-record.
 
 Lines: the fused path (value), the plain per-stage GPU form (plain), the same
-step end to end through host buffers (e2e), the roofline of the fused kernel,
-sampled SM clocks, and the FP64 oracle on the host cores (cpu_baseline).
-`--impl reference` times the oracle alone on the same workload.
+step end to end through the library's host-buffer entry point (e2e), the
+roofline of the fused kernel (ALU time at the measured FP32 peak against DRAM time
+at the measured HBM bandwidth), sampled SM clocks, and the FP64 oracle on the
+host cores (cpu_baseline).  `--impl reference` times the oracle alone on the same
+workload.
+
+Multi-GPU (`--gpus N` under torchrun): the workload's objects are split into N
+contiguous blocks; each rank builds only its objects' grids and optimises only
+their candidates, with no exchange in the step loop; the job time is the slowest
+rank's, and one optimisation step's (q, loss) is gathered on rank 0 at the end.
 
 Optional legs on the same candidates: --gs (Gauss-Seidel projection), --tstep T
 (the T-step metric), --mesh (the objects as meshes with the Phong SDF; with --gs
 also that combination), --quality (contact area and epsilon), --order-quality (the
 grasps of a whole optimisation in the Jacobi and the Gauss-Seidel order, compared
-by their quality metrics), --serving N and
---serving-sweep (request latency against offered load); --workload selects the
-larger polyhedra32 / sweep256 configurations; --profile-kernel runs a few
-launches of the selected kernel for ncu and exits.
+by their quality metrics), --serving N and --serving-sweep (request latency
+against offered load); --profile-kernel runs a few launches of the selected
+kernel for ncu and exits.
 """
 
 from __future__ import annotations
@@ -41,7 +51,8 @@ sys.path.insert(0, ROOT)
 
 # Algorithmic floating-point operations per point-step: the method as the FP64
 # oracle computes it (forward pass + reverse mode, every branch evaluated), from
-# the oracle's counting instantiation (oracle/flop_count.py) on this workload.
+# the oracle's counting instantiation (oracle/flop_count.py); the same for the
+# 4- and 5-finger hands.
 FLOPS_PER_POINT_STEP = 2092
 # The fused kernel's own minimal count for a point out of contact (forward once +
 # leaky adjoint once, FMA = 2), reported beside it.
@@ -50,9 +61,10 @@ KERNEL_MIN_FLOPS_PER_POINT_STEP = 599
 GS_FLOPS_PER_POINT_STEP = 2540
 # The T-step form, by the number of simulation steps T (same counter, same workload).
 TSTEP_FLOPS_PER_POINT_STEP = {1: 6228, 2: 13061, 4: 26729}
-SM_COUNT = 152
-FP32_LANES_PER_SM = 128
 METRIC = "candidate-steps/sec fused fwd+bwd vs plain GPU form at 1e-3 grad tol; p50/p99 latency"
+WORKLOADS = ("sweep256", "superquadric8", "polyhedra32")
+# HBM copy bandwidth when the measured-peaks file is absent (the profiling recipe's fallback)
+FALLBACK_HBM_GBS = 6800.0
 
 
 def dist_env():
@@ -110,9 +122,11 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-def load_traffic(kernel_tag: str):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on the
-    current kernel sources (matching source hash); else None."""
+def load_profile(kernel_tag: str, workload: str):
+    """The committed ncu figures of one kernel on one workload (profiles/traffic.txt),
+    if they were taken on the current kernel sources (matching source hash): DRAM
+    bytes per launch and, where recorded, the FP32 operations the kernel executes per
+    point-step (FADD, FMUL 1, FFMA 2, packed forms twice).  None otherwise."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
     if not os.path.exists(path):
         return None
@@ -120,35 +134,55 @@ def load_traffic(kernel_tag: str):
     cur = source_hash(FUSED_SOURCES)
     for line in open(path):
         parts = line.split()
-        if len(parts) >= 3 and parts[0] == kernel_tag and parts[1] == cur:
-            return float(parts[2])
+        if line.startswith("#") or len(parts) < 4:
+            continue
+        if parts[0] == kernel_tag and parts[1] == workload and parts[2] == cur:
+            rec = {"traffic": float(parts[3]), "source_hash": cur}
+            if len(parts) >= 5 and parts[4] != "-":
+                rec["executed_fp32_flops_per_point_step"] = float(parts[4])
+            return rec
     return None
 
 
-WORKLOADS = ("superquadric8", "polyhedra32", "sweep256")
+def measured_hbm_gbs():
+    """(HBM copy bandwidth in GB/s, its basis): the driver's measured-peaks file, else the
+    profiling recipe's fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "measured (STREAM-style copy)"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
 
 
-def build_workload(device, rank, kind="superquadric8", n_obj=8, per_obj=1024, grid_n=128):
-    """The benchmark workload for one rank: by default the 8 superquadrics (128^3), the
-    4-finger hand and 8,192 candidates (sizes adjustable for tests); "polyhedra32" the 32 polyhedra (128^3) with the
-    5-finger hand and 131,072 candidates; "sweep256" the 256 objects (192^3) with the
-    5-finger hand and 65,536 candidates.  Weak scaling: every rank holds the same objects
-    and its own share of the global candidate set (rank 0 the recipe's candidates, rank
-    k > 0 candidates drawn from seed base + 100 + k), so ranks never exchange data."""
+def build_workload(device, rank: int = 0, world: int = 1, kind: str = "sweep256", lazy: bool = False, **sizes):
+    """Rank `rank`'s share of a benchmark workload and a description of the partition.
+
+    Workloads: "sweep256" the 256 objects (192^3) with the 5-finger hand and 65,536
+    candidates; "superquadric8" the 8 superquadrics (128^3) with the 4-finger hand and
+    8,192 candidates; "polyhedra32" the 32 polyhedra (128^3) with the 5-finger hand and
+    131,072 candidates (sizes adjustable for tests).  The objects are split into
+    `world` contiguous blocks; rank k builds only the grids of block k and keeps the
+    candidates of those objects (object indices renumbered within the block).  With
+    lazy=True no grid is built (``synth.realize`` builds one when it is needed)."""
     import synth
+    from paper_2306_08132_gb300 import shard
     if kind == "polyhedra32":
-        w = synth.polyhedra_workload(device=device)
+        full = synth.polyhedra_workload(device=device, build=False, **sizes)
     elif kind == "sweep256":
-        w = synth.sweep_workload(device=device)
+        full = synth.sweep_workload(device=device, build=False, **sizes)
+    elif kind == "superquadric8":
+        full = synth.batched_superquadric_workload(device=device, build=False, **sizes)
     else:
-        w = synth.batched_superquadric_workload(n_obj=n_obj, per_obj=per_obj, grid_n=grid_n, device=device)
-    if rank:
-        rng = np.random.default_rng(synth.workloads.SEED_BASE + 100 + rank)
-        from synth.candidates import sample_candidates
-        per_obj = w.B // len(w.objects)
-        q = [sample_candidates(rng, w.hand, per_obj, o["bound_radius"] + 0.06) for o in w.objects]
-        w.q0 = np.concatenate(q)
-    return w
+        raise ValueError("unknown workload %r" % kind)
+    part = shard.shard_workload(len(full.objects), full.obj_of_cand, rank, world)
+    objs = [full.objects[k] if lazy else synth.realize(full.objects[k], device) for k in part["objects"]]
+    w = synth.Workload(full.name, full.hand, objs, full.q0[part["candidates"]], part["obj_of_cand"],
+                       full.params, full.steps)
+    grid_bytes = int(sum(o["grid"].numel() * o["grid"].element_size() for o in objs if "grid" in o))
+    info = {"objects": part["objects"], "candidates": part["candidates"], "total_candidates": full.B,
+            "total_objects": len(full.objects), "grid_bytes": grid_bytes}
+    return w, info
 
 
 def max_over_ranks(value: float, world: int, device="cpu") -> float:
@@ -162,22 +196,79 @@ def max_over_ranks(value: float, world: int, device="cpu") -> float:
     return float(t.item())
 
 
-def oracle_rate(w, budget_s: float, r: float, max_cands: int | None = None):
-    """FP64 oracle on the host: candidate-steps/s over chunks of candidates until the
-    time budget is used."""
+def sum_over_ranks(value: float, world: int, device="cpu") -> float:
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def oracle_sample(w, n_objects: int = 2):
+    """The FP64 oracle's set-up for the candidates of the workload's first n_objects
+    objects (the sample the CPU legs time), on the host: (setup, q, object indices)."""
+    import synth
+    from oracle import fastgraspd_oracle as O
+    objs = [synth.realize(o, "cpu") for o in w.objects[:n_objects]]
+    keep = np.nonzero(np.asarray(w.obj_of_cand) < n_objects)[0]
+    S = O.Setup(w.hand, objs, w.params)
+    return S, w.q0[keep], np.asarray(w.obj_of_cand)[keep]
+
+
+def oracle_rate(S, q, oc, budget_s: float, r: float, max_cands: int | None = None, offset: int = 0):
+    """FP64 oracle on the host: candidate-steps/s over chunks of 8 candidates of the
+    sample until the time budget (or max_cands) is used."""
     import torch
     from oracle import fastgraspd_oracle as O
-    S = O.Setup(w.hand, w.objects, w.params)
     done, t0 = 0, time.perf_counter()
-    B = w.B
-    rng = np.random.default_rng(3)
-    order = rng.permutation(B)
+    B = len(q)
+    order = np.random.default_rng(3).permutation(B)
     while time.perf_counter() - t0 < budget_s and (max_cands is None or done < max_cands):
-        sel = order[done % B:done % B + 8]
-        O.batch_loss_and_grad(S, w.q0[sel], w.obj_of_cand[sel], r, chunk=8)
+        start = (offset + done) % B
+        sel = order[start:start + 8]
+        O.batch_loss_and_grad(S, q[sel], oc[sel], r, chunk=8)
         done += len(sel)
     dt = time.perf_counter() - t0
     return done / dt, done, dt, torch.get_num_threads()
+
+
+def measure_fp32_peak(fg, device, gpu_index: int, seconds: float = 0.6):
+    """FP32 fused multiply-add throughput of this GPU (the library's microbenchmark,
+    scalar FFMA and packed f32x2 FMA, 8 independent chains per thread, 8 CTAs of 256
+    threads per SM), timed with CUDA events, SM clocks sampled meanwhile.  The peak is
+    the faster form's best launch."""
+    import torch
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    out = torch.empty(sms * 8 * 256, device=device)
+    stream = torch.cuda.current_stream()
+    res = {}
+    sampler = ClockSampler(gpu_index)
+    sampler.start()
+    for packed in (False, True):
+        fg.fp32_peak_launch(out, packed, 1000)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fg.fp32_peak_launch(out, packed, 20000)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        iters = max(1000, int(20000 * 150.0 / max(e0.elapsed_time(e1), 1e-3)))    # ~150 ms a launch
+        best = 0.0
+        t_end = time.perf_counter() + seconds
+        while time.perf_counter() < t_end:
+            e0.record(stream)
+            flops = fg.fp32_peak_launch(out, packed, iters)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            best = max(best, flops / (e0.elapsed_time(e1) / 1000.0) / 1e12)
+        res["packed" if packed else "scalar"] = best
+    clocks = sampler.stop()
+    form = max(res, key=res.get)
+    return {"tflops": res[form], "form": form, "scalar_tflops": res["scalar"], "packed_tflops": res["packed"],
+            "sms": sms, "clocks": clocks,
+            "basis": "FMA microbenchmark (fg_fp32_peak_launch): %d SMs x 8 CTAs x 256 threads, 8 chains each, "
+                     "best of ~150 ms launches" % sms}
 
 
 def run_serving(fg, n_requests: int, rates_hz, device, budget_bytes: int, steps_per_launch: int = 10):
@@ -292,22 +383,27 @@ def run_order_quality(fg, w, hand, scene, oc, q0, device, lrs, steps_per_launch:
              "mu 0.5, interior lattice 3 mm (%d samples)" % (w.B, w.steps, 1000.0 * w.params["r0"], ih["P"]))
     return {"setup": setup, "runs": runs}
 
+
+
 def run_reference(args):
+    """The reference arm: the FP64 oracle, as it stands, on the host cores, on the same
+    workload (each timed step a bounded sample of it: 16 candidates of its first two
+    objects, one step each).  Under torchrun only rank 0 runs."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     import torch
-    import synth
     from oracle import fastgraspd_oracle as O
-    w = synth.batched_superquadric_workload(device="cpu")
-    r = O.dilation_radius(O.Params.from_dict(w.params), 0, w.steps)
+    w, _ = build_workload("cpu", 0, 1, args.workload, lazy=True)
+    S, qs, ocs = oracle_sample(w)
+    r = O.dilation_radius(S.prm, 0, w.steps)
     per_step = 16
-    for _ in range(args.warmup):
-        oracle_rate(w, 0.0, r, max_cands=8)
+    for k in range(args.warmup):
+        oracle_rate(S, qs, ocs, 0.0, r, max_cands=8, offset=8 * k)
     t0 = time.perf_counter()
     total = 0
-    for _ in range(args.steps):
-        _, n, _, cores = oracle_rate(w, 1e9, r, max_cands=per_step)
+    for k in range(args.steps):
+        _, n, _, cores = oracle_rate(S, qs, ocs, 1e9, r, max_cands=per_step, offset=per_step * k)
         total += n
     dt = time.perf_counter() - t0
     value = total / dt
@@ -316,11 +412,195 @@ def run_reference(args):
             "ms_per_step": 1000.0 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w.name, "candidates": w.B, "points_per_candidate": w.hand["P"],
-                       "sample_per_step": "%d candidates x 1 step (FP64 oracle, host cores)" % per_step},
+                       "sample_per_step": "%d candidates x 1 step (FP64 oracle, host cores), drawn from the "
+                                          "candidates of the workload's first two objects" % per_step},
             "cpu_baseline": {"value": value, "unit": "candidate-steps/s", "cores": torch.get_num_threads(),
                              "kind": "oracle", "sample": "%d candidates x %d steps" % (per_step, args.steps)},
             "e2e": {"value": value, "unit": "candidate-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+
+def graphed(step_fn):
+    """Capture one step (q reset + launches) in a CUDA graph; replaying it keeps host
+    launch latency out of the per-step device time."""
+    import torch
+    for _ in range(2):
+        step_fn()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        step_fn()
+    torch.cuda.synchronize()
+    return g.replay
+
+
+def prewarm(fn, seconds=0.5):
+    import torch
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        fn()
+        torch.cuda.synchronize()
+
+
+def timed(step_fn, nsteps, warm, flush, world, pre=None):
+    """Per-step device time (ms) with CUDA events on the launching stream; the L2 flush
+    (and `pre`, e.g. a reset of q) run before each start event.  Barriers on both
+    sides under torchrun."""
+    import torch
+    stream = torch.cuda.current_stream()
+    for _ in range(warm):
+        if pre is not None:
+            pre()
+        step_fn()
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(nsteps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(nsteps)]
+    for i in range(nsteps):
+        flush.fill_(i & 0xff)
+        if pre is not None:
+            pre()
+        starts[i].record(stream)
+        step_fn()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    return ms
+
+
+class Bound:
+    """A workload bound to the library on one device."""
+
+    def __init__(self, fg, w, device):
+        import torch
+        self.w = w
+        self.hand = fg.Hand.from_synth(w.hand)
+        self.sdfs = [fg.Sdf.from_synth(o) for o in w.objects]
+        self.scene = fg.Scene(self.sdfs)
+        self.oc = torch.tensor(w.obj_of_cand, device=device, dtype=torch.int32)
+        self.q0 = torch.tensor(w.q0, device=device)
+        self.q = self.q0.clone()
+        self.loss = torch.empty(w.B, device=device)
+
+
+def roofline_of(w, S_in, kern_ms, peak, hbm_gbs, hbm_basis, prof):
+    """Roofline of one fused launch: the ALU time of the method's work at the measured
+    FP32 peak against the DRAM time of the launch's measured traffic at the HBM
+    bandwidth; the slower one bounds it.  Three fractions of the ALU peak, by the
+    basis of the flop count."""
+    units = w.B * w.hand["P"] * S_in
+    kern_s = kern_ms / 1000.0
+    P = peak["tflops"]
+    flops = FLOPS_PER_POINT_STEP * units
+    t_alu = flops / (P * 1e12)
+    traffic = prof["traffic"] if prof else None
+    t_hbm = traffic / (hbm_gbs * 1e9) if traffic else None
+    bound = "alu" if t_hbm is None or t_alu >= t_hbm else "hbm"
+    alu_tflops = flops / kern_s / 1e12
+    fractions = {
+        "oracle_count": {"flops_per_point_step": FLOPS_PER_POINT_STEP, "frac": alu_tflops / P,
+                         "basis": "the method's work as the FP64 oracle computes it (oracle/flop_count.py: "
+                                  "forward pass + reverse mode, both arms of every select)"},
+        "kernel_minimal": {"flops_per_point_step": KERNEL_MIN_FLOPS_PER_POINT_STEP,
+                           "frac": KERNEL_MIN_FLOPS_PER_POINT_STEP * units / kern_s / 1e12 / P,
+                           "basis": "the fused kernel's own operation count for a point out of contact "
+                                    "(forward once + leaky adjoint once, FMA = 2); contacts add work"},
+        "executed_fp32": None,
+    }
+    if prof and "executed_fp32_flops_per_point_step" in prof:
+        x = prof["executed_fp32_flops_per_point_step"]
+        fractions["executed_fp32"] = {"flops_per_point_step": x, "frac": x * units / kern_s / 1e12 / P,
+                                      "basis": "FP32 operations the kernel executes (ncu instruction counts of "
+                                               "this workload: FADD, FMUL 1, FFMA 2, packed f32x2 forms twice)"}
+    rec = {"bound": bound, "kernel_ms": kern_ms, "traffic": traffic,
+           "alu_time_ms": 1000.0 * t_alu, "hbm_time_ms": None if t_hbm is None else 1000.0 * t_hbm,
+           "flops_per_launch": flops, "flops_per_point_step": FLOPS_PER_POINT_STEP,
+           "flops_basis": fractions["oracle_count"]["basis"], "fractions": fractions,
+           "alu_peak_tflops": P, "alu_peak_basis": "of measured: " + peak["basis"],
+           "alu_peak_derived_tflops": (peak["sms"] * 128 * 2 * peak["clocks"]["sm_mhz"] * 1e6 / 1e12
+                                       if peak.get("clocks") and peak["clocks"].get("sm_mhz") else None),
+           "hbm_peak_gbs": hbm_gbs, "hbm_basis": hbm_basis}
+    if bound == "alu":
+        rec.update({"achieved": alu_tflops, "peak": P, "unit": "TFLOP/s", "frac": alu_tflops / P})
+    else:
+        rec.update({"achieved": traffic / kern_s / 1e9, "peak": hbm_gbs, "unit": "GB/s",
+                    "frac": traffic / kern_s / 1e9 / hbm_gbs})
+    return rec
+
+
+def measure_fused(fg, b, args, world, flush, peak, label_clocks=None):
+    """The fused step on one bound workload: autotuned configuration, graphed timed steps,
+    the per-stage form, the host-buffer end-to-end step and the kernel-only time for
+    the roofline."""
+    import torch
+    w, S_in, K = b.w, args.inner_steps, b.w.steps
+
+    def fused_step():
+        b.q.copy_(b.q0)
+        fg.optimize_step(b.hand, b.scene, b.q, w.params, 0, K, S_in, obj_of_cand=b.oc, loss=b.loss)
+
+    best_cfg, cfg_ms = fg.autotune(b.hand, b.scene, b.q0, w.params, 0, K, S_in, obj_of_cand=b.oc, reps=3)
+    cfgs = fg.fused_configs()
+    if args.config is not None:
+        best_cfg = args.config
+        fg.fused_config_select(best_cfg)
+    g = graphed(fused_step)
+    prewarm(g)
+    sampler = ClockSampler(label_clocks) if label_clocks is not None else None
+    if sampler:
+        sampler.start()
+    t_wall = time.perf_counter()
+    ms = timed(g, args.steps, args.warmup, flush, world)
+    wall = time.perf_counter() - t_wall
+    clocks = sampler.stop() if sampler else None
+    out = {"ms": ms, "wall": wall, "clocks": clocks, "best_cfg": best_cfg, "cfg_ms": cfg_ms, "cfgs": cfgs}
+
+    if not args.no_plain:
+        ws = torch.empty(fg.plain_workspace_size(b.hand, w.B) + 256, dtype=torch.uint8, device=b.q.device)
+
+        def plain_step():
+            b.q.copy_(b.q0)
+            fg.optimize_step_plain(b.hand, b.scene, b.q, w.params, 0, K, S_in, obj_of_cand=b.oc, loss=b.loss,
+                                   workspace=ws)
+
+        pms = timed(graphed(plain_step), max(3, args.steps // 2), 3, flush, world)
+        pstep = float(np.mean(pms))
+        out["plain"] = {"value": w.B * S_in / (pstep / 1000.0), "ms_per_step": pstep,
+                        "speedup_fused_over_plain": pstep / float(np.mean(ms)), "gpu_launches_per_step": 8 * S_in}
+        del ws
+    else:
+        out["plain"] = None
+
+    # end to end: pinned host q in, the step, q and loss back to pinned host memory,
+    # every copy made by the library's host-buffer entry point
+    hq0 = torch.tensor(w.q0).pin_memory()
+    hq = torch.empty_like(hq0).pin_memory()
+    hloss = torch.empty(w.B).pin_memory()
+
+    def e2e_step():
+        fg.optimize_step_host(b.hand, b.scene, hq0, b.q, w.params, 0, K, S_in, obj_of_cand=b.oc, loss=b.loss,
+                              host_q_out=hq, host_loss=hloss)
+
+    ems = timed(e2e_step, max(3, args.steps // 2), 3, flush, world)
+    out["e2e_ms"] = float(np.mean(ems))
+    out["e2e_bytes"] = (int(hq0.numel() * 4), int(hq.numel() * 4 + hloss.numel() * 4))
+
+    def kernel_only():
+        fg.optimize_step(b.hand, b.scene, b.q, w.params, 0, K, S_in, obj_of_cand=b.oc, loss=b.loss)
+
+    def reset_q():
+        b.q.copy_(b.q0)
+
+    kms = timed(graphed(kernel_only), max(3, args.steps // 2), 3, flush, world, pre=reset_q)
+    out["kern_ms"] = float(np.mean(kms))
+    out["fused_step"] = fused_step
+    return out
 
 
 def main():
@@ -332,15 +612,16 @@ def main():
     ap.add_argument("--inner-steps", type=int, default=1, help="optimisation steps per fused launch")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle time for cpu_baseline")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-sub", action="store_true", help="skip the 8-superquadric sub-record")
     ap.add_argument("--profile-kernel", action="store_true",
                     help="set up the workload, run a few fused launches and exit (for ncu)")
     ap.add_argument("--config", type=int, default=None, help="fused configuration index (default: autotune)")
-    ap.add_argument("--serving", type=int, default=40, help="requests in the serving (p50/p99) run; 0 skips it")
+    ap.add_argument("--serving", type=int, default=500, help="requests in the serving (p50/p99) run; 0 skips it")
     ap.add_argument("--serving-rate", type=float, default=200.0)
     ap.add_argument("--tstep", default="",
                     help="comma-separated T: also time the T-step metric (SDF re-queried for T steps) on this workload")
-    ap.add_argument("--workload", default="superquadric8", choices=WORKLOADS,
-                    help="superquadric8 (the benchmark configuration), polyhedra32 or sweep256 (larger configurations)")
+    ap.add_argument("--workload", default="sweep256", choices=WORKLOADS,
+                    help="sweep256 (256 objects on 192^3, the default), superquadric8 or polyhedra32")
     ap.add_argument("--gs", action="store_true",
                     help="also time the Gauss-Seidel form (constraints projected in point order) on this workload")
     ap.add_argument("--quality", action="store_true",
@@ -352,8 +633,8 @@ def main():
     ap.add_argument("--order-quality-lr", default="1e-3,1e-5,1e-6,1e-7",
                     help="learning rates of the --order-quality runs")
     ap.add_argument("--mesh", action="store_true",
-                    help="also time the fused step on mesh objects (the same superquadrics as watertight meshes, "
-                         "queried through the BVH with the Phong SDF)")
+                    help="also time the fused step on mesh objects (the superquadric8 workload's objects as "
+                         "watertight meshes, queried through the BVH with the Phong SDF)")
     ap.add_argument("--mesh-res", default="24,48", help="latitude,longitude divisions of the superquadric meshes")
     ap.add_argument("--serving-sweep", default="",
                     help="comma-separated arrival rates (req/s) for a latency-vs-load sweep of the same stream")
@@ -374,206 +655,177 @@ def main():
     if world > 1:
         dist.barrier()
     import paper_2306_08132_gb300 as fg
-    from oracle import fastgraspd_oracle as O   # rank 0 cpu_baseline leg only
+    from paper_2306_08132_gb300 import shard
 
-    w = build_workload(dev, rank, args.workload)
-    hand = fg.Hand.from_synth(w.hand)
-    sdfs = [fg.Sdf.from_synth(o) for o in w.objects]
-    scene = fg.Scene(sdfs)
-    oc = torch.tensor(w.obj_of_cand, device=dev, dtype=torch.int32)
-    q0 = torch.tensor(w.q0, device=dev)
-    q = q0.clone()
-    loss = torch.empty(w.B, device=dev)
-    K = w.steps
-    S_in = args.inner_steps
+    w, part = build_workload(dev, rank, world, args.workload)
+    b = Bound(fg, w, dev)
+    K, S_in = w.steps, args.inner_steps
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream()
-
-    def fused_step():
-        q.copy_(q0)
-        fg.optimize_step(hand, scene, q, w.params, 0, K, S_in, obj_of_cand=oc, loss=loss)
 
     if args.profile_kernel:
         if args.config is not None:
             fg.fused_config_select(args.config)
         if args.tstep:                       # the T-step kernel instead, T = the first value
-            pT = dict(w.params, sim_steps=int(args.tstep.split(",")[0]))
-            for _ in range(3):
-                q.copy_(q0)
-                fg.optimize_step(hand, scene, q, pT, 0, K, S_in, obj_of_cand=oc, loss=loss)
+            prm = dict(w.params, sim_steps=int(args.tstep.split(",")[0]))
         elif args.gs:                        # the Gauss-Seidel kernel
-            pG = dict(w.params, gauss_seidel=1)
-            for _ in range(3):
-                q.copy_(q0)
-                fg.optimize_step(hand, scene, q, pG, 0, K, S_in, obj_of_cand=oc, loss=loss)
-        elif args.mesh:                      # the fused kernel on the superquadrics as meshes
-            from synth import meshes as SM
-            n_lat, n_lon = [int(x) for x in args.mesh_res.split(",")]
-            mobjs = [SM.superquadric_mesh(o["params"]["semi_axes"], float(np.clip(o["params"]["eps1"], 0.5, 1.5)),
-                                          float(np.clip(o["params"]["eps2"], 0.5, 1.5)), n_lat, n_lon)
-                     for o in w.objects]
-            mscene = fg.Scene([fg.Sdf.from_synth(m) for m in mobjs])
-            for _ in range(3):
-                q.copy_(q0)
-                fg.optimize_step(hand, mscene, q, w.params, 0, K, S_in, obj_of_cand=oc, loss=loss)
-        elif args.quality:                   # the epsilon kernel over 1,024 directions
-            import synth as _synth
-            dirs = torch.tensor(_synth.unit_directions(1024), device=dev)
-            for _ in range(3):
-                fg.grasp_epsilon(hand, scene, q0, 0.005, 0.5, 8, 1.0 / 0.08, dirs, obj_of_cand=oc)
+            prm = dict(w.params, gauss_seidel=1)
         else:
-            for _ in range(5):
-                fused_step()
+            prm = w.params
+        if args.mesh:                        # the fused kernel on the superquadrics as meshes
+            scene = fg.Scene([fg.Sdf.from_synth(m) for m in superquadric_meshes(w, args.mesh_res)])
+        else:
+            scene = b.scene
+        for _ in range(3 if (args.tstep or args.gs or args.mesh or args.quality) else 5):
+            if args.quality:                 # the epsilon kernel over 1,024 directions
+                import synth as _synth
+                dirs = torch.tensor(_synth.unit_directions(1024), device=dev)
+                fg.grasp_epsilon(b.hand, scene, b.q0, 0.005, 0.5, 8, 1.0 / 0.08, dirs, obj_of_cand=b.oc)
+            else:
+                b.q.copy_(b.q0)
+                fg.optimize_step(b.hand, scene, b.q, prm, 0, K, S_in, obj_of_cand=b.oc, loss=b.loss)
         torch.cuda.synchronize()
         return
 
-    ws = None if args.no_plain else torch.empty(fg.plain_workspace_size(hand, w.B) + 256, dtype=torch.uint8,
-                                                device=dev)
-
-    def plain_step():
-        q.copy_(q0)
-        fg.optimize_step_plain(hand, scene, q, w.params, 0, K, S_in, obj_of_cand=oc, loss=loss, workspace=ws)
-
-    def graphed(step_fn):
-        """Capture one step (q reset + launches) in a CUDA graph; replaying it keeps
-        host launch latency out of the per-step device time."""
-        for _ in range(2):
-            step_fn()
-        torch.cuda.synchronize()
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g):
-            step_fn()
-        torch.cuda.synchronize()
-        return g.replay
-
-    def prewarm(fn, seconds=0.5):
-        t0 = time.perf_counter()
-        while time.perf_counter() - t0 < seconds:
-            fn()
-            torch.cuda.synchronize()
-
-    def timed(step_fn, nsteps, warm, pre=None):
-        """Per-step device time with CUDA events on the launching stream; the L2
-        flush (and `pre`, e.g. a reset of q) run before each start event."""
-        for _ in range(warm):
-            if pre is not None:
-                pre()
-            step_fn()
-        torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
-        starts = [torch.cuda.Event(enable_timing=True) for _ in range(nsteps)]
-        ends = [torch.cuda.Event(enable_timing=True) for _ in range(nsteps)]
-        for i in range(nsteps):
-            flush.fill_(i & 0xff)
-            if pre is not None:
-                pre()
-            starts[i].record(stream)
-            step_fn()
-            ends[i].record(stream)
-        torch.cuda.synchronize()
-        ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-        if world > 1:
-            dist.barrier()
-        return ms
-
-    # the project's autotuner picks the fused-kernel configuration on this workload
-    best_cfg, cfg_ms = fg.autotune(hand, scene, q0, w.params, 0, K, S_in, obj_of_cand=oc, reps=3)
-    cfgs = fg.fused_configs()
-    if args.config is not None:
-        best_cfg = args.config
-        fg.fused_config_select(best_cfg)
-    fused_graph = graphed(fused_step)
-    prewarm(fused_graph)
-    sampler = ClockSampler(local)
-    sampler.start()
-    t_wall = time.perf_counter()
-    ms = timed(fused_graph, args.steps, args.warmup)
-    wall = time.perf_counter() - t_wall
-    clocks = sampler.stop()
+    peak = measure_fp32_peak(fg, dev, local)
+    hbm_gbs, hbm_basis = measured_hbm_gbs()
+    res = measure_fused(fg, b, args, world, flush, peak, label_clocks=local)
+    ms = res["ms"]
     ms_step = max_over_ranks(float(np.mean(ms)), world, dev)
-    cand_steps = w.B * S_in * world
+    cand_steps = sum_over_ranks(w.B * S_in, world, dev)
     value = cand_steps / (ms_step / 1000.0)
-
-    plain = None
-    if not args.no_plain:
-        plain_graph = graphed(plain_step)
-        pms = timed(plain_graph, max(3, args.steps // 2), 3)
-        pstep = float(np.mean(pms))
-        plain = {"value": w.B * S_in / (pstep / 1000.0), "ms_per_step": pstep,
-                 "speedup_fused_over_plain": pstep / float(np.mean(ms)), "gpu_launches_per_step": 8 * S_in}
-
-    # e2e: pinned host q in, fused step, q and loss back to pinned host, per step
-    hq0 = torch.tensor(w.q0).pin_memory()
-    hq = torch.empty_like(hq0).pin_memory()
-    hloss = torch.empty(w.B).pin_memory()
-
-    def e2e_step():
-        q.copy_(hq0, non_blocking=True)
-        fg.optimize_step(hand, scene, q, w.params, 0, K, S_in, obj_of_cand=oc, loss=loss)
-        hq.copy_(q, non_blocking=True)
-        hloss.copy_(loss, non_blocking=True)
-
-    ems = timed(e2e_step, max(3, args.steps // 2), 3)
-    e2e_ms = max_over_ranks(float(np.mean(ems)), world, dev)
+    e2e_ms = max_over_ranks(res["e2e_ms"], world, dev)
     e2e = {"value": cand_steps / (e2e_ms / 1000.0), "unit": "candidate-steps/s",
-           "h2d_bytes_per_step": int(hq0.numel() * 4), "d2h_bytes_per_step": int(hq.numel() * 4 + hloss.numel() * 4)}
+           "h2d_bytes_per_step": res["e2e_bytes"][0], "d2h_bytes_per_step": res["e2e_bytes"][1],
+           "entry_point": "fg_optimize_step_host (pinned host q in; q and loss out)"}
+    roofline = roofline_of(w, S_in, res["kern_ms"], peak, hbm_gbs, hbm_basis, load_profile("fused_step", w.name))
+    cfgs, best_cfg = res["cfgs"], res["best_cfg"]
 
-    # roofline of the fused kernel (ALU-bound): kernel time measured alone on the stream
-    def kernel_only():
-        fg.optimize_step(hand, scene, q, w.params, 0, K, S_in, obj_of_cand=oc, loss=loss)
+    sub = None
+    if not args.no_sub and args.workload != "superquadric8" and world == 1:
+        w2, _ = build_workload(dev, 0, 1, "superquadric8")
+        b2 = Bound(fg, w2, dev)
+        r2 = measure_fused(fg, b2, args, 1, flush, peak)
+        m2 = float(np.mean(r2["ms"]))
+        sub = {"workload": w2.name, "value": w2.B * S_in / (m2 / 1000.0), "unit": "candidate-steps/s",
+               "ms_per_step": m2, "plain": r2["plain"],
+               "e2e": {"value": w2.B * S_in / (r2["e2e_ms"] / 1000.0), "unit": "candidate-steps/s"},
+               "roofline": roofline_of(w2, S_in, r2["kern_ms"], peak, hbm_gbs, hbm_basis,
+                                       load_profile("fused_step", w2.name)),
+               "fused_config": "%dw/%d/%dp" % r2["cfgs"][r2["best_cfg"]]}
+        del b2
+        fg.autotune(b.hand, b.scene, b.q0, w.params, 0, K, S_in, obj_of_cand=b.oc, reps=3)   # back to the main workload
 
-    def reset_q():
-        q.copy_(q0)
+    legs = run_legs(fg, args, b, dev, world, flush, cand_steps)
+    grid_bytes = int(sum_over_ranks(part["grid_bytes"], world, dev))
 
-    kms = timed(graphed(kernel_only), max(3, args.steps // 2), 3, pre=reset_q)
-    kern_ms = float(np.mean(kms))
-    flops = FLOPS_PER_POINT_STEP * w.B * w.hand["P"] * S_in
-    achieved = flops / (kern_ms / 1000.0) / 1e12
-    peak = SM_COUNT * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12
-    min_achieved = KERNEL_MIN_FLOPS_PER_POINT_STEP * w.B * w.hand["P"] * S_in / (kern_ms / 1000.0) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": load_traffic("fused_step"), "kernel_ms": kern_ms,
-                "flops_per_launch": flops, "flops_per_point_step": FLOPS_PER_POINT_STEP,
-                "flops_basis": "oracle counting instantiation (forward + reverse mode)",
-                "kernel_min_flops_per_point_step": KERNEL_MIN_FLOPS_PER_POINT_STEP,
-                "frac_kernel_min": min_achieved / peak,
-                "peak_basis": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz"}
+    # multi-GPU: one optimisation step of every rank's candidates, gathered on rank 0
+    gathered = None
+    if world > 1:
+        b.q.copy_(b.q0)
+        fg.optimize_step(b.hand, b.scene, b.q, w.params, 0, K, 1, obj_of_cand=b.oc, loss=b.loss)
+        torch.cuda.synchronize()
+        Q = shard.gather_rows(b.q.cpu().numpy(), part["candidates"], part["total_candidates"])
+        L = shard.gather_rows(b.loss.cpu().numpy(), part["candidates"], part["total_candidates"])
+        if rank == 0:
+            gathered = {"candidates": int(Q.shape[0]), "finite": bool(np.isfinite(Q).all() and np.isfinite(L).all())}
 
-    tstep = None
+    if rank == 0:
+        from oracle import fastgraspd_oracle as O   # the cpu_baseline leg only
+        S, qs, ocs = oracle_sample(w)
+        r0 = O.dilation_radius(S.prm, 0, K)
+        rate, n, dt, cores = oracle_rate(S, qs, ocs, args.cpu_budget, r0)
+        cpu = {"value": rate, "unit": "candidate-steps/s", "cores": cores, "kind": "oracle",
+               "sample": "%d candidates x 1 step of the workload's first two objects in %.1f s (FP64, torch CPU)"
+                         % (n, dt)}
+        if args.cpu_budget > 0:
+            threads = torch.get_num_threads()
+            torch.set_num_threads(1)
+            try:
+                r1, n1, dt1, _ = oracle_rate(S, qs, ocs, args.cpu_budget / 3.0, r0)
+            finally:
+                torch.set_num_threads(threads)
+            cpu["value_1_thread"] = r1
+            cpu["sample_1_thread"] = "%d candidates x 1 step in %.1f s on one thread" % (n1, dt1)
+        line = {"metric": METRIC, "value": value, "unit": "candidate-steps/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+                "scaling": "strong" if world > 1 else "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": w.name, "objects": part["total_objects"],
+                           "grid": "%d^3 f32" % w.objects[0]["grid"].shape[0],
+                           "hand": "%d-finger, %d links, %d points" % (w.hand["kind"], w.hand["L"], w.hand["P"]),
+                           "candidates": int(cand_steps // S_in), "inner_steps_per_launch": S_in,
+                           "state": "q reset to the initial candidates each step",
+                           "l2": "flushed between timed steps (256 MiB write)", "parallelism": "dp%d" % world,
+                           "partition": ("objects in %d contiguous blocks, one per rank; rank 0 holds %d objects "
+                                         "(%d grid bytes) and %d candidates" % (world, len(part["objects"]),
+                                                                                part["grid_bytes"], w.B)),
+                           "grid_bytes": grid_bytes,
+                           "fused_config": {"warps_per_candidate": cfgs[best_cfg][0],
+                                            "min_ctas_per_sm": cfgs[best_cfg][1],
+                                            "points_per_thread": cfgs[best_cfg][2],
+                                            "autotune_ms": {"%dw/%d/%dp" % c: round(t, 4)
+                                                            for c, t in zip(cfgs, res["cfg_ms"])}}},
+                "plain": res["plain"], "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
+                "fp32_peak": peak, "superquadric8": sub,
+                "latency": None if legs["serving"] is None else {"p50_s": legs["serving"]["p50_s"],
+                                                                 "p99_s": legs["serving"]["p99_s"]},
+                **legs, "gathered": gathered,
+                "gpu_launches": args.steps, "clocks": res["clocks"],
+                "wall_s_timed_region": res["wall"],
+                "per_step_ms": {"min": float(np.min(ms)), "median": float(np.median(ms)), "max": float(np.max(ms))}}
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def superquadric_meshes(w, mesh_res):
+    """The workload's superquadrics as watertight latitude/longitude meshes (exponents
+    held to [0.5, 1.5]: sharper ones fold the pole triangles)."""
+    from synth import meshes as SM
+    n_lat, n_lon = [int(x) for x in mesh_res.split(",")]
+    out = []
+    for o in w.objects:
+        if o["kind"] != "superquadric":
+            raise ValueError("the mesh leg needs superquadric objects (--workload superquadric8)")
+        pr = o["params"]
+        e1, e2 = [float(np.clip(pr[k], 0.5, 1.5)) for k in ("eps1", "eps2")]
+        out.append(SM.superquadric_mesh(pr["semi_axes"], e1, e2, n_lat, n_lon))
+    return out
+
+
+def run_legs(fg, args, b, dev, world, flush, cand_steps):
+    """The optional legs on the bound workload (each None unless asked for)."""
+    import torch
+    w, K, S_in = b.w, b.w.steps, args.inner_steps
+    out = {"tstep": None, "gauss_seidel": None, "mesh": None, "quality": None, "order_quality": None,
+           "serving": None, "serving_sweep": None}
+    units = w.B * w.hand["P"] * S_in
+
+    def step_with(prm, scene=None):
+        def f():
+            b.q.copy_(b.q0)
+            fg.optimize_step(b.hand, scene or b.scene, b.q, prm, 0, K, S_in, obj_of_cand=b.oc, loss=b.loss)
+        return f
+
     if args.tstep:
-        tstep = []
+        out["tstep"] = []
         for T in [int(x) for x in args.tstep.split(",") if x.strip()]:
-            pT = dict(w.params, sim_steps=T)
-
-            def tstep_step(pT=pT):
-                q.copy_(q0)
-                fg.optimize_step(hand, scene, q, pT, 0, K, S_in, obj_of_cand=oc, loss=loss)
-
-            tms = timed(graphed(tstep_step), max(3, args.steps // 4), 3)
+            tms = timed(graphed(step_with(dict(w.params, sim_steps=T))), max(3, args.steps // 4), 3, flush, world)
             t_ms = max_over_ranks(float(np.mean(tms)), world, dev)
             rec = {"T": T, "ms_per_step": t_ms, "value": cand_steps / (t_ms / 1000.0),
                    "unit": "candidate-steps/s", "sdf_queries_per_point_step": 2 * 7 * T}
             if T in TSTEP_FLOPS_PER_POINT_STEP:
                 rec["flops_per_point_step"] = TSTEP_FLOPS_PER_POINT_STEP[T]
-                rec["achieved_tflops"] = TSTEP_FLOPS_PER_POINT_STEP[T] * w.B * w.hand["P"] * S_in / (t_ms / 1e3) / 1e12
-            tstep.append(rec)
+                rec["achieved_tflops"] = TSTEP_FLOPS_PER_POINT_STEP[T] * units / (t_ms / 1e3) / 1e12
+            out["tstep"].append(rec)
 
-    gs = None
     if args.gs:
-        pG = dict(w.params, gauss_seidel=1)
-
-        def gs_step():
-            q.copy_(q0)
-            fg.optimize_step(hand, scene, q, pG, 0, K, S_in, obj_of_cand=oc, loss=loss)
-
-        gms = timed(graphed(gs_step), max(3, args.steps // 4), 3)
+        gms = timed(graphed(step_with(dict(w.params, gauss_seidel=1))), max(3, args.steps // 4), 3, flush, world)
         g_ms = max_over_ranks(float(np.mean(gms)), world, dev)
-        gs = {"ms_per_step": g_ms, "value": cand_steps / (g_ms / 1000.0), "unit": "candidate-steps/s",
-              "flops_per_point_step": GS_FLOPS_PER_POINT_STEP,
-              "achieved_tflops": GS_FLOPS_PER_POINT_STEP * w.B * w.hand["P"] * S_in / (g_ms / 1000.0) / 1e12}
+        out["gauss_seidel"] = {"ms_per_step": g_ms, "value": cand_steps / (g_ms / 1000.0),
+                               "unit": "candidate-steps/s", "flops_per_point_step": GS_FLOPS_PER_POINT_STEP,
+                               "achieved_tflops": GS_FLOPS_PER_POINT_STEP * units / (g_ms / 1000.0) / 1e12}
 
-    quality = None
     if args.quality:
         import synth as _synth
         areas = torch.tensor(w.hand["point_area"], device=dev)
@@ -581,104 +833,47 @@ def main():
         qeps = torch.empty(w.B, device=dev)
 
         def ca_step():
-            fg.contact_measure(hand, scene, q0, areas, 0.005, obj_of_cand=oc)
+            fg.contact_measure(b.hand, b.scene, b.q0, areas, 0.005, obj_of_cand=b.oc)
 
         def eps_step():
-            e, _ = fg.grasp_epsilon(hand, scene, q0, 0.005, 0.5, 8, 1.0 / 0.08, dirs, obj_of_cand=oc)
+            e, _ = fg.grasp_epsilon(b.hand, b.scene, b.q0, 0.005, 0.5, 8, 1.0 / 0.08, dirs, obj_of_cand=b.oc)
             qeps.copy_(e)
 
-        cms = timed(ca_step, max(3, args.steps // 4), 3)
-        ems_ = timed(eps_step, max(3, args.steps // 4), 3)
-        e, nc = fg.grasp_epsilon(hand, scene, q0, 0.005, 0.5, 8, 1.0 / 0.08, dirs, obj_of_cand=oc)
+        cms = timed(ca_step, max(3, args.steps // 4), 3, flush, world)
+        ems_ = timed(eps_step, max(3, args.steps // 4), 3, flush, world)
+        _, nc = fg.grasp_epsilon(b.hand, b.scene, b.q0, 0.005, 0.5, 8, 1.0 / 0.08, dirs, obj_of_cand=b.oc)
         ncm = float(nc.float().mean())
-        quality = {"contact_area_ms": float(np.mean(cms)), "epsilon_ms": float(np.mean(ems_)),
-                   "candidates": w.B, "threshold_m": 0.005, "directions": 1024, "cone_edges": 8,
-                   "mean_contacts": ncm,
-                   "epsilon_direction_contact_pairs_per_s": 1024 * ncm * w.B / (float(np.mean(ems_)) / 1000.0)}
+        out["quality"] = {"contact_area_ms": float(np.mean(cms)), "epsilon_ms": float(np.mean(ems_)),
+                          "candidates": w.B, "threshold_m": 0.005, "directions": 1024, "cone_edges": 8,
+                          "mean_contacts": ncm,
+                          "epsilon_direction_contact_pairs_per_s": 1024 * ncm * w.B / (float(np.mean(ems_)) / 1e3)}
 
-    mesh = None
     if args.mesh:
-        from synth import meshes as SM
-        n_lat, n_lon = [int(x) for x in args.mesh_res.split(",")]
-        mobjs = []
-        for o in w.objects:
-            pr = o["params"]
-            # exponents held to [0.5, 1.5]: sharper ones fold the pole triangles of a lat/long mesh
-            e1, e2 = [float(np.clip(pr[k], 0.5, 1.5)) for k in ("eps1", "eps2")]
-            mobjs.append(SM.superquadric_mesh(pr["semi_axes"], e1, e2, n_lat, n_lon))
+        mobjs = superquadric_meshes(w, args.mesh_res)
         mscene = fg.Scene([fg.Sdf.from_synth(m) for m in mobjs])
-
-        def mesh_step():
-            q.copy_(q0)
-            fg.optimize_step(hand, mscene, q, w.params, 0, K, S_in, obj_of_cand=oc, loss=loss)
-
-        mms = timed(graphed(mesh_step), max(3, args.steps // 4), 3)
+        mms = timed(graphed(step_with(w.params, mscene)), max(3, args.steps // 4), 3, flush, world)
         m_ms = max_over_ranks(float(np.mean(mms)), world, dev)
-        mesh = {"ms_per_step": m_ms, "value": cand_steps / (m_ms / 1000.0), "unit": "candidate-steps/s",
-                "objects": "%d superquadric meshes, %d faces each, Phong SDF" % (len(mobjs), len(mobjs[0]["faces"])),
-                "fused_config": "%dw/%d/%dp" % fg.fused_configs()[fg.fused_config_current()]}
+        out["mesh"] = {"ms_per_step": m_ms, "value": cand_steps / (m_ms / 1000.0), "unit": "candidate-steps/s",
+                       "objects": "%d superquadric meshes, %d faces each, Phong SDF" % (len(mobjs),
+                                                                                         len(mobjs[0]["faces"])),
+                       "fused_config": "%dw/%d/%dp" % fg.fused_configs()[fg.fused_config_current()]}
         if args.gs:                          # the paper's combination: Phong SDF of a mesh, Gauss-Seidel
-            pGm = dict(w.params, gauss_seidel=1)
-
-            def mesh_gs_step():
-                q.copy_(q0)
-                fg.optimize_step(hand, mscene, q, pGm, 0, K, S_in, obj_of_cand=oc, loss=loss)
-
-            gms2 = timed(graphed(mesh_gs_step), max(3, args.steps // 4), 3)
+            gms2 = timed(graphed(step_with(dict(w.params, gauss_seidel=1), mscene)), max(3, args.steps // 4), 3,
+                         flush, world)
             mg_ms = max_over_ranks(float(np.mean(gms2)), world, dev)
-            mesh["gauss_seidel"] = {"ms_per_step": mg_ms, "value": cand_steps / (mg_ms / 1000.0),
-                                    "unit": "candidate-steps/s"}
+            out["mesh"]["gauss_seidel"] = {"ms_per_step": mg_ms, "value": cand_steps / (mg_ms / 1000.0),
+                                           "unit": "candidate-steps/s"}
 
-    order_quality = None
     if args.order_quality:
-        order_quality = run_order_quality(fg, w, hand, scene, oc, q0, dev,
-                                          [float(x) for x in args.order_quality_lr.split(",")])
+        out["order_quality"] = run_order_quality(fg, w, b.hand, b.scene, b.oc, b.q0, dev,
+                                                 [float(x) for x in args.order_quality_lr.split(",")])
 
-    serving, sweep = None, None
     if args.serving > 0:
         free, _ = torch.cuda.mem_get_info()
         rates = [args.serving_rate] + [float(x) for x in args.serving_sweep.split(",") if x.strip()]
         runs = run_serving(fg, args.serving, rates, dev, int(0.5 * free))
-        serving, sweep = runs[0], (runs[1:] or None)
-
-    if rank == 0:
-        r0 = O.dilation_radius(O.Params.from_dict(w.params), 0, K)
-        rate, n, dt, cores = oracle_rate(w, args.cpu_budget, r0)
-        cpu = {"value": rate, "unit": "candidate-steps/s", "cores": cores, "kind": "oracle",
-               "sample": "%d candidates x 1 step of the same workload in %.1f s (FP64, torch CPU)" % (n, dt)}
-        if args.cpu_budget > 0:
-            import torch as _t
-            threads = _t.get_num_threads()
-            _t.set_num_threads(1)
-            try:
-                r1, n1, dt1, _ = oracle_rate(w, args.cpu_budget / 3.0, r0)
-            finally:
-                _t.set_num_threads(threads)
-            cpu["value_1_thread"] = r1
-            cpu["sample_1_thread"] = "%d candidates x 1 step in %.1f s on one thread" % (n1, dt1)
-        line = {"metric": METRIC, "value": value, "unit": "candidate-steps/s", "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": w.name, "objects": len(w.objects),
-                           "grid": "%d^3 f32" % w.objects[0]["grid"].shape[0],
-                           "hand": "%d-finger, %d links, %d points" % (w.hand["kind"], w.hand["L"], w.hand["P"]),
-                           "candidates": w.B * world,
-                           "inner_steps_per_launch": S_in, "state": "q reset to the initial candidates each step",
-                           "l2": "flushed between timed steps (256 MiB write)", "parallelism": "dp%d" % world,
-                           "fused_config": {"warps_per_candidate": cfgs[best_cfg][0],
-                                            "min_ctas_per_sm": cfgs[best_cfg][1],
-                                            "points_per_thread": cfgs[best_cfg][2],
-                                            "autotune_ms": {"%dw/%d/%dp" % c: round(t, 4)
-                                                            for c, t in zip(cfgs, cfg_ms)}}},
-                "plain": plain, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu,
-                "latency": None if serving is None else {"p50_s": serving["p50_s"], "p99_s": serving["p99_s"]},
-                "serving": serving, "serving_sweep": sweep, "tstep": tstep, "gauss_seidel": gs, "mesh": mesh,
-                "quality": quality, "order_quality": order_quality,
-                "gpu_launches": args.steps * 1, "clocks": clocks, "wall_s_timed_region": wall,
-                "per_step_ms": {"min": float(np.min(ms)), "median": float(np.median(ms)), "max": float(np.max(ms))}}
-        print(json.dumps(line))
-    if world > 1:
-        dist.destroy_process_group()
+        out["serving"], out["serving_sweep"] = runs[0], (runs[1:] or None)
+    return out
 
 
 if __name__ == "__main__":

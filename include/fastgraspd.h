@@ -30,12 +30,16 @@
  *    immutable after creation; they may be shared by concurrent streams.  Destroy
  *    a handle only after the work that uses it has completed.
  *  - The persistent kernels take candidates from a counter that each launch
- *    draws from a pool of 1,024 and leaves at zero when it ends.  Calls may run on
- *    concurrent streams (fewer than 1,024 launches of one kind in flight at once).
- *    A call captured in a CUDA graph keeps the counter it drew at capture, so one
- *    graph must not be replayed on two streams at once (capture one per stream).
- *    Run each kind of call once before capturing it: its first launch on a device
- *    sets kernel attributes and looks up the counter pool.
+ *    draws from a pool and leaves at zero when it ends.  Eager calls cycle
+ *    through 1,024 counters per kind of call, so calls may run on concurrent
+ *    streams (fewer than 1,024 launches of one kind in flight at once).  A call
+ *    captured in a CUDA graph keeps the counter it drew at capture; captured
+ *    calls draw from a separate range of 16,384 counters that eager calls never
+ *    use, so a graph may replay while any number of eager calls run.  One graph
+ *    must not be replayed on two streams at once (capture one per stream), and
+ *    graphs captured 16,384 or more captures of one kind apart may share a counter
+ *    (do not run those at once).  Run each kind of call once before capturing it:
+ *    its first launch on a device sets kernel attributes and looks up the pool.
  *  - Configuration vector layout, per candidate (row-major [B][D]):
  *      q = (t_x, t_y, t_z, w_x, w_y, w_z, theta_0 .. theta_{J-1}),  D = 6 + J,
  *    t the palm origin (metres), w the palm rotation vector (R_b = Exp(w)),
@@ -239,6 +243,20 @@ fg_status fg_optimize_step(const fg_hand* hand, const fg_scene* scene, const int
                            float* q, int B, const fg_params* host_params, int step, int total_steps,
                            int nsteps, float* loss, void* stream);
 
+/* fg_optimize_step from and to host memory (Sec. IV-A, as fg_optimize_step): on
+ * `stream`, copies host_q_in [B][D] to the device buffer q [B][D] (caller-owned
+ * scratch, overwritten), runs the nsteps, then copies q to host_q_out [B][D] and,
+ * when host_loss is non-NULL, the device loss [B] (then required) to host_loss.
+ * Asynchronous like every compute call: the host buffers must stay valid, and be
+ * read only after the stream reaches this point; pinned host memory makes the
+ * copies asynchronous, pageable memory makes them synchronous.  host_q_in and
+ * host_q_out may be the same buffer.  Errors as fg_optimize_step, plus
+ * FG_ERR_INVALID for a NULL buffer. */
+fg_status fg_optimize_step_host(const fg_hand* hand, const fg_scene* scene, const int* obj_of_cand,
+                                const float* host_q_in, float* q, int B, const fg_params* host_params, int step,
+                                int total_steps, int nsteps, float* loss, float* host_q_out, float* host_loss,
+                                void* stream);
+
 /* The same step as fg_optimize_step, run as the plain one-kernel-per-stage
  * form: FK links -> point transform -> SDF query -> contact forward -> loss ->
  * contact adjoint -> link reduction -> FK adjoint + update, with the per-point
@@ -296,7 +314,10 @@ typedef struct {
 fg_status fg_queue_create(size_t hbm_budget_bytes, const fg_queue_opts* opts, fg_queue** out);
 /* Non-blocking.  FG_ERR_BUDGET if the request alone exceeds the budget (it could
  * never be admitted); FG_ERR_BUSY if max_requests are outstanding; FG_ERR_INVALID
- * for a malformed request. */
+ * for a malformed request; FG_ERR_OOM if its host copy cannot be allocated (a
+ * request whose device state cannot be allocated at admission fails with
+ * FG_ERR_OOM, reported by fg_queue_result); FG_ERR_CUDA once the queue has failed
+ * (a round exceeded timeout_ms or a CUDA call failed) or is being destroyed. */
 fg_status fg_queue_submit(fg_queue* queue, const fg_request* host_req, uint64_t* id);
 /* Non-blocking: *done = 1 once the request finished (or failed). */
 fg_status fg_queue_poll(fg_queue* queue, uint64_t id, int* done);
@@ -308,7 +329,11 @@ fg_status fg_queue_wait(fg_queue* queue, uint64_t id, int timeout_ms);
 fg_status fg_queue_result(fg_queue* queue, uint64_t id, float* host_q, float* host_loss, double* latency_s);
 fg_status fg_queue_stats(fg_queue* queue, fg_queue_stat* out);
 /* Waiting requests are dropped, the round in flight completes, then the
- * queue's resources are freed. */
+ * queue's resources are freed.  After a round that exceeded timeout_ms the
+ * kernel may still be running: destroy waits for the queue's stream at most
+ * timeout_ms more and, if it has not drained, returns FG_ERR_TIMEOUT and leaves
+ * the handle valid (call fg_queue_destroy again later; nothing else may be
+ * called on it).  It never blocks without a bound. */
 fg_status fg_queue_destroy(fg_queue* queue);
 
 /* ------------------------------------------------------------ no allocation */
@@ -398,6 +423,33 @@ fg_status fg_fused_config_current(int* index);
 fg_status fg_autotune(const fg_hand* hand, const fg_scene* scene, const int* obj_of_cand, const float* q, int B,
                       const fg_params* host_params, int step, int total_steps, int nsteps, int reps,
                       float* host_times_ms, int* best, void* stream);
+
+/* ---------------------------------------------------------------------- testing
+ * The paper has no counterpart: a hook that lets tests exercise the library's
+ * out-of-memory paths without exhausting the device.
+ *
+ * fg_test_fail_allocation(after): after `after` more allocation points pass,
+ * the next one fails as if the allocation had returned out-of-memory, once;
+ * -1 disarms.  Allocation points: the device buffers of fg_hand_create, the grid
+ * of fg_sdf_create, the host copy of a request in fg_queue_submit and a request's
+ * device state at admission.  Process-wide; not for use while other threads
+ * create handles or submit requests.  Errors: FG_ERR_INVALID (after < -1). */
+fg_status fg_test_fail_allocation(int after);
+
+/* ------------------------------------------------------------------ measurement
+ * The paper has no counterpart: this is the measured denominator of the ALU
+ * roofline that the library's kernels are reported against.
+ *
+ * fg_fp32_peak_launch enqueues one kernel of `blocks` CTAs of 256 threads, each
+ * thread running 8 independent chains of `iters` fused multiply-adds, as scalar
+ * FFMA (packed = 0: 2 flops each) or packed f32x2 FMA (packed != 0: 4 flops
+ * each), and stores one float per thread in out (device, blocks * 256 floats,
+ * caller-owned; the values are of no use).  *host_flops (nullable) receives the
+ * floating-point operations of the launch; the caller times it on `stream` (CUDA
+ * events) and divides.  Size it to several hundred milliseconds and a multiple
+ * of the SM count for a steady figure.  Errors: FG_ERR_INVALID (blocks < 1,
+ * iters < 1, out NULL), FG_ERR_CUDA. */
+fg_status fg_fp32_peak_launch(int packed, int blocks, int iters, float* out, double* host_flops, void* stream);
 
 #ifdef __cplusplus
 }

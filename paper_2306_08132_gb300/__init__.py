@@ -9,9 +9,9 @@ from .autograd import GraspLoss, grasp_loss
 from .api import (Hand, Sdf, Scene, make_params, fk, sdf_query, contact_wrench, loss_and_grad,
                   optimize_step, optimize_step_plain, plain_workspace_size, fused_configs, fused_config_select,
                   fused_config_current, autotune, Queue,
-                  optimize_step_plain_noalloc, contact_measure, grasp_epsilon)
+                  optimize_step_plain_noalloc, contact_measure, grasp_epsilon, fp32_peak_launch, optimize_step_host, test_fail_allocation)
 
 __all__ = ["GraspLoss", "grasp_loss", "Hand", "Sdf", "Scene", "make_params", "fk", "sdf_query", "contact_wrench", "loss_and_grad",
            "optimize_step", "optimize_step_plain", "plain_workspace_size", "fused_configs",
            "fused_config_select", "fused_config_current", "autotune", "Queue",
-           "optimize_step_plain_noalloc", "contact_measure", "grasp_epsilon"]
+           "optimize_step_plain_noalloc", "contact_measure", "grasp_epsilon", "fp32_peak_launch", "optimize_step_host", "test_fail_allocation"]

@@ -78,6 +78,7 @@ SIGNATURES = {
     "fg_contact_wrench": [_vp, _vp, _vp, _vp, _i, C.POINTER(Params), _f, _vp, _vp, _vp, _vp],
     "fg_loss_and_grad": [_vp, _vp, _vp, _vp, _i, C.POINTER(Params), _f, _vp, _vp, _vp],
     "fg_optimize_step": [_vp, _vp, _vp, _vp, _i, C.POINTER(Params), _i, _i, _i, _vp, _vp],
+    "fg_optimize_step_host": [_vp, _vp, _vp, _vp, _vp, _i, C.POINTER(Params), _i, _i, _i, _vp, _vp, _vp, _vp],
     "fg_contact_measure": [_vp, _vp, _vp, _vp, _i, _vp, _f, _vp, _vp],
     "fg_grasp_epsilon": [_vp, _vp, _vp, _vp, _i, _f, _f, _i, _f, _vp, _i, _vp, _vp, _vp],
     "fg_plain_workspace_size": [_vp, _i, C.POINTER(C.c_size_t)],
@@ -95,6 +96,8 @@ SIGNATURES = {
     "fg_fused_config_select": [_i],
     "fg_fused_config_current": [C.POINTER(_i)],
     "fg_autotune": [_vp, _vp, _vp, _vp, _i, C.POINTER(Params), _i, _i, _i, _i, C.POINTER(_f), C.POINTER(_i), _vp],
+    "fg_fp32_peak_launch": [_i, _i, _i, _vp, C.POINTER(C.c_double), _vp],
+    "fg_test_fail_allocation": [_i],
 }
 _RESTYPE = {"fg_status_string": C.c_char_p}
 OPTIONAL = set()

@@ -312,6 +312,36 @@ def autotune(hand: Hand, scene: Scene, q: torch.Tensor, params: dict, step: int 
     return best.value, [float(t) for t in times]
 
 
+def optimize_step_host(hand: Hand, scene: Scene, host_q_in: torch.Tensor, q: torch.Tensor, params: dict, step: int,
+                       total_steps: int, nsteps: int = 1, obj_of_cand: torch.Tensor | None = None,
+                       loss: torch.Tensor | None = None, host_q_out: torch.Tensor | None = None,
+                       host_loss: torch.Tensor | None = None):
+    """fg_optimize_step from and to host memory: the library copies host_q_in into the
+    device scratch q, steps, and copies q (and the loss) back into host_q_out /
+    host_loss (pinned CPU tensors for asynchronous copies; host_q_out defaults to
+    host_q_in).  Asynchronous on the current stream."""
+    B = q.shape[0]
+    _dptr(q, "q", shape=(B, hand.D))
+    for t, name in ((host_q_in, "host_q_in"), (host_q_out, "host_q_out"), (host_loss, "host_loss")):
+        if t is not None and (t.device.type != "cpu" or t.dtype != _F32 or not t.is_contiguous()):
+            raise ValueError("%s must be a contiguous float32 CPU tensor" % name)
+    if host_q_out is None:
+        host_q_out = host_q_in
+    if tuple(host_q_in.shape) != (B, hand.D) or tuple(host_q_out.shape) != (B, hand.D):
+        raise ValueError("host q buffers must be [B, D]")
+    if host_loss is not None and loss is None:
+        loss = torch.empty(B, device=q.device, dtype=_F32)
+    prm = make_params(params)
+    check(_lib.load().fg_optimize_step_host(hand.handle, scene.handle, _oc(obj_of_cand, B),
+                                            C.c_void_p(host_q_in.data_ptr()), _dptr(q, "q"), B, C.byref(prm),
+                                            int(step), int(total_steps), int(nsteps),
+                                            _dptr(loss, "loss", shape=(B,)) if loss is not None else None,
+                                            C.c_void_p(host_q_out.data_ptr()),
+                                            C.c_void_p(host_loss.data_ptr()) if host_loss is not None else None,
+                                            _stream()), "fg_optimize_step_host")
+    return loss
+
+
 def optimize_step_plain_noalloc(hand: Hand, scene: Scene, q: torch.Tensor, params: dict, step: int,
                                 total_steps: int, nsteps: int = 1, obj_of_cand: torch.Tensor | None = None,
                                 loss: torch.Tensor | None = None):
@@ -377,10 +407,40 @@ class Queue:
         check(_lib.load().fg_queue_stats(self.handle, C.byref(st)), "fg_queue_stats")
         return {k: getattr(st, k) for k, _ in st._fields_}
 
-    def close(self) -> None:
-        if getattr(self, "handle", None) is not None and _lib._lib is not None:
-            _lib._lib.fg_queue_destroy(self.handle)
-            self.handle = None
+    def close(self, attempts: int = 100) -> None:
+        """Destroy the queue.  After a round that exceeded timeout_ms the library may
+        report that its stream has not drained yet (FG_ERR_TIMEOUT, each wait bounded
+        by timeout_ms); the destroy is retried up to `attempts` times, then raises."""
+        if getattr(self, "handle", None) is None or _lib._lib is None:
+            return
+        for _ in range(max(1, attempts)):
+            st = _lib._lib.fg_queue_destroy(self.handle)
+            if st != 4:                                  # FG_ERR_TIMEOUT: the stream is still busy
+                break
+        if st == 4:
+            check(st, "fg_queue_destroy")
+        self.handle = None
 
     def __del__(self):
-        self.close()
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fp32_peak_launch(out: torch.Tensor, packed: bool, iters: int) -> float:
+    """Enqueue the FP32 fused multiply-add throughput kernel on the current stream:
+    out.numel() // 256 CTAs of 256 threads, 8 chains of iters FMAs per thread,
+    scalar or packed f32x2.  Returns the launch's floating-point operations; the
+    caller times the launch."""
+    blocks = out.numel() // 256
+    flops = C.c_double()
+    check(_lib.load().fg_fp32_peak_launch(int(bool(packed)), int(blocks), int(iters), _dptr(out, "out"),
+                                          C.byref(flops), _stream()), "fg_fp32_peak_launch")
+    return flops.value
+
+
+def test_fail_allocation(after: int) -> None:
+    """Arm the library's allocation-failure injection (tests): after `after` more
+    allocation points pass, the next one fails with FG_ERR_OOM, once; -1 disarms."""
+    check(_lib.load().fg_test_fail_allocation(int(after)), "fg_test_fail_allocation")

@@ -1,10 +1,11 @@
 """torch.autograd.Function over the fused loss/adjoint kernel.
 
-Forward runs fg_loss_and_grad once: the loss and, when q needs a gradient, dL/dq
-from the hand-written adjoint (which recomputes each point's forward quantities
-inside the kernel, so nothing per point is kept).  Only the [B, D] gradient is
-saved for backward, which scales it by the incoming gradient.  The gradient is
-the paper's leaky one (Sec. III-C), not the exact derivative of the loss.
+Forward runs fg_loss_and_grad for the loss alone (no adjoint sweep) and saves
+only q.  Backward runs fg_loss_and_grad again with the gradient: the fused
+kernel recomputes the forward quantities of each point inside the adjoint, so
+nothing per point is kept between the passes, and a forward-only call pays for
+the forward sweep alone.  The gradient is the paper's leaky one (Sec. III-C),
+not the exact derivative of the loss.
 """
 
 from __future__ import annotations
@@ -17,16 +18,17 @@ from . import api
 class GraspLoss(torch.autograd.Function):
     @staticmethod
     def forward(ctx, q, hand, scene, params, r_dil, obj_of_cand):
-        need = q.requires_grad
-        loss, grad = api.loss_and_grad(hand, scene, q.detach().contiguous(), params, r_dil,
-                                       obj_of_cand=obj_of_cand, want_grad=need)
-        if need:
-            ctx.save_for_backward(grad)
+        qd = q.detach().contiguous()
+        loss, _ = api.loss_and_grad(hand, scene, qd, params, r_dil, obj_of_cand=obj_of_cand, want_grad=False)
+        ctx.save_for_backward(qd)
+        ctx.args = (hand, scene, params, r_dil, obj_of_cand)
         return loss
 
     @staticmethod
     def backward(ctx, g_loss):
-        (grad,) = ctx.saved_tensors
+        (qd,) = ctx.saved_tensors
+        hand, scene, params, r_dil, obj_of_cand = ctx.args
+        _, grad = api.loss_and_grad(hand, scene, qd, params, r_dil, obj_of_cand=obj_of_cand, want_grad=True)
         return g_loss[:, None] * grad, None, None, None, None, None
 
 

@@ -4,6 +4,7 @@
 #include <cmath>
 #include <cstdio>
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <new>
 #include <string>
@@ -59,6 +60,18 @@ static fg_status invalid(const std::string& msg) {
   return FG_ERR_INVALID;
 }
 
+// Allocation-failure injection for tests: -1 disarmed, else the number of
+// allocation points still to pass before one fails.
+static std::atomic<long long> g_alloc_countdown{-1};
+
+bool alloc_fault() {
+  long long v = g_alloc_countdown.load();
+  while (v >= 0) {
+    if (g_alloc_countdown.compare_exchange_weak(v, v - 1)) return v == 0;
+  }
+  return false;
+}
+
 static fg_status check_params(const fg_params* p) {
   if (!p) return invalid("params is NULL");
   if (!(p->dt > 0.0f) || !std::isfinite(p->dt)) return invalid("params.dt must be > 0");
@@ -101,6 +114,12 @@ const char* fg_status_string(fg_status s) {
     case FG_ERR_NOT_FOUND: return "FG_ERR_NOT_FOUND";
   }
   return "FG_ERR_UNKNOWN";
+}
+
+fg_status fg_test_fail_allocation(int after) {
+  if (after < -1) return invalid("fg_test_fail_allocation: after must be >= -1");
+  g_alloc_countdown.store(after);
+  return FG_OK;
 }
 
 fg_status fg_last_error(char* buf, size_t n) {
@@ -235,6 +254,7 @@ fg_status fg_hand_create(const fg_hand_desc* d, fg_hand** out) {
   if (e == cudaSuccess) e = cudaMalloc(&h->chunk_link, sizeof(int) * nchunks);
   if (e == cudaSuccess) e = cudaMalloc(&h->units, sizeof(int4) * std::max<size_t>(units.size(), 1));
   if (e == cudaSuccess) e = cudaMalloc(&h->dev, sizeof(HandDev));
+  if (e == cudaSuccess && alloc_fault()) e = cudaErrorMemoryAllocation;
   if (e != cudaSuccess) return fail(e, "fg_hand_create: cudaMalloc");
   H.pts = h->pts;
   H.chunk_sphere = h->chunk_sphere;
@@ -287,7 +307,7 @@ fg_status fg_sdf_create(const float* grid, int nx, int ny, int nz, const float* 
   fg_sdf* s = new (std::nothrow) fg_sdf;
   if (!s) return FG_ERR_OOM;
   s->bytes = sizeof(float) * (size_t)nx * ny * nz;
-  cudaError_t e = cudaMalloc(&s->grid, s->bytes);
+  cudaError_t e = alloc_fault() ? cudaErrorMemoryAllocation : cudaMalloc(&s->grid, s->bytes);
   if (e != cudaSuccess) {
     delete s;
     return cuda_status(e, "fg_sdf_create: cudaMalloc");
@@ -396,14 +416,18 @@ fg_status fg_sdf_query(const fg_sdf* s, const float* pts, int n, float r, float*
   return cuda_status(launch_sdf_query(s->host, pts, n, r, phi, grad, (cudaStream_t)stream), "fg_sdf_query");
 }
 
-static fg_status check_common(const char* fn, const fg_hand* h, const fg_scene* sc, int B, const fg_params* p) {
+}  // extern "C"
+
+namespace fg {
+
+fg_status check_common(const char* fn, const fg_hand* h, const fg_scene* sc, int B, const fg_params* p) {
   if (!h || !sc) return invalid(std::string(fn) + ": NULL hand or scene");
   if (B < 0) return invalid(std::string(fn) + ": B < 0");
   return check_params(p);
 }
 
 // Entry points that implement the one-step metric only.
-static fg_status check_one_step(const char* fn, const fg_params* p) {
+fg_status check_one_step(const char* fn, const fg_params* p) {
   if (p->sim_steps != 0)
     return invalid(std::string(fn) + ": params.sim_steps must be 0 here (T-step metric: fg_loss_and_grad, "
                    "fg_optimize_step)");
@@ -412,6 +436,10 @@ static fg_status check_one_step(const char* fn, const fg_params* p) {
                    "fg_optimize_step)");
   return FG_OK;
 }
+
+}  // namespace fg
+
+extern "C" {
 
 // The Gauss-Seidel form: hands whose chunks fit the kernel's tables.
 static fg_status check_gs(const char* fn, const fg_hand* h, const fg_scene* sc) {
@@ -519,6 +547,27 @@ fg_status fg_optimize_step(const fg_hand* h, const fg_scene* sc, const int* oc, 
                        "fg_optimize_step (Gauss-Seidel)");
   }
   return cuda_status(launch_fused(kModeOptimize, a, h, (cudaStream_t)stream), "fg_optimize_step");
+}
+
+fg_status fg_optimize_step_host(const fg_hand* h, const fg_scene* sc, const int* oc, const float* host_q_in,
+                                float* q, int B, const fg_params* p, int step, int total_steps, int nsteps,
+                                float* loss, float* host_q_out, float* host_loss, void* stream) {
+  if (B > 0 && (!host_q_in || !q || !host_q_out)) return invalid("fg_optimize_step_host: NULL buffer");
+  if (B > 0 && !h) return invalid("fg_optimize_step_host: NULL hand");
+  if (host_loss && !loss) return invalid("fg_optimize_step_host: host_loss needs the device loss buffer");
+  fg_status st = check_common("fg_optimize_step_host", h, sc, B, p);
+  if (st != FG_OK) return st;
+  if (B == 0) return FG_OK;
+  const size_t qbytes = sizeof(float) * (size_t)B * h->host.D;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaMemcpyAsync(q, host_q_in, qbytes, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_status(e, "fg_optimize_step_host (host to device)");
+  st = fg_optimize_step(h, sc, oc, q, B, p, step, total_steps, nsteps, loss, stream);
+  if (st != FG_OK) return st;
+  e = cudaMemcpyAsync(host_q_out, q, qbytes, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess && host_loss)
+    e = cudaMemcpyAsync(host_loss, loss, sizeof(float) * (size_t)B, cudaMemcpyDeviceToHost, s);
+  return cuda_status(e, "fg_optimize_step_host (device to host)");
 }
 
 fg_status fg_contact_measure(const fg_hand* h, const fg_scene* sc, const int* oc, const float* q, int B,

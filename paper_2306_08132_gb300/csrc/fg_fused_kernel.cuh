@@ -687,7 +687,7 @@ cudaError_t launch_fused_cfg(const FusedArgs& a, cudaStream_t st) {
   if (grid > a.B) grid = a.B;
   if (grid < 1) return cudaSuccess;
   FusedArgs b = a;
-  cudaError_t e = work_pair(&b.work);
+  cudaError_t e = work_pair(&b.work, st);
   if (e != cudaSuccess) return e;
   fused_step_kernel<MODE, NW, MINB, PPT, ANY><<<(int)grid, NW * 32, 0, st>>>(b);
   return cudaGetLastError();

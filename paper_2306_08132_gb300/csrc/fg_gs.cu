@@ -458,18 +458,40 @@ __global__ void __launch_bounds__(kGW * 32, 3) gs_kernel(FusedArgs a) {
         int cnt = 0;
         // |x~ + dx| and |dth| of the current state (recomputed when a projection changes it)
         float ex = sqrtf(xt[0] * xt[0] + xt[1] * xt[1] + xt[2] * xt[2]), en = 0.0f;
-        for (int j = 0; j < nch; ++j) {
-          float* sn = snap(dyn, j, m);
+        // The chunks are visited in windows of 32: lane l tests chunk j + l at the
+        // current state, and the chunks before the first one that can hold a contact
+        // get their snapshot (the current state, no events) in parallel.  The state
+        // changes only at projections, so every chunk is tested at the same state
+        // as in a walk that visits the chunks one by one.
+        int j = 0;
+        while (j < nch) {
+          const int jj = j + lane;
+          bool open_ = false;
+          if (jj < nch) {
+            // largest |n . D| over the chunk: |x~ + dx| + |dth| (|c - x~| + R)
+            const float bound = fmaf(en, S.reach[jj][m], ex);
+            const float lbj = S.lb[jj];
+            open_ = !(lbj - bound * (1.0f + 1e-5f) - (1e-6f + 1e-5f * fabsf(lbj)) > 0.0f);
+          }
+          const unsigned ob = __ballot_sync(kFull, open_);
+          const int jn = ob ? j + __ffs(ob) - 1 : min(j + 32, nch);
+          if (jj < jn) {                                  // culled chunks: state, no events
+            float* sc = snap(dyn, jj, m);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) sc[k] = st[k];
+            sc[12] = __uint_as_float(0u);
+          }
+          if (!ob) {
+            j = jn;
+            continue;
+          }
+          float* sn = snap(dyn, jn, m);
           if (lane < 6) sn[lane] = pick6(st, lane);
-          // largest |n . D| over the chunk: |x~ + dx| + |dth| (|c - x~| + R)
-          const float bound = fmaf(en, S.reach[j][m], ex);
-          const float lbj = S.lb[j];
           unsigned mask = 0u;
-          const bool culled = lbj - bound * (1.0f + 1e-5f) - (1e-6f + 1e-5f * fabsf(lbj)) > 0.0f;
-          if (!culled) {
-            const int i = 32 * j + lane;
+          {
+            const int i = 32 * jn + lane;
             const bool valid = i < P;
-            const float4 sp = __ldg(H.pts + (valid ? i : 32 * j));
+            const float4 sp = __ldg(H.pts + (valid ? i : 32 * jn));
             float p[3];
             world_point(S.frame4[(int)sp.w], sp, p);
             SdfSample smp;
@@ -505,6 +527,7 @@ __global__ void __launch_bounds__(kGW * 32, 3) gs_kernel(FusedArgs a) {
             ex = sqrtf(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
             en = sqrtf(st[3] * st[3] + st[4] * st[4] + st[5] * st[5]);
           }
+          j = jn + 1;
         }
 #pragma unroll
         for (int k = 0; k < 6; ++k) {
@@ -601,13 +624,30 @@ __global__ void __launch_bounds__(kGW * 32, 3) gs_kernel(FusedArgs a) {
         float av[6];
 #pragma unroll
         for (int k = 0; k < 6; ++k) av[k] = S.afin[m][k];
-        for (int j = nch - 1; j >= 0; --j) {
-          float* sn = snap(dyn, j, m);
+        // Windows of 32 chunks from the end: lane l reads the event mask of chunk
+        // j - l; the chunks after the last one with events get the adjoint (unchanged
+        // across them) in parallel, then that chunk is reversed.
+        int j = nch - 1;
+        while (j >= 0) {
+          const int jj = j - lane;
+          const bool ev = jj >= 0 && __float_as_uint(snap(dyn, jj, m)[12]) != 0u;
+          const unsigned eb = __ballot_sync(kFull, ev);
+          const int je = eb ? j - (__ffs(eb) - 1) : max(j - 32, -1);
+          if (jj > je && jj >= 0) {                      // chunks without events: the adjoint passes through
+            float* sc = snap(dyn, jj, m);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) sc[6 + k] = av[k];
+          }
+          if (!eb) {
+            j = je;
+            continue;
+          }
+          float* sn = snap(dyn, je, m);
           const unsigned mask = __float_as_uint(sn[12]);
-          if (mask) {
-            const int i = 32 * j + lane;
+          {
+            const int i = 32 * je + lane;
             const bool valid = i < P;
-            const float4 sp = __ldg(H.pts + (valid ? i : 32 * j));
+            const float4 sp = __ldg(H.pts + (valid ? i : 32 * je));
             const int link = (int)sp.w;
             float p[3];
             world_point(S.frame4[link], sp, p);
@@ -635,6 +675,7 @@ __global__ void __launch_bounds__(kGW * 32, 3) gs_kernel(FusedArgs a) {
             link_accumulate(S.lacc[warp], lane, link, valid, v, cur, acc);
           }
           if (lane < 6) sn[6 + lane] = pick6(av, lane);
+          j = je - 1;
         }
       }
       __syncthreads();
@@ -777,7 +818,7 @@ cudaError_t launch_gs_mode(const FusedArgs& a, int nchunks, cudaStream_t st) {
   if (grid > a.B) grid = a.B;
   if (grid < 1) return cudaSuccess;
   FusedArgs b = a;
-  e = work_pair(&b.work);
+  e = work_pair(&b.work, st);
   if (e != cudaSuccess) return e;
   gs_kernel<MODE, ANY><<<(int)grid, kGW * 32, dyn, st>>>(b);
   return cudaGetLastError();

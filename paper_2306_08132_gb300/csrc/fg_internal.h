@@ -37,6 +37,13 @@ namespace fg {
 
 void set_error(const std::string& msg);
 fg_status cuda_status(cudaError_t e, const char* what);
+// Argument checks shared by the entry points: handles, B >= 0 and the parameters;
+// the one-step metric only (sim_steps = 0, gauss_seidel = 0).
+fg_status check_common(const char* fn, const fg_hand* h, const fg_scene* sc, int B, const fg_params* p);
+fg_status check_one_step(const char* fn, const fg_params* p);
+// True when the allocation-failure injection (fg_test_fail_allocation) makes this
+// allocation point fail.
+bool alloc_fault();
 ParamsDev params_from(const fg_params* p);
 int device_sm_count();
 size_t min_pyramid_floats(int nx, int ny, int nz, int* levels);

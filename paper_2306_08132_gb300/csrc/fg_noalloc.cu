@@ -58,18 +58,12 @@ using namespace fg;
 extern "C" fg_status fg_optimize_step_plain_noalloc(const fg_hand* h, const fg_scene* sc, const int* oc, float* q,
                                                     int B, const fg_params* p, int step, int total_steps, int nsteps,
                                                     float* loss, void* stream) {
-  if (!h || !sc || !p) {
-    set_error("fg_optimize_step_plain_noalloc: NULL hand, scene or params");
-    return FG_ERR_INVALID;
-  }
-  if (B < 0 || nsteps < 1 || step < 0 || total_steps < 1) {
-    set_error("fg_optimize_step_plain_noalloc: need B >= 0, nsteps >= 1, step >= 0, total_steps >= 1");
-    return FG_ERR_INVALID;
-  }
-  if (!(p->dt > 0.0f) || !std::isfinite(p->dt) || !(p->v_test >= 0.0f) || !(p->mu >= 0.0f) ||
-      !(p->alpha_leak >= 0.0f && p->alpha_leak <= 1.0f) || !(p->r0 >= 0.0f) || !std::isfinite(p->lr) ||
-      (p->schedule != 0 && p->schedule != 1) || p->sim_steps != 0 || p->gauss_seidel != 0) {
-    set_error("fg_optimize_step_plain_noalloc: invalid params (sim_steps and gauss_seidel must be 0)");
+  // the same checks as the workspace form, fg_optimize_step_plain
+  fg_status st = check_common("fg_optimize_step_plain_noalloc", h, sc, B, p);
+  if (st == FG_OK) st = check_one_step("fg_optimize_step_plain_noalloc", p);
+  if (st != FG_OK) return st;
+  if (nsteps < 1 || step < 0 || total_steps < 1) {
+    set_error("fg_optimize_step_plain_noalloc: need nsteps >= 1, step >= 0, total_steps >= 1");
     return FG_ERR_INVALID;
   }
   if (sc->has_mesh) {

@@ -253,7 +253,7 @@ cudaError_t grid_for_kernel(Kern k, size_t dyn, int B, int* grid) {
 cudaError_t launch_contact_measure(const FusedArgs& a0, const float* weights, float tau, float* out, cudaStream_t st) {
   if (a0.B <= 0) return cudaSuccess;
   FusedArgs a = a0;
-  cudaError_t ew = work_pair(&a.work);
+  cudaError_t ew = work_pair(&a.work, st);
   if (ew != cudaSuccess) return ew;
   int grid = 0;
   if (a.any_mesh) {
@@ -274,7 +274,7 @@ cudaError_t launch_grasp_epsilon(const FusedArgs& a0, float tau, float mu, int k
                                  const float* dirs, int K, float* eps, int* ncontact, cudaStream_t st) {
   if (a0.B <= 0) return cudaSuccess;
   FusedArgs a = a0;
-  cudaError_t ew = work_pair(&a.work);
+  cudaError_t ew = work_pair(&a.work, st);
   if (ew != cudaSuccess) return ew;
   const size_t dyn = epsilon_smem_bytes(K);
   static size_t attr_set[2][64] = {{0}, {0}};

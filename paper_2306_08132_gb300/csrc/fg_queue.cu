@@ -66,8 +66,10 @@ struct fg_queue {
   uint64_t next_id = 1;
   uint64_t rounds = 0, cand_steps = 0;
   bool stop = false;
+  bool joined = false;                // fg_queue_destroy has stopped the scheduler
   bool broken = false;                // a round failed or timed out: no further rounds
   std::string broken_msg;
+  std::vector<float*> orphans;        // device state of the requests of a failed round
   cudaStream_t stream = nullptr;
   cudaEvent_t event = nullptr;
   fg::QueueSlotDev* h_slots = nullptr;   // pinned
@@ -107,6 +109,7 @@ void admit(fg_queue* Q) {
     Q->pending.pop_front();
     cudaError_t e = cudaMallocAsync(&r->d_q, sizeof(float) * (size_t)r->B * r->D, Q->stream);
     if (e == cudaSuccess) e = cudaMallocAsync(&r->d_loss, sizeof(float) * (size_t)r->B, Q->stream);
+    if (e == cudaSuccess && fg::alloc_fault()) e = cudaErrorMemoryAllocation;
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(r->d_q, r->q0.data(), sizeof(float) * (size_t)r->B * r->D, cudaMemcpyHostToDevice,
                           Q->stream);
@@ -185,8 +188,13 @@ void scheduler(fg_queue* Q) {
       // the round did not finish: its requests fail and the queue takes no more work
       Q->broken = true;
       Q->broken_msg = !in_time ? "a round exceeded timeout_ms" : std::string(cudaGetErrorString(e));
-      for (Request* r : Q->active)
+      for (Request* r : Q->active) {
         fail_request(Q, r, !in_time ? FG_ERR_TIMEOUT : FG_ERR_CUDA, Q->broken_msg);
+        // the round may still be running on them: freed by fg_queue_destroy once the stream drains
+        Q->orphans.push_back(r->d_q);
+        Q->orphans.push_back(r->d_loss);
+        r->d_q = r->d_loss = nullptr;
+      }
       Q->active.clear();
       for (Request* r : Q->pending) fail_request(Q, r, FG_ERR_CUDA, "queue stopped: " + Q->broken_msg);
       Q->pending.clear();
@@ -293,8 +301,11 @@ fg_status fg_queue_submit(fg_queue* Q, const fg_request* r, uint64_t* id) {
                   " bytes, more than the queue's budget of " + std::to_string(Q->budget));
     return FG_ERR_BUDGET;
   }
-  Request* req = new (std::nothrow) Request;
-  if (!req) return FG_ERR_OOM;
+  Request* req = fg::alloc_fault() ? nullptr : new (std::nothrow) Request;
+  if (!req) {
+    fg::set_error("fg_queue_submit: out of host memory");
+    return FG_ERR_OOM;
+  }
   req->hand = r->hand;
   req->sdf = r->sdf;
   req->B = r->B;
@@ -403,15 +414,31 @@ fg_status fg_queue_stats(fg_queue* Q, fg_queue_stat* out) {
 
 fg_status fg_queue_destroy(fg_queue* Q) {
   if (!Q) return FG_OK;
-  {
-    std::lock_guard<std::mutex> lock(Q->mu);
-    Q->stop = true;
-    // requests still waiting are dropped; the scheduler finishes the round in flight
-    for (Request* r : Q->pending) fail_request(Q, r, FG_ERR_CUDA, "queue destroyed");
-    Q->pending.clear();
-    Q->cv.notify_all();
+  if (!Q->joined) {
+    {
+      std::lock_guard<std::mutex> lock(Q->mu);
+      Q->stop = true;
+      // requests still waiting are dropped; the scheduler finishes the round in flight
+      for (Request* r : Q->pending) fail_request(Q, r, FG_ERR_CUDA, "queue destroyed");
+      Q->pending.clear();
+      Q->cv.notify_all();
+    }
+    if (Q->worker.joinable()) Q->worker.join();
+    Q->joined = true;
   }
-  if (Q->worker.joinable()) Q->worker.join();
+  // a round that exceeded timeout_ms may still run: wait for the stream, again at most timeout_ms
+  const auto t0 = Clock::now();
+  cudaError_t e;
+  while ((e = cudaStreamQuery(Q->stream)) == cudaErrorNotReady) {
+    if (Clock::now() - t0 > std::chrono::milliseconds(Q->opts.timeout_ms)) {
+      fg::set_error("fg_queue_destroy: the queue's stream did not drain within timeout_ms; the handle stays "
+                    "valid, call fg_queue_destroy again");
+      return FG_ERR_TIMEOUT;
+    }
+    std::this_thread::sleep_for(std::chrono::microseconds(200));
+  }
+  for (float* p : Q->orphans) cudaFreeAsync(p, Q->stream);
+  Q->orphans.clear();
   cudaStreamSynchronize(Q->stream);
   for (auto& kv : Q->all) delete kv.second;
   Q->all.clear();

@@ -771,7 +771,7 @@ cudaError_t launch_tstep_mode(const FusedArgs& a, cudaStream_t st) {
   if (grid > a.B) grid = a.B;
   if (grid < 1) return cudaSuccess;
   FusedArgs b = a;
-  cudaError_t e = work_pair(&b.work);
+  cudaError_t e = work_pair(&b.work, st);
   if (e != cudaSuccess) return e;
   tstep_kernel<MODE, ANY><<<(int)grid, kTW * 32, 0, st>>>(b);
   return cudaGetLastError();

@@ -6,8 +6,12 @@
 // (the next candidate; the number of CTAs that found none left).  Each launch draws
 // its own pair from a pool of this translation unit, and the last CTA to finish sets
 // both words back to zero, so the pair is clean for the next launch that draws it.
-// A launch captured in a graph keeps its pair on every replay: one graph must not
-// be replayed on two streams at once.
+// Eager launches cycle through the first kWorkSlots pairs.  A launch captured in a
+// graph keeps its pair on every replay, so captured launches draw from a separate
+// range of kCapturedSlots pairs that eager launches never use: a graph's replays
+// never share a counter with eager launches, nor with another graph unless
+// kCapturedSlots launches were captured in between.  One graph must not be
+// replayed on two streams at once.
 #pragma once
 
 #include <atomic>
@@ -17,11 +21,13 @@
 namespace fg {
 
 constexpr int kWorkSlots = 1024;
-static __device__ unsigned g_work_pool[kWorkSlots][2];
+constexpr int kCapturedSlots = 16384;
+static __device__ unsigned g_work_pool[kWorkSlots + kCapturedSlots][2];
 static std::atomic<unsigned> g_work_seq{0};
+static std::atomic<unsigned> g_captured_seq{0};
 
-// Host: the counter pair of one launch on the current device.
-static inline cudaError_t work_pair(unsigned** out) {
+// Host: the counter pair of one launch on `stream` on the current device.
+static inline cudaError_t work_pair(unsigned** out, cudaStream_t stream) {
   static unsigned* pool[64] = {nullptr};
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -33,7 +39,13 @@ static inline cudaError_t work_pair(unsigned** out) {
     if (e != cudaSuccess) return e;
     p = static_cast<unsigned*>(q);
   }
-  *out = p + 2 * (g_work_seq.fetch_add(1u) % kWorkSlots);
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  e = cudaStreamIsCapturing(stream, &cap);
+  if (e != cudaSuccess) return e;
+  if (cap == cudaStreamCaptureStatusActive)
+    *out = p + 2 * (kWorkSlots + g_captured_seq.fetch_add(1u) % kCapturedSlots);
+  else
+    *out = p + 2 * (g_work_seq.fetch_add(1u) % kWorkSlots);
   return cudaSuccess;
 }
 

@@ -156,14 +156,28 @@ def polyhedron_grid(points: np.ndarray, n: int, device="cpu", shift=DEFAULT_SHIF
     return _pack("polyhedron", g, origin, pitch, rb, {"n_faces": int(F), "points": np.asarray(points).tolist()})
 
 
-def random_superquadric(rng: np.random.Generator, n: int, device="cpu"):
+def lazy_object(kind: str, bound_radius: float, make) -> dict:
+    """An object whose grid is not built yet: ``realize`` builds it with make(device).
+    The bound radius (all the candidate generator needs) is known from the draws."""
+    return {"kind": kind, "lazy": make, "bound_radius": float(bound_radius)}
+
+
+def realize(obj: dict, device="cpu") -> dict:
+    """The built object (obj itself when it is not lazy)."""
+    return obj["lazy"](device) if "lazy" in obj else obj
+
+
+def random_superquadric(rng: np.random.Generator, n: int, device="cpu", build: bool = True):
     eps1, eps2 = rng.uniform(0.3, 2.0, size=2)
     semi = rng.uniform(0.02, 0.08, size=3)
     shift = rng.uniform(-0.5, 0.5, size=3)
-    return superquadric_grid(semi, float(eps1), float(eps2), n, device=device, shift=shift)
+
+    def make(dev):
+        return superquadric_grid(semi, float(eps1), float(eps2), n, device=dev, shift=shift)
+    return make(device) if build else lazy_object("superquadric", float(max(semi)), make)
 
 
-def random_polyhedron(rng: np.random.Generator, n: int, device="cpu", n_pts=None):
+def random_polyhedron(rng: np.random.Generator, n: int, device="cpu", n_pts=None, build: bool = True):
     """Hull of k ~ U{8..22} points on an ellipsoid (semi-axes U(2, 8) cm): all points
     are extreme, so the hull has 2k - 4 triangular faces (12..40)."""
     k = int(rng.integers(8, 23)) if n_pts is None else int(n_pts)
@@ -171,4 +185,8 @@ def random_polyhedron(rng: np.random.Generator, n: int, device="cpu", n_pts=None
     d = rng.normal(size=(k, 3))
     d /= np.linalg.norm(d, axis=1, keepdims=True)
     shift = rng.uniform(-0.5, 0.5, size=3)
-    return polyhedron_grid(d * semi, n, device=device, shift=shift)
+    pts = d * semi
+
+    def make(dev):
+        return polyhedron_grid(pts, n, device=dev, shift=shift)
+    return make(device) if build else lazy_object("polyhedron", float(np.linalg.norm(pts, axis=1).max()), make)

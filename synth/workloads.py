@@ -78,38 +78,41 @@ def tiny_sphere_workload(n_cand: int = 16, steps: int = 100, device="cpu") -> Wo
 
 def batched_superquadric_workload(n_obj: int = 8, per_obj: int = 1024, grid_n: int = 128,
                                   points_per_link: int = 256, steps: int = 500,
-                                  device="cpu") -> Workload:
+                                  device="cpu", build: bool = True) -> Workload:
     """Random superquadrics (exponents U(0.3, 2), semi-axes U(2, 8) cm) on grid_n^3
     grids, 4-finger hand (17 links x points_per_link), per_obj candidates per object
-    with the palm at R_b + 6 cm, dilation 10 mm -> 0 over the run."""
+    with the palm at R_b + 6 cm, dilation 10 mm -> 0 over the run.  build=False leaves
+    the grids unbuilt (``synth.realize`` builds one on demand)."""
     rng = np.random.default_rng(SEED_BASE + 2)
     hand = make_hand(4, points_per_link)
-    objs = [random_superquadric(rng, grid_n, device=device) for _ in range(n_obj)]
+    objs = [random_superquadric(rng, grid_n, device=device, build=build) for _ in range(n_obj)]
     q0, oc = _cands_for_objects(rng, hand, objs, per_obj, lambda ob: ob["bound_radius"] + 0.06)
     return Workload("superquadric%d_%d^3_hand4_B%d" % (n_obj, grid_n, n_obj * per_obj), hand, objs,
                     q0, oc, default_params(r0=0.010, schedule="linear"), steps)
 
 
 def polyhedra_workload(n_obj: int = 32, per_obj: int = 4096, grid_n: int = 128,
-                       points_per_link: int = 256, steps: int = 100, device="cpu") -> Workload:
-    """Convex polyhedra (12-40 faces) on grid_n^3 grids, 5-finger hand (23 links)."""
+                       points_per_link: int = 256, steps: int = 100, device="cpu", build: bool = True) -> Workload:
+    """Convex polyhedra (12-40 faces) on grid_n^3 grids, 5-finger hand (23 links).
+    build=False leaves the grids unbuilt (``synth.realize`` builds one on demand)."""
     rng = np.random.default_rng(SEED_BASE + 3)
     hand = make_hand(5, points_per_link)
-    objs = [random_polyhedron(rng, grid_n, device=device) for _ in range(n_obj)]
+    objs = [random_polyhedron(rng, grid_n, device=device, build=build) for _ in range(n_obj)]
     q0, oc = _cands_for_objects(rng, hand, objs, per_obj, lambda ob: ob["bound_radius"] + 0.06)
     return Workload("polyhedra%d_%d^3_hand5_B%d" % (n_obj, grid_n, n_obj * per_obj), hand, objs,
                     q0, oc, default_params(r0=0.010, schedule="linear"), steps)
 
 
 def sweep_workload(n_obj: int = 256, total_cand: int = 65536, grid_n: int = 192,
-                   points_per_link: int = 256, steps: int = 1000, device="cpu") -> Workload:
-    """Half superquadrics, half polyhedra on grid_n^3 grids, 5-finger hand."""
+                   points_per_link: int = 256, steps: int = 1000, device="cpu", build: bool = True) -> Workload:
+    """Half superquadrics, half polyhedra on grid_n^3 grids, 5-finger hand.
+    build=False leaves the grids unbuilt (``synth.realize`` builds one on demand)."""
     rng = np.random.default_rng(SEED_BASE + 5)
     hand = make_hand(5, points_per_link)
     objs = []
     for k in range(n_obj):
-        objs.append(random_superquadric(rng, grid_n, device=device) if k % 2 == 0
-                    else random_polyhedron(rng, grid_n, device=device))
+        objs.append(random_superquadric(rng, grid_n, device=device, build=build) if k % 2 == 0
+                    else random_polyhedron(rng, grid_n, device=device, build=build))
     per_obj = total_cand // n_obj
     q0, oc = _cands_for_objects(rng, hand, objs, per_obj, lambda ob: ob["bound_radius"] + 0.06)
     return Workload("sweep%d_%d^3_hand5_B%d" % (n_obj, grid_n, per_obj * n_obj), hand, objs,

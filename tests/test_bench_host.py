@@ -116,3 +116,72 @@ def test_reference_arm_line():
     out1 = subprocess.run(cmd, capture_output=True, text=True, timeout=120, cwd=root,
                           env=dict(env, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1"))
     assert out1.returncode == 0 and out1.stdout.strip() == ""
+
+
+def test_roofline_takes_the_slower_of_alu_and_hbm_time():
+    """bench.roofline_of: the ALU time (the oracle's flop count at the measured FP32
+    peak) against the DRAM time (the launch's measured traffic at the HBM bandwidth);
+    the slower bounds the launch, and frac is measured against that bound's peak.  The
+    three fractions of the ALU peak differ only by their flop basis."""
+    import bench
+    w = types.SimpleNamespace(B=1000, hand={"P": 100})
+    peak = {"tflops": 50.0, "basis": "test", "sms": 10, "clocks": {"sm_mhz": 2000.0}}
+    units = 1000 * 100
+    flops = bench.FLOPS_PER_POINT_STEP * units
+    kern_ms = 1000.0 * flops / 25e12                   # half the ALU peak
+    prof = {"traffic": 1e6, "executed_fp32_flops_per_point_step": 500.0}
+    r = bench.roofline_of(w, 1, kern_ms, peak, 1000.0, "test", prof)
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert np.isclose(r["frac"], 0.5) and np.isclose(r["achieved"], 25.0) and r["peak"] == 50.0
+    f = r["fractions"]
+    assert np.isclose(f["oracle_count"]["frac"], 0.5)
+    assert np.isclose(f["kernel_minimal"]["frac"], 0.5 * bench.KERNEL_MIN_FLOPS_PER_POINT_STEP / bench.FLOPS_PER_POINT_STEP)
+    assert np.isclose(f["executed_fp32"]["frac"], 0.5 * 500.0 / bench.FLOPS_PER_POINT_STEP)
+    assert np.isclose(r["alu_peak_derived_tflops"], 10 * 128 * 2 * 2000e6 / 1e12)
+    # the same launch moving 1e12 bytes at 1,000 GB/s takes 1 s: DRAM-bound
+    r = bench.roofline_of(w, 1, 1000.0, peak, 1000.0, "test", {"traffic": 1e12})
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and np.isclose(r["frac"], 1.0)
+    assert r["fractions"]["executed_fp32"] is None
+    # without a traffic record the ALU bounds it
+    assert bench.roofline_of(w, 1, kern_ms, peak, 1000.0, "test", None)["bound"] == "alu"
+
+
+def test_profile_records_are_keyed_by_kernel_workload_and_sources(tmp_path, monkeypatch):
+    """bench.load_profile returns a kernel's DRAM traffic only for the workload it was
+    captured on and only while the kernel's sources hash to the recorded value."""
+    import bench
+    from paper_2306_08132_gb300.build import source_hash, FUSED_SOURCES
+    cur = source_hash(FUSED_SOURCES)
+    (tmp_path / "profiles").mkdir()
+    (tmp_path / "profiles" / "traffic.txt").write_text(
+        "# kernel workload hash bytes flops\n"
+        "fused_step wl_a %s 123 456\nfused_step wl_b deadbeef0000 789 -\nfused_step wl_c %s 5 -\n" % (cur, cur))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.load_profile("fused_step", "wl_a") == {"traffic": 123.0, "source_hash": cur,
+                                                        "executed_fp32_flops_per_point_step": 456.0}
+    assert bench.load_profile("fused_step", "wl_b") is None          # stale sources
+    assert bench.load_profile("fused_step", "wl_c") == {"traffic": 5.0, "source_hash": cur}
+    assert bench.load_profile("fused_step", "wl_d") is None          # another workload
+    assert bench.load_profile("gs_step", "wl_a") is None
+
+
+def test_workload_partition_by_object():
+    """bench.build_workload: rank k of N builds only the grids of its block of objects
+    and keeps exactly their candidates; the blocks cover the workload."""
+    import bench
+    sizes = dict(n_obj=5, per_obj=2, grid_n=10, points_per_link=8)
+    full, info = bench.build_workload("cpu", 0, 1, "superquadric8", **sizes)
+    seen = []
+    total = 0
+    for r in range(3):
+        w, part = bench.build_workload("cpu", r, 3, "superquadric8", **sizes)
+        assert len(w.objects) == len(part["objects"]) and part["total_candidates"] == full.B
+        np.testing.assert_array_equal(w.q0, full.q0[part["candidates"]])
+        np.testing.assert_array_equal(part["objects"][w.obj_of_cand], full.obj_of_cand[part["candidates"]])
+        for k, o in zip(part["objects"], w.objects):
+            assert torch.equal(o["grid"], full.objects[k]["grid"])
+        seen += part["candidates"].tolist()
+        total += part["grid_bytes"]
+    assert sorted(seen) == list(range(full.B)) and total == info["grid_bytes"]
+    lazy, _ = bench.build_workload("cpu", 0, 1, "sweep256", lazy=True)
+    assert lazy.B == 65536 and not any("grid" in o for o in lazy.objects)

@@ -135,3 +135,47 @@ def test_quality_kernels_repeat(fg, case):
         assert torch.equal(ca, ca0)
         assert torch.equal(n, n0)
         assert torch.equal(torch.nan_to_num(e, nan=math.inf), torch.nan_to_num(e0, nan=math.inf))
+
+
+def test_graph_replays_beside_more_eager_launches_than_the_pool(fg, case):
+    """A captured launch keeps its counter on every replay; eager launches cycle
+    through the pool.  Captured launches draw from a range that eager launches never
+    use, so a graph replayed on one stream while 1,100 eager launches (more than the
+    pool's 1,024 counters) run on another stream still computes every candidate of
+    both, bit for bit as serial calls do."""
+    w, hand, _, scene, q0, oc = case
+    qa, oa = q0[:64].contiguous(), oc[:64].contiguous()
+    qb, ob = q0[90:95].contiguous(), oc[90:95].contiguous()
+    ref_a = fg.loss_and_grad(hand, scene, qa, w.params, 0.004, obj_of_cand=oa)
+    ref_b = fg.loss_and_grad(hand, scene, qb, w.params, 0.004, obj_of_cand=ob)
+    torch.cuda.synchronize()
+    la = torch.empty(64, device="cuda")
+    ga = torch.empty_like(qa)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    s1.wait_stream(torch.cuda.current_stream())
+    s2.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s1):
+        l, g_ = fg.loss_and_grad(hand, scene, qa, w.params, 0.004, obj_of_cand=oa)    # warm before capture
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s1):
+        l, g_ = fg.loss_and_grad(hand, scene, qa, w.params, 0.004, obj_of_cand=oa)
+        la.copy_(l)
+        ga.copy_(g_)
+    torch.cuda.synchronize()
+    outs_a, outs_b = [], []
+    for i in range(1100):
+        with torch.cuda.stream(s2):
+            outs_b.append(fg.loss_and_grad(hand, scene, qb, w.params, 0.004, obj_of_cand=ob))
+        if i % 25 == 0:
+            with torch.cuda.stream(s1):
+                la.fill_(NAN)
+                ga.fill_(NAN)
+                graph.replay()
+                outs_a.append((la.clone(), ga.clone()))
+    torch.cuda.synchronize()
+    assert len(outs_a) == 44
+    for l_, g_ in outs_a:
+        assert torch.equal(l_, ref_a[0]) and torch.equal(g_, ref_a[1])
+    for l_, g_ in outs_b:
+        assert torch.equal(l_, ref_b[0]) and torch.equal(g_, ref_b[1])

@@ -39,6 +39,9 @@ MESHES = {
     "icosphere": (SM.icosphere(0.04, 3), MS.PHONG_ALPHA),
     "superquadric": (SM.superquadric_mesh((0.05, 0.03, 0.04), 0.7, 1.3, 20, 40), MS.PHONG_ALPHA),
     "hull": (SM.hull_mesh(np.random.default_rng(7).normal(size=(40, 3)) * 0.04), MS.PHONG_ALPHA),
+    # non-convex, genus 1: saddle-shaped inner half, concave edges and vertices
+    "torus_smooth": (SM.torus_mesh(0.04, 0.015, 24, 12), MS.PHONG_ALPHA),
+    "torus_coarse": (SM.torus_mesh(0.04, 0.015, 6, 3), MS.PHONG_ALPHA),
 }
 
 
@@ -72,6 +75,75 @@ def test_mesh_query_matches_oracle(fg, name):
         gerr = np.abs(g.cpu().numpy().T.astype(np.float64) - grad).max(axis=1)[clean]
         assert (gerr < 5e-4 + 2e-8 / d[clean]).all(), (name, n, gerr.max())
         assert np.median(gerr) < 1e-5
+
+
+def _torus_points(m, rng, n=600):
+    """Points that probe a torus's sign: the bounding box (the hole included), within
+    0.2-3 mm of the smooth torus on both sides, and around the mesh's vertices and
+    edges (where the sharp convex and concave features are)."""
+    R, r = 0.04, 0.015
+    V = m["vertices"].astype(np.float64)
+    F = np.asarray(m["faces"])
+    box = rng.uniform(-1.0, 1.0, size=(n, 3)) * np.array([R + 1.5 * r, R + 1.5 * r, 1.5 * r])
+    th, ph = rng.uniform(0, 2 * np.pi, size=(2, n))
+    nrm = np.stack([np.cos(ph) * np.cos(th), np.cos(ph) * np.sin(th), np.sin(ph)], -1)
+    srf = np.stack([(R + r * np.cos(ph)) * np.cos(th), (R + r * np.cos(ph)) * np.sin(th), r * np.sin(ph)], -1)
+    near = srf + nrm * (rng.choice([-1.0, 1.0], size=n) * rng.uniform(0.0002, 0.003, size=n))[:, None]
+    at_v = V[rng.integers(0, len(V), n)] + rng.normal(size=(n, 3)) * 0.003
+    e = rng.integers(0, len(F), n)
+    t = rng.uniform(size=(n, 1))
+    at_e = V[F[e, 0]] * t + V[F[e, 1]] * (1 - t) + rng.normal(size=(n, 3)) * 0.003
+    return np.concatenate([box, near, at_v, at_e])
+
+
+@pytest.mark.parametrize("n_major,n_minor", [(24, 12), (8, 4), (6, 3)])
+@pytest.mark.parametrize("alpha", [0.0, MS.PHONG_ALPHA])
+def test_torus_sign_and_value_match_oracle(fg, n_major, n_minor, alpha):
+    """Non-convex meshes on the GPU (Sec. III-B: inside or outside by the closest
+    feature, then the Phong point): tori whose inner half is saddle-shaped; the coarse
+    ones (tubes of 3 or 4 faces) have sharp concave edges and vertices, where the sign
+    needs the edge or vertex pseudonormal.  Against the oracle's brute-force query
+    (whose sign is pinned on these tori by the winding number): the sign exactly, the
+    value and gradient within the query tolerances, on points outside the guard band."""
+    m = SM.torus_mesh(0.04, 0.015, n_major, n_minor)
+    sdf = fg.Sdf.from_mesh(m["vertices"], m["faces"], m["mass"], m["inertia"], phong_alpha=alpha)
+    ref_mesh = MS.MeshObj.from_synth(m, alpha=alpha)
+    p32 = _torus_points(m, np.random.default_rng(n_major)).astype(np.float32)
+    phi, g = fg.sdf_query(sdf, torch.tensor(p32.T.copy(), device=_dev()), 0.0)
+    res = MS.mesh_query(ref_mesh, p32.astype(np.float64))
+    diff = p32.astype(np.float64) - res["q_rho"]
+    d = np.linalg.norm(diff, axis=1)
+    clean = (res["gap"] > 1e-6) & (res["dist"] > 1e-6) & (d > 1e-6)
+    assert clean.sum() >= 0.9 * len(p32)
+    got = phi.cpu().numpy().astype(np.float64)
+    inside = res["sign"] < 0
+    assert inside[clean].sum() > 300 and (~inside[clean]).sum() > 300
+    assert np.array_equal((got < 0)[clean], inside[clean])
+    err = np.abs(got - res["sign"] * d)[clean]
+    assert (err < 2e-6 + 1e-4 * d[clean]).all(), err.max()
+    grad = res["sign"][:, None] * diff / d[:, None]
+    gerr = np.abs(g.cpu().numpy().T.astype(np.float64) - grad).max(axis=1)[clean]
+    assert (gerr < 5e-4 + 2e-8 / d[clean]).all(), gerr.max()
+
+
+@pytest.mark.parametrize("n_major,n_minor", [(24, 12), (6, 3)])
+def test_torus_loss_and_grad_match_oracle(fg, n_major, n_minor):
+    """The 3-finger hand's candidates around a torus (tube radius 1.5 cm, ring 4 cm):
+    loss and leaky gradient of the fused kernel (BVH walk, pseudonormal sign, Phong
+    SDF, contacts) against the oracle on clean candidates."""
+    w = synth.tiny_sphere_workload(n_cand=48)
+    c = Case(fg, w.hand, [SM.torus_mesh(0.04, 0.015, n_major, n_minor)], w.obj_of_cand, w.q0, w.params)
+    loss, grad = fg.loss_and_grad(c.hand, c.scene, torch.tensor(w.q0, device=_dev()), w.params, 0.004,
+                                  obj_of_cand=c.oc)
+    ref = O.batch_loss_and_grad(c.S, w.q0, w.obj_of_cand, 0.004)
+    clean = c.clean(w.q0, 0.004)
+    assert clean.sum() >= 0.6 * len(clean)
+    assert (ref["N"].sum(axis=1) > 0).sum() >= 5, "workload must exercise contacts"
+    _compare(loss.cpu().numpy(), grad.cpu().numpy(), ref, clean)
+    q1 = torch.tensor(w.q0, device=_dev())
+    l1 = fg.optimize_step(c.hand, c.scene, q1, w.params, 0, w.steps, 1, obj_of_cand=c.oc)
+    step = (q1 - torch.tensor(w.q0, device=_dev())).cpu().numpy().astype(np.float64) / -w.params["lr"]
+    _compare(l1.cpu().numpy(), step, ref, clean)
 
 
 class Case:

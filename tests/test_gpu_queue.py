@@ -187,3 +187,77 @@ def test_mesh_request_in_the_mix(fg, requests):
     np.testing.assert_allclose(mixed[1][0], alone[1][0], rtol=1e-5, atol=1e-5)
     np.testing.assert_allclose(mixed[1][1], alone[1][1], rtol=1e-4)
     assert np.isfinite(mixed[0][0]).all() and np.isfinite(mixed[0][1]).all()
+
+
+def test_round_time_limit_fails_the_round_and_destroy_returns(fg, requests):
+    """A queue whose round limit (timeout_ms = 1) is far below one round's duration
+    (2,048 candidates of the 5-finger hand for 200 steps, tens of milliseconds): the
+    round's request fails with FG_ERR_TIMEOUT, the queue refuses further work, and
+    fg_queue_destroy returns (it waits for the still-running round with a bounded
+    wait and frees its state).  Nothing on the GPU waits: the kernel finishes its
+    round on its own.  The device then serves a fresh queue normally."""
+    from paper_2306_08132_gb300 import _lib
+    hand, sdf, q0, params, _ = requests[2]
+    big = np.repeat(q0, -(-2048 // len(q0)), axis=0)[:2048]
+    queue = fg.Queue(1 << 30, steps_per_launch=200, timeout_ms=1)
+    try:
+        rid = queue.submit(hand, sdf, big, 400, params)
+        queue.wait(rid, 60000)
+        with pytest.raises(_lib.FgError) as e:
+            queue.result(rid)
+        assert e.value.name == "FG_ERR_TIMEOUT"
+        with pytest.raises(_lib.FgError) as e:
+            queue.submit(hand, sdf, q0, 5, params)
+        assert e.value.name == "FG_ERR_CUDA" and "timeout_ms" in str(e.value)
+        assert queue.stats()["failed"] == 1
+    finally:
+        t0 = time.time()
+        queue.close()
+        assert time.time() - t0 < 30
+    torch.cuda.synchronize()
+    queue = fg.Queue(1 << 30, steps_per_launch=5)
+    try:
+        rid = queue.submit(hand, sdf, q0, 5, params)
+        queue.wait(rid, 60000)
+        q, loss, _ = queue.result(rid)
+        assert np.isfinite(q).all() and np.isfinite(loss).all()
+    finally:
+        queue.close()
+
+
+def test_allocation_failures_are_reported_cleanly(fg, requests):
+    """The library's allocation-failure injection: a hand, an object, a request's host
+    copy and a request's device state at admission each fail with FG_ERR_OOM when
+    their allocation fails, leave nothing half-built, and the next attempt succeeds;
+    the queue keeps serving after a request failed at admission."""
+    from paper_2306_08132_gb300 import _lib
+    w = synth.tiny_sphere_workload(n_cand=8)
+    try:
+        for make in (lambda: fg.Hand.from_synth(w.hand), lambda: fg.Sdf.from_synth(w.objects[0])):
+            fg.test_fail_allocation(0)
+            with pytest.raises(_lib.FgError) as e:
+                make()
+            assert e.value.name == "FG_ERR_OOM"
+            assert make() is not None                # disarmed after one failure
+        hand, sdf, q0, params, _ = requests[0]
+        queue = fg.Queue(1 << 30, steps_per_launch=5)
+        try:
+            fg.test_fail_allocation(0)               # the submit's host copy
+            with pytest.raises(_lib.FgError) as e:
+                queue.submit(hand, sdf, q0, 5, params)
+            assert e.value.name == "FG_ERR_OOM"
+            fg.test_fail_allocation(1)               # the submit passes, its admission fails
+            rid = queue.submit(hand, sdf, q0, 5, params)
+            queue.wait(rid, 60000)
+            with pytest.raises(_lib.FgError) as e:
+                queue.result(rid)
+            assert e.value.name == "FG_ERR_OOM"
+            assert queue.stats()["bytes_in_use"] == 0
+            rid = queue.submit(hand, sdf, q0, 5, params)
+            queue.wait(rid, 60000)
+            q, loss, _ = queue.result(rid)
+            assert np.isfinite(q).all()
+        finally:
+            queue.close()
+    finally:
+        fg.test_fail_allocation(-1)

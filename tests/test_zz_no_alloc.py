@@ -83,3 +83,37 @@ def test_noalloc_step_refuses_oversized_batches():
                                             C.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert st == 1
     assert "too large" in _last_error(lib)
+
+
+def test_noalloc_step_refuses_what_the_workspace_step_refuses():
+    """Both entry points check their arguments with the same routine: parameters the
+    workspace form refuses (infinite test velocity, friction or dilation, non-finite
+    loss weights, the T-step or Gauss-Seidel forms) are refused here too, before any
+    launch, with FG_ERR_INVALID."""
+    from paper_2306_08132_gb300.build import build_library
+    build_library()
+    import paper_2306_08132_gb300 as fg
+    from paper_2306_08132_gb300 import _lib
+    lib = _lib.load()
+
+    w = synth.tiny_sphere_workload(n_cand=4)
+    hand = fg.Hand.from_synth(w.hand)
+    scene = fg.Scene([fg.Sdf.from_synth(w.objects[0])])
+    B = 4
+    q = torch.tensor(w.q0, device="cuda:0")
+    ws = torch.empty(fg.plain_workspace_size(hand, B) + 256, dtype=torch.uint8, device="cuda:0")
+    ws_ptr = (ws.data_ptr() + 255) // 256 * 256
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    bad = [{"v_test": float("inf")}, {"mu": float("inf")}, {"r0": float("inf")}, {"w_range": float("nan")},
+           {"w_limit": float("inf")}, {"w_pen": float("-inf")}, {"dt": 0.0}, {"alpha_leak": 1.5},
+           {"sim_steps": 1}, {"gauss_seidel": 1}]
+    for change in bad:
+        prm = fg.make_params(dict(w.params, **change))
+        st_ws = lib.fg_optimize_step_plain(hand.handle, scene.handle, None, C.c_void_p(q.data_ptr()), B,
+                                           C.byref(prm), 0, 10, 1, None, C.c_void_p(ws_ptr), ws.numel() - 256,
+                                           stream)
+        st_na = lib.fg_optimize_step_plain_noalloc(hand.handle, scene.handle, None, C.c_void_p(q.data_ptr()), B,
+                                                   C.byref(prm), 0, 10, 1, None, stream)
+        assert st_ws == 1 and st_na == 1, (change, st_ws, st_na)
+    torch.cuda.synchronize()
+    assert torch.equal(q, torch.tensor(w.q0, device="cuda:0"))    # nothing ran
