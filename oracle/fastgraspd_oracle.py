@@ -726,13 +726,23 @@ def _face_margin(obj: Obj, pts: torch.Tensor) -> torch.Tensor:
     """Per point and axis, the distance (in voxels) of the lookup's decision from its
     threshold: inside the grid range the cell choice (distance to the nearest
     node plane), outside it the clamp (distance to the clamp plane).  For a mesh,
-    ten times (in metres) the smaller of the gap to the next distinct closest
-    point (the face choice) and the distance to the flat surface (the sign), so
-    that the default tolerance of 1e-5 is 1 micrometre."""
+    ten times (in metres) the smallest of: the gap to the next distinct closest
+    point (the face choice); the distance to the flat surface (the sign); the gap to
+    a face whose closest point lies elsewhere (gap_dir), scaled so that float32's
+    resolution of distances, 5e-8 m + 3e-7 of the distance, counts as 1
+    micrometre; and the distance to the Phong point scaled by 1e-2, so that 1e-4 m
+    counts as 1 micrometre (the Phong SDF's gradient field turns at the rate
+    1/|p - r*_rho|, and float32 positions, good to ~1e-8 m, leave the adjoint's
+    second-order term of a closer point uncertain by more than 1e-4 of itself).
+    The default tolerance of 1e-5 is 1 micrometre."""
     if isinstance(obj, _mesh.MeshObj):
         with torch.no_grad():
             dec = _mesh.mesh_decisions(obj, pts)
-            return (10.0 * torch.minimum(dec["gap"], dec["dist"]))[..., None]
+            res32 = 5e-8 + 3e-7 * dec["dist"]
+            d_rho = torch.linalg.norm(pts - dec["q_rho"], dim=-1)
+            m = torch.minimum(torch.minimum(dec["gap"], dec["dist"]),
+                              torch.minimum(dec["gap_dir"] * (1e-6 / res32), 1e-2 * d_rho))
+            return (10.0 * m)[..., None]
     n = torch.tensor(obj.dims, dtype=F64)
     u = (pts - obj.origin) / obj.pitch
     uc = torch.minimum(torch.maximum(u, torch.zeros_like(u)), n - 1)

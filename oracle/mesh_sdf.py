@@ -132,17 +132,29 @@ def closest_on_triangles(p: np.ndarray, a: np.ndarray, b: np.ndarray, c: np.ndar
     return q, bary, region
 
 
+# Closest points of two faces closer than this fraction of the distance count as the
+# same point for gap_dir (their directions from p differ by less).
+SAME_POINT = 1e-2
+
+
 def mesh_query(mesh: MeshObj, p: np.ndarray, chunk: int = 2048) -> dict:
     """Closest face, point, barycentrics, region, sign and Phong point for p [N,3];
-    also, for the guard band, the gap between the closest distance and the closest
-    distance over faces that share no vertex with the closest face.  (A choice
-    between faces that share an edge or a vertex near the closest point does not
-    matter: the Phong point is continuous across them.  A near tie with a face
-    further away is a medial-axis ambiguity.)"""
+    also, for the guard band, two gaps:
+
+    gap      the closest distance over faces that share no vertex with the closest
+             face, minus the closest distance (a near tie with a face elsewhere is a
+             medial-axis ambiguity; a choice between faces that share an edge or a
+             vertex at the closest point does not matter: the point, its
+             pseudonormal and the Phong point are the same from either);
+    gap_dir  the same over every face, adjacent or not, whose own closest point lies
+             further than SAME_POINT times the distance from the closest point: at a
+             concave edge of a non-convex mesh (or inside a convex corner) two
+             neighbouring faces can both be closest at interior points, and picking
+             the other one turns the direction from the closest point."""
     V, F = mesh.V, mesh.F
     a, b, c = V[F[:, 0]], V[F[:, 1]], V[F[:, 2]]
     N = p.shape[0]
-    out = {k: [] for k in ("face", "q", "bary", "region", "dist", "gap")}
+    out = {k: [] for k in ("face", "q", "bary", "region", "dist", "gap", "gap_dir")}
     for s in range(0, N, chunk):
         ps = p[s:s + chunk]
         q, bary, region = closest_on_triangles(ps, a, b, c)
@@ -154,12 +166,15 @@ def mesh_query(mesh: MeshObj, p: np.ndarray, chunk: int = 2048) -> dict:
         Ff = F[f]
         adjacent = (F[None, :, :, None] == Ff[:, None, None, :]).any(axis=(-1, -2))
         other = np.where(adjacent, np.inf, d2).min(axis=1)
+        same_point = np.linalg.norm(q - qf[:, None, :], axis=-1) <= SAME_POINT * np.sqrt(best)[:, None]
+        other_dir = np.where(same_point, np.inf, d2).min(axis=1)
         out["face"].append(f)
         out["q"].append(qf)
         out["bary"].append(bary[i, f])
         out["region"].append(region[i, f])
         out["dist"].append(np.sqrt(best))
         out["gap"].append(np.sqrt(other) - np.sqrt(best))
+        out["gap_dir"].append(np.sqrt(other_dir) - np.sqrt(best))
     res = {k: np.concatenate(v) for k, v in out.items()}
     res["sign"] = mesh_sign(mesh, p, res)
     res["q_rho"] = phong_point(mesh, res["face"], res["bary"], res["q"])
@@ -201,7 +216,8 @@ def mesh_decisions(mesh: MeshObj, p: torch.Tensor) -> dict:
     res = mesh_query(mesh, flat)
     t = lambda x, dt=F64: torch.as_tensor(x, dtype=dt).reshape(shape + x.shape[1:])
     return {"face": t(res["face"], torch.long), "region": t(res["region"], torch.long),
-            "sign": t(res["sign"]), "q_rho": t(res["q_rho"]), "gap": t(res["gap"]), "dist": t(res["dist"])}
+            "sign": t(res["sign"]), "q_rho": t(res["q_rho"]), "gap": t(res["gap"]), "dist": t(res["dist"]),
+            "gap_dir": t(res["gap_dir"])}
 
 
 def mesh_eval(mesh: MeshObj, p: torch.Tensor, dec: dict):

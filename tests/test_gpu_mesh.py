@@ -96,6 +96,22 @@ def _torus_points(m, rng, n=600):
     return np.concatenate([box, near, at_v, at_e])
 
 
+def _direction_ambiguous(mesh, p, res, sep=4e-4, tol_abs=5e-8, tol_rel=3e-7):
+    """Points whose closest point float32 cannot pin down to the direction tolerance:
+    another face (adjacent or not) has its own closest point further than sep times
+    the distance from the oracle's, at a distance within float32 resolution of the
+    best (tol_abs + tol_rel d).  At a concave edge two neighbouring faces can both be
+    closest at interior points, which the guard band's gap (non-adjacent faces)
+    does not see."""
+    V, F = mesh.V, mesh.F
+    q, _, _ = MS.closest_on_triangles(p, V[F[:, 0]], V[F[:, 1]], V[F[:, 2]])
+    dist = np.linalg.norm(p[:, None, :] - q, axis=-1)
+    best = res["dist"]
+    far = np.linalg.norm(q - res["q"][:, None, :], axis=-1) > sep * best[:, None]
+    near = dist - best[:, None] <= tol_abs + tol_rel * best[:, None]
+    return (far & near).any(axis=1)
+
+
 @pytest.mark.parametrize("n_major,n_minor", [(24, 12), (8, 4), (6, 3)])
 @pytest.mark.parametrize("alpha", [0.0, MS.PHONG_ALPHA])
 def test_torus_sign_and_value_match_oracle(fg, n_major, n_minor, alpha):
@@ -104,7 +120,8 @@ def test_torus_sign_and_value_match_oracle(fg, n_major, n_minor, alpha):
     ones (tubes of 3 or 4 faces) have sharp concave edges and vertices, where the sign
     needs the edge or vertex pseudonormal.  Against the oracle's brute-force query
     (whose sign is pinned on these tori by the winding number): the sign exactly, the
-    value and gradient within the query tolerances, on points outside the guard band."""
+    value and gradient within the query tolerances, on points outside the guard band
+    (the gradient also away from concave-edge ties, _direction_ambiguous)."""
     m = SM.torus_mesh(0.04, 0.015, n_major, n_minor)
     sdf = fg.Sdf.from_mesh(m["vertices"], m["faces"], m["mass"], m["inertia"], phong_alpha=alpha)
     ref_mesh = MS.MeshObj.from_synth(m, alpha=alpha)
@@ -122,8 +139,11 @@ def test_torus_sign_and_value_match_oracle(fg, n_major, n_minor, alpha):
     err = np.abs(got - res["sign"] * d)[clean]
     assert (err < 2e-6 + 1e-4 * d[clean]).all(), err.max()
     grad = res["sign"][:, None] * diff / d[:, None]
-    gerr = np.abs(g.cpu().numpy().T.astype(np.float64) - grad).max(axis=1)[clean]
-    assert (gerr < 5e-4 + 2e-8 / d[clean]).all(), gerr.max()
+    # the direction where float32 can pick a closest point elsewhere is left out
+    cdir = clean & ~_direction_ambiguous(ref_mesh, p32.astype(np.float64), res)
+    assert cdir.sum() >= 0.9 * clean.sum()
+    gerr = np.abs(g.cpu().numpy().T.astype(np.float64) - grad).max(axis=1)[cdir]
+    assert (gerr < 5e-4 + 2e-8 / d[cdir]).all(), gerr.max()
 
 
 @pytest.mark.parametrize("n_major,n_minor", [(24, 12), (6, 3)])
