@@ -443,10 +443,11 @@ def prewarm(fn, seconds=0.5):
         torch.cuda.synchronize()
 
 
-def timed(step_fn, nsteps, warm, flush, world, pre=None):
+def timed(step_fn, nsteps, warm, flush, world, pre=None, label="timed"):
     """Per-step device time (ms) with CUDA events on the launching stream; the L2 flush
     (and `pre`, e.g. a reset of q) run before each start event.  Barriers on both
-    sides under torchrun."""
+    sides under torchrun.  The timed steps are an NVTX range named `label` (a
+    profiler can select their launches with it)."""
     import torch
     stream = torch.cuda.current_stream()
     for _ in range(warm):
@@ -459,6 +460,7 @@ def timed(step_fn, nsteps, warm, flush, world, pre=None):
         dist.barrier()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(nsteps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(nsteps)]
+    torch.cuda.nvtx.range_push(label)
     for i in range(nsteps):
         flush.fill_(i & 0xff)
         if pre is not None:
@@ -466,6 +468,7 @@ def timed(step_fn, nsteps, warm, flush, world, pre=None):
         starts[i].record(stream)
         step_fn()
         ends[i].record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     if world > 1:
@@ -556,7 +559,7 @@ def measure_fused(fg, b, args, world, flush, peak, label_clocks=None):
     if sampler:
         sampler.start()
     t_wall = time.perf_counter()
-    ms = timed(g, args.steps, args.warmup, flush, world)
+    ms = timed(g, args.steps, args.warmup, flush, world, label="fused")
     wall = time.perf_counter() - t_wall
     clocks = sampler.stop() if sampler else None
     out = {"ms": ms, "wall": wall, "clocks": clocks, "best_cfg": best_cfg, "cfg_ms": cfg_ms, "cfgs": cfgs}
@@ -569,7 +572,7 @@ def measure_fused(fg, b, args, world, flush, peak, label_clocks=None):
             fg.optimize_step_plain(b.hand, b.scene, b.q, w.params, 0, K, S_in, obj_of_cand=b.oc, loss=b.loss,
                                    workspace=ws)
 
-        pms = timed(graphed(plain_step), max(3, args.steps // 2), 3, flush, world)
+        pms = timed(graphed(plain_step), max(3, args.steps // 2), 3, flush, world, label="plain")
         pstep = float(np.mean(pms))
         out["plain"] = {"value": w.B * S_in / (pstep / 1000.0), "ms_per_step": pstep,
                         "speedup_fused_over_plain": pstep / float(np.mean(ms)), "gpu_launches_per_step": 8 * S_in}
@@ -587,7 +590,7 @@ def measure_fused(fg, b, args, world, flush, peak, label_clocks=None):
         fg.optimize_step_host(b.hand, b.scene, hq0, b.q, w.params, 0, K, S_in, obj_of_cand=b.oc, loss=b.loss,
                               host_q_out=hq, host_loss=hloss)
 
-    ems = timed(e2e_step, max(3, args.steps // 2), 3, flush, world)
+    ems = timed(e2e_step, max(3, args.steps // 2), 3, flush, world, label="e2e")
     out["e2e_ms"] = float(np.mean(ems))
     out["e2e_bytes"] = (int(hq0.numel() * 4), int(hq.numel() * 4 + hloss.numel() * 4))
 
@@ -597,7 +600,7 @@ def measure_fused(fg, b, args, world, flush, peak, label_clocks=None):
     def reset_q():
         b.q.copy_(b.q0)
 
-    kms = timed(graphed(kernel_only), max(3, args.steps // 2), 3, flush, world, pre=reset_q)
+    kms = timed(graphed(kernel_only), max(3, args.steps // 2), 3, flush, world, pre=reset_q, label="kernel")
     out["kern_ms"] = float(np.mean(kms))
     out["fused_step"] = fused_step
     return out
@@ -613,6 +616,8 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle time for cpu_baseline")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-sub", action="store_true", help="skip the 8-superquadric sub-record")
+    ap.add_argument("--no-sub-legs", action="store_true",
+                    help="in the 8-superquadric sub-record, time the fused and per-stage forms only")
     ap.add_argument("--profile-kernel", action="store_true",
                     help="set up the workload, run a few fused launches and exit (for ncu)")
     ap.add_argument("--config", type=int, default=None, help="fused configuration index (default: autotune)")
@@ -638,6 +643,9 @@ def main():
     ap.add_argument("--mesh-res", default="24,48", help="latitude,longitude divisions of the superquadric meshes")
     ap.add_argument("--serving-sweep", default="",
                     help="comma-separated arrival rates (req/s) for a latency-vs-load sweep of the same stream")
+    ap.add_argument("--objects", type=int, default=None,
+                    help="a smaller copy of the workload with this many objects and the same candidates per object "
+                         "(for profiling captures)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -657,7 +665,7 @@ def main():
     import paper_2306_08132_gb300 as fg
     from paper_2306_08132_gb300 import shard
 
-    w, part = build_workload(dev, rank, world, args.workload)
+    w, part = build_workload(dev, rank, world, args.workload, **workload_sizes(args))
     b = Bound(fg, w, dev)
     K, S_in = w.steps, args.inner_steps
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
@@ -712,6 +720,13 @@ def main():
                "roofline": roofline_of(w2, S_in, r2["kern_ms"], peak, hbm_gbs, hbm_basis,
                                        load_profile("fused_step", w2.name)),
                "fused_config": "%dw/%d/%dp" % r2["cfgs"][r2["best_cfg"]]}
+        if not args.no_sub_legs:
+            # the other forms of the step on this batch: Gauss-Seidel, T-step (T = 1), mesh objects, quality
+            sub_args = argparse.Namespace(**dict(vars(args), tstep="1", gs=True, quality=True, mesh=True,
+                                                 order_quality=False, serving=0))
+            sub.update(run_legs(fg, sub_args, b2, dev, 1, flush, w2.B * S_in))
+            for k in ("order_quality", "serving", "serving_sweep"):
+                sub.pop(k, None)
         del b2
         fg.autotune(b.hand, b.scene, b.q0, w.params, 0, K, S_in, obj_of_cand=b.oc, reps=3)   # back to the main workload
 
@@ -776,6 +791,15 @@ def main():
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def workload_sizes(args) -> dict:
+    """Size arguments of a smaller copy of the workload (--objects), the same candidates per object."""
+    if args.objects is None:
+        return {}
+    if args.workload == "sweep256":
+        return {"n_obj": args.objects, "total_cand": 256 * args.objects}
+    return {"n_obj": args.objects}
 
 
 def superquadric_meshes(w, mesh_res):

@@ -43,7 +43,7 @@ struct FusedSmem {
   SimConsts K;                     // constants of the simulation adjoint
   float q[64];
   float grad[64];
-  float wred[NW][kSims][8];        // per warp: W (6), N, pen
+  unsigned long long wfix[kSims][8];  // forward sums in fixed point: W (6), N (integer), pen
   float lacc[NW][kMaxLinks][6];    // per warp, per link: sum g, sum (p - t) x g (fixed ranges)
   float uacc[kMaxUnits][6];        // per work unit: sum g, sum (p - t) x g
   float Wtot[kSims][8];
@@ -52,6 +52,7 @@ struct FusedSmem {
   int bad_object;
   int n_active;
   int next_unit;                   // adjoint sweep: next unclaimed work unit
+  int next_chunk;                  // forward sweep: next unclaimed active chunk
   unsigned active_bits[kMaxCullChunks / 32];
   unsigned short active_list[kMaxCullChunks];
   // source of the current candidate (the call's arguments, or a queue slot)
@@ -215,6 +216,38 @@ __device__ __forceinline__ void unit_reduce_store(const float a[6], int lane, fl
   if ((lane & 3) == 0 && k < 6) slot[k] = w;
 }
 
+// Fixed point with 44 fractional bits: every force and torque sum here is far
+// inside +-2^19, and the quantum 2^-44 lies far below float32 rounding of them.
+__device__ __forceinline__ unsigned long long to_fixed(float v) {
+  return (unsigned long long)__float2ll_rn(__fmul_rn(v, 0x1p44f));
+}
+__device__ __forceinline__ float from_fixed(long long x) { return __fmul_rn(__ll2float_rn(x), 0x1p-44f); }
+
+// The warp's sums of a[0..5] (the fixed pattern of unit_reduce_store) added in
+// fixed point to slot[0..5]: lane 4k holds the total of value k.
+__device__ __forceinline__ void unit_reduce_add_fixed(const float a[6], int lane, unsigned long long* slot) {
+  const float v[8] = {a[0], a[1], a[2], a[3], a[4], a[5], 0.0f, 0.0f};
+  const bool h16 = (lane & 16) != 0, h8 = (lane & 8) != 0, h4 = (lane & 4) != 0;
+  float w4[4], w2[2];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const float send = h16 ? v[j] : v[4 + j];
+    const float keep = h16 ? v[4 + j] : v[j];
+    w4[j] = keep + __shfl_xor_sync(kFull, send, 16);
+  }
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const float send = h8 ? w4[j] : w4[2 + j];
+    const float keep = h8 ? w4[2 + j] : w4[j];
+    w2[j] = keep + __shfl_xor_sync(kFull, send, 8);
+  }
+  float w = (h4 ? w2[1] : w2[0]) + __shfl_xor_sync(kFull, h4 ? w2[0] : w2[1], 4);
+  w += __shfl_xor_sync(kFull, w, 2);
+  w += __shfl_xor_sync(kFull, w, 1);
+  const int k = lane >> 2;
+  if ((lane & 3) == 0 && k < 6) atomicAdd(slot + k, to_fixed(w));
+}
+
 // Adds 32 points' (g, r x g) to the warp's per-link sums.  Runs of points of one
 // link accumulate in registers (acc, for link cur) and are reduced when the link
 // changes; a group of 32 that straddles links is reduced link by link.
@@ -334,7 +367,8 @@ __global__ void __launch_bounds__(NW * 32, MINB) fused_step_kernel(FusedArgs a) 
       const float r = kOpt ? dilation_at(Pm, S.step0 + s, S.total) : a.r_fixed;
       __syncthreads();
       if (warp == 0) fk_warp(H, S.q, S.frame4, lane);
-      for (int idx = tid; idx < NW * kSims * 8; idx += NW * 32) (&S.wred[0][0][0])[idx] = 0.0f;
+      for (int idx = tid; idx < kSims * 8; idx += NW * 32) (&S.wfix[0][0])[idx] = 0ull;
+      if (tid == 0) S.next_chunk = 0;
       __syncthreads();
       const ObjDev& O = S.O;
 
@@ -406,17 +440,20 @@ __global__ void __launch_bounds__(NW * 32, MINB) fused_step_kernel(FusedArgs a) 
       }
 
       // ---------------------------------------------------------------- sweep 1
+      // Warps claim active chunks from a shared counter (a chunk with contacts costs
+      // more).  A simulation's forces in a chunk are summed over its lanes with a
+      // fixed shuffle pattern and added to the CTA's sums in fixed point, so the
+      // totals do not depend on which warp ran which chunk, nor on the order.
       {
-        // per-thread wrench sums (registers), contact counts from ballots (warp-uniform)
-        float W[kSims][6], cnt[kSims], pen = 0.0f;
-#pragma unroll
-        for (int m = 0; m < kSims; ++m) {
-          cnt[m] = 0.0f;
-#pragma unroll
-          for (int k = 0; k < 6; ++k) W[m][k] = 0.0f;
-        }
         const int n_work = cull ? S.n_active : H.nchunks;
-        for (int idx = warp; idx < n_work; idx += NW) {
+        auto claim = [&]() {
+          int j = 0;
+          if (lane == 0) j = atomicAdd(&S.next_chunk, 1);
+          return __shfl_sync(kFull, j, 0);
+        };
+        int idx = claim();
+        while (idx < n_work) {
+          const int nidx = claim();
           const int base = 32 * (cull ? (int)S.active_list[idx] : idx);
           const int i = base + lane;
           const bool valid = i < P;
@@ -427,36 +464,31 @@ __global__ void __launch_bounds__(NW * 32, MINB) fused_step_kernel(FusedArgs a) 
           sdf_lookup<false, ANY>(O, p, smp);
           PointState ps;
           point_state(smp, p, r, ps);
-#pragma unroll
+#pragma unroll 1
           for (int m = 0; m < kSims; ++m) {
             const float phm = sim_phi(ps, m, dtV);
             const bool kap = valid && phm < 0.0f;
             const unsigned bal = __ballot_sync(kFull, kap);
-            cnt[m] += (float)__popc(bal);
             if (MODE == kModeWrench && lane == 0 && a.bits)
               a.bits[((size_t)c * kSims + m) * nwords + (base >> 5)] = bal;
+            if (bal == 0u) continue;
+            float v[6] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
             if (kap) {
               float f[3], d[3], tq[3];
               contact_force(ps, m, -phm, Pm, O, f, d);
               cross3(d, f, tq);
-              W[m][0] += f[0]; W[m][1] += f[1]; W[m][2] += f[2];
-              W[m][3] += tq[0]; W[m][4] += tq[1]; W[m][5] += tq[2];
-              if (m == 0) pen -= phm;
+              v[0] = f[0]; v[1] = f[1]; v[2] = f[2];
+              v[3] = tq[0]; v[4] = tq[1]; v[5] = tq[2];
+            }
+            unit_reduce_add_fixed(v, lane, S.wfix[m]);
+            if (lane == 0) atomicAdd(&S.wfix[m][6], (unsigned long long)__popc(bal));
+            if (m == 0 && Pm.w_pen != 0.0f) {
+              const float pen = warp_sum(kap ? -phm : 0.0f);
+              if (lane == 0) atomicAdd(&S.wfix[0][7], to_fixed(pen));
             }
           }
+          idx = nidx;
         }
-        // one reduction per warp and step
-#pragma unroll
-        for (int m = 0; m < kSims; ++m) {
-#pragma unroll
-          for (int k = 0; k < 6; ++k) {
-            const float v = warp_sum(W[m][k]);
-            if (lane == 0) S.wred[warp][m][k] = v;
-          }
-          if (lane == 0) S.wred[warp][m][6] = cnt[m];
-        }
-        pen = warp_sum(pen);
-        if (lane == 0) S.wred[warp][0][7] = pen;
       }
       __syncthreads();
 
@@ -464,10 +496,8 @@ __global__ void __launch_bounds__(NW * 32, MINB) fused_step_kernel(FusedArgs a) 
       if (warp == 0) {
         for (int idx = lane; idx < kSims * 8; idx += 32) {
           const int m = idx >> 3, k = idx & 7;
-          float v = 0.0f;
-#pragma unroll
-          for (int w = 0; w < NW; ++w) v += S.wred[w][m][k];
-          S.Wtot[m][k] = v;
+          const long long x = (long long)S.wfix[m][k];
+          S.Wtot[m][k] = k == 6 ? (float)x : from_fixed(x);
         }
         __syncwarp();
         if (MODE != kModeWrench) {

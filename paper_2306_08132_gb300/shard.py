@@ -68,3 +68,50 @@ def gather_rows(rows: np.ndarray, candidates: np.ndarray, n_total: int, group=No
     if not seen.all():
         raise RuntimeError("%d candidates were computed by no rank" % int((~seen).sum()))
     return out
+
+
+class RequestRouter:
+    """Routes serving requests to GPUs by HBM budget (one request queue per GPU).
+
+    A request needs its optimiser state (q and loss: B (D + 1) floats) on the GPU
+    that serves it, plus its object's grid unless that GPU already holds the object
+    for another request.  Each request goes to the GPU where it adds the fewest
+    bytes (its object already resident there first), ties broken by the most free
+    budget, then the lowest index; a request that fits no GPU's remaining budget is
+    refused (None) and can be submitted again after `release`.  Host bookkeeping
+    only: the queues admit and run the requests."""
+
+    def __init__(self, budgets):
+        self.budget = [int(b) for b in budgets]
+        self.used = [0] * len(self.budget)
+        self.objects = [dict() for _ in self.budget]      # object key -> (bytes, requests using it)
+
+    def need(self, gpu: int, state_bytes: int, obj_key, obj_bytes: int) -> int:
+        return int(state_bytes) + (0 if obj_key in self.objects[gpu] else int(obj_bytes))
+
+    def route(self, state_bytes: int, obj_key, obj_bytes: int):
+        best = None
+        for g in range(len(self.budget)):
+            n = self.need(g, state_bytes, obj_key, obj_bytes)
+            if self.used[g] + n > self.budget[g]:
+                continue
+            key = (n, -(self.budget[g] - self.used[g]), g)
+            if best is None or key < best[0]:
+                best = (key, g, n)
+        if best is None:
+            return None
+        _, g, n = best
+        self.used[g] += n
+        b, refs = self.objects[g].get(obj_key, (int(obj_bytes), 0))
+        self.objects[g][obj_key] = (b, refs + 1)
+        return g
+
+    def release(self, gpu: int, state_bytes: int, obj_key) -> None:
+        """The request finished on `gpu`: its state, and its object once unused, free up."""
+        self.used[gpu] -= int(state_bytes)
+        b, refs = self.objects[gpu][obj_key]
+        if refs == 1:
+            del self.objects[gpu][obj_key]
+            self.used[gpu] -= b
+        else:
+            self.objects[gpu][obj_key] = (b, refs - 1)

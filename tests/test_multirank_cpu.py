@@ -79,3 +79,21 @@ def test_object_and_candidate_shards():
     assert full.shape == (8, 2) and full[5, 0] == 1 and full[0, 0] == 0
     with pytest.raises(ValueError):
         shard.object_shard(3, 2, 2)
+
+
+def test_requests_routed_by_hbm_budget():
+    """Serving on several GPUs: each request goes to the GPU where it adds the fewest
+    bytes (its object already resident first), then to the one with the most free
+    budget; requests that fit nowhere are refused until others release their bytes."""
+    from paper_2306_08132_gb300.shard import RequestRouter
+    r = RequestRouter([1000, 1000])
+    assert r.route(100, "a", 500) == 0                 # both empty: the lower index
+    assert r.route(100, "b", 500) == 1                 # GPU 1 has more free budget
+    assert r.route(50, "a", 500) == 0                  # object a resident on GPU 0: 50 bytes there
+    assert r.used == [650, 600]
+    assert r.route(300, "c", 400) is None              # 700 fits neither (350 and 400 left)
+    assert r.route(300, "b", 500) == 1                 # b resident on GPU 1
+    r.release(0, 100, "a")
+    r.release(0, 50, "a")                              # a's last request: its grid leaves GPU 0
+    assert r.used == [0, 900] and "a" not in r.objects[0]
+    assert r.route(300, "c", 400) == 0
