@@ -314,6 +314,7 @@ def run_serving(fg, n_requests: int, rates_hz, device, budget_bytes: int, steps_
                     "p99_s": float(np.percentile(lat, 99)), "mean_s": float(lat.mean()), "makespan_s": makespan,
                     "offered_candidate_steps_per_s": offered, "candidate_steps_per_s": served,
                     "rounds": st["rounds"], "steps_per_launch": steps_per_launch,
+                    "mean_round_ms": 1000.0 * makespan / max(st["rounds"], 1),
                     "note": ("offered load exceeds capacity: latency includes queueing" if served < 0.9 * offered
                              else "offered load within capacity")})
     return out

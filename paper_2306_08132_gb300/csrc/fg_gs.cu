@@ -51,7 +51,7 @@ namespace fg {
 namespace {
 
 constexpr int kGW = kSims;                    // one warp per simulation
-constexpr int kSnapWords = 13;                // per chunk and simulation: state (6), adjoint (6), event mask
+constexpr int kSnapWords = 14;                // per chunk and simulation: state (6), adjoint (6), event mask, pad
 
 struct GsSmem {
   HandDev H;
@@ -63,7 +63,7 @@ struct GsSmem {
   float lb[kMaxCullChunks];        // lower bound of phi_hat over the chunk (-inf: never culled)
   float reach[kMaxCullChunks][kSims];   // |c - x~_m| + R: lever bound of the chunk's points in simulation m
   float sfin[kSims][6];            // final state per simulation
-  float afin[kSims][6];            // dL/d(final state)
+  __align__(8) float afin[kSims][6];   // dL/d(final state)
   float red[kSims][8];             // per simulation: sum f (3), sum d x f (3), contacts, penetration
   float lacc[kGW][kMaxLinks][6];   // per warp, per link: sum g, sum (p - t) x g
   float loss;
@@ -74,7 +74,8 @@ struct GsSmem {
 
 // Dynamic shared memory, per chunk c and simulation m (word offsets):
 //   [0, 6)  state at the chunk's start,  [6, 12) state adjoint at the chunk's start,
-//   12      event mask (lanes projected, as float bits)
+//   12      event mask (lanes projected, as float bits), 13 padding (an even stride
+//   keeps the state and the adjoint 8-byte aligned: three 8-byte loads each)
 __device__ __forceinline__ float* snap(float* dyn, int c, int m) { return dyn + ((size_t)c * kSims + m) * kSnapWords; }
 
 // v[k] for k = lane (0..5), by selects (no local-memory indexing).
@@ -192,6 +193,65 @@ __device__ __forceinline__ void gs_leaky(const PointState& ps, const float xt[3]
   for (int k = 0; k < 3; ++k) {
     dn[k] -= phibar * D[k];
     dp[k] += phibar * wn_[k];
+  }
+}
+
+// The record a chunk without events of simulation m keeps for the adjoint of its
+// points, in place of its state and state adjoint: e = x~ + dx - dth x x~ (then
+// D = e + dth x p for every point of the chunk), dth, and the state adjoint scaled
+// by the inverse mass and inertia.  The state and its adjoint are constant across
+// such a chunk, so these are shared by its 32 points.
+__device__ __forceinline__ void gs_segment_record(float* sc, const float a[6], const float xt[3], const ObjDev& O) {
+  const float dth[3] = {sc[3], sc[4], sc[5]};
+  float c[3];
+  cross3(dth, xt, c);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    sc[k] = sc[k] + xt[k] - c[k];
+    sc[6 + k] = O.inv_mass * a[k];
+    sc[9 + k] = O.inv_inertia * a[3 + k];
+  }
+}
+
+// gs_leaky from a chunk's record (gs_segment_record): the same leaky adjoint, with
+// U = p x n shared by the simulations and the outputs that are linear in phibar
+// accumulated per point (sd = sum phibar dth, se = sum phibar e; afterwards
+// dn -= se + sd x p and dp += sd x n).
+__device__ __forceinline__ void gs_leaky_rec(const PointState& ps, const float U[3], const float xt[3],
+                                             const float e[3], const float dth[3], const float ax[3],
+                                             const float ath[3], float extra_dC, const ParamsDev& P,
+                                             const ObjDev& O, float& dphi, float sd[3], float se[3]) {
+  float c3[3], xn[3], D[3], un[3];
+  cross3(dth, ps.p, c3);
+  cross3(xt, ps.n, xn);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    D[k] = e[k] + c3[k];
+    un[k] = U[k] - xn[k];
+  }
+  const float rwn = rcp_fast(fma_(O.inv_inertia, dot3(un, un), O.inv_mass));
+  const float sn = dot3(D, ps.n);
+  float t[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) t[k] = fmaf(-sn, ps.n[k], D[k]);
+  const float s2 = dot3(t, t);
+  float c = rwn * (dot3(ax, ps.n) + dot3(ath, un));
+  if (s2 > 0.0f) {
+    const float rs = rsqrtf(s2);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) t[k] *= rs;
+    const float d[3] = {ps.p[0] - xt[0], ps.p[1] - xt[1], ps.p[2] - xt[2]};
+    float ut[3];
+    cross3(d, t, ut);
+    const float rwt = rcp_fast(fma_(O.inv_inertia, dot3(ut, ut), O.inv_mass));
+    c += P.mu * rwt * (dot3(ax, t) + dot3(ath, ut));
+  }
+  const float phibar = P.alpha * (c - extra_dC);
+  dphi += phibar;
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    sd[k] = fmaf(phibar, dth[k], sd[k]);
+    se[k] = fmaf(phibar, e[k], se[k]);
   }
 }
 
@@ -633,11 +693,8 @@ __global__ void __launch_bounds__(kGW * 32, 3) gs_kernel(FusedArgs a) {
           const bool ev = jj >= 0 && __float_as_uint(snap(dyn, jj, m)[12]) != 0u;
           const unsigned eb = __ballot_sync(kFull, ev);
           const int je = eb ? j - (__ffs(eb) - 1) : max(j - 32, -1);
-          if (jj > je && jj >= 0) {                      // chunks without events: the adjoint passes through
-            float* sc = snap(dyn, jj, m);
-#pragma unroll
-            for (int k = 0; k < 6; ++k) sc[6 + k] = av[k];
-          }
+          if (jj > je && jj >= 0)                        // chunks without events: the adjoint passes through
+            gs_segment_record(snap(dyn, jj, m), av, xt, O);
           if (!eb) {
             j = je;
             continue;
@@ -694,20 +751,33 @@ __global__ void __launch_bounds__(kGW * 32, 3) gs_kernel(FusedArgs a) {
           PointState ps;
           point_state(smp, p, r, ps);
           float dphi = 0.0f, dn[3] = {0.0f, 0.0f, 0.0f}, dp[3] = {0.0f, 0.0f, 0.0f};
+          float U[3], sd[3] = {0.0f, 0.0f, 0.0f}, se[3] = {0.0f, 0.0f, 0.0f};
+          cross3(ps.p, ps.n, U);
 #pragma unroll 1
           for (int m = 0; m < kSims; ++m) {
+            const float* sn = snap(dyn, j, m);
+            if (__float_as_uint(sn[12]) != 0u) continue;    // reversed with its events above
             float xt[3];
             sim_pred(m, dtV, xt);
-            const float* sn = snap(dyn, j, m);
-            const float* an = j + 1 < nch ? snap(dyn, j + 1, m) + 6 : S.afin[m];
-            float st0[6], ae[6];
+            const float2* r2 = reinterpret_cast<const float2*>(sn);
+            float rec[12];
 #pragma unroll
             for (int k = 0; k < 6; ++k) {
-              st0[k] = sn[k];
-              ae[k] = an[k];
+              const float2 x = r2[k];
+              rec[2 * k] = x.x;
+              rec[2 * k + 1] = x.y;
             }
-            const unsigned mask = __float_as_uint(sn[12]);
-            if (mask == 0u) gs_leaky(ps, xt, st0, ae, m == 0 ? Pm.w_pen : 0.0f, Pm, O, dphi, dn, dp);
+            gs_leaky_rec(ps, U, xt, rec, rec + 3, rec + 6, rec + 9, m == 0 ? Pm.w_pen : 0.0f, Pm, O, dphi, sd, se);
+          }
+          {
+            float sp_[3], sn_[3];
+            cross3(sd, ps.p, sp_);
+            cross3(sd, ps.n, sn_);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+              dn[k] -= se[k] + sp_[k];
+              dp[k] += sn_[k];
+            }
           }
           sdf_adjoint(smp, ps, dphi, dn, dp);
           float v[6];
