@@ -225,12 +225,13 @@ __device__ __forceinline__ void sdf_index(const ObjDev& O, const float p[3], Sdf
     const float uc = fminf(fmaxf(u, 0.0f), n_max[k]);     // NaN -> 0
     ix.clamped[k] = uc != u;
     ix.du[k] = sub_(u, uc);                               // 0 unless clamped
-    const int ii = (int)floorf(uc);
+    const int ii = __float2int_rd(uc);                   // floor (uc >= 0)
     const int cap = (int)n_max[k] - 1;
     i0[k] = ii < cap ? ii : cap;
     ix.f[k] = sub_(uc, (float)i0[k]);
   }
-  ix.cell = O.grid + ((size_t)i0[2] * O.ny + i0[1]) * O.nx + i0[0];
+  // fewer than 2^31 nodes per grid (checked at creation): the index fits 32 bits
+  ix.cell = O.grid + (unsigned)((i0[2] * O.ny + i0[1]) * O.nx + i0[0]);
 }
 
 __device__ __forceinline__ void sdf_gather(const ObjDev& O, const float* G, float c[8]) {
@@ -327,6 +328,28 @@ __device__ __forceinline__ void sdf_finish_pair(const ObjDev& O, const SdfIndex&
   sdf_finish_v<true, float2>(O, f, du, cl, c, s);
 }
 
+
+// Lower bound of the interpolated SDF at p from one entry of the min-pyramid: the
+// block of 2^lev cells (level 2 when the grid has it) holding p's cell, the cell
+// sdf_index picks.  The interpolant in a cell is a convex combination of its
+// corners and the excess distance outside the grid is non-negative, so
+// phi(p) >= the block's minimum.
+__device__ __forceinline__ float point_min_bound(const ObjDev& O, const float p[3]) {
+  const int lev = O.pyr_levels >= 2 ? 2 : 1;
+  const float n_max[3] = {(float)(O.nx - 1), (float)(O.ny - 1), (float)(O.nz - 1)};
+  const int n[3] = {O.nx, O.ny, O.nz};
+  int b[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float u = fma_(p[k], O.inv_h, O.uo[k]);
+    const float uc = fminf(fmaxf(u, 0.0f), n_max[k]);      // NaN -> 0
+    const int ii = __float2int_rd(uc);
+    const int cap = n[k] - 2;
+    b[k] = (ii < cap ? ii : cap) >> lev;
+  }
+  const int bx = ((n[0] - 1) + (1 << lev) - 1) >> lev, by = ((n[1] - 1) + (1 << lev) - 1) >> lev;
+  return __ldg(O.pyr + O.pyr_off[lev - 1] + (unsigned)((b[2] * by + b[1]) * bx + b[0]));
+}
 
 // Lower bound of the interpolated SDF over every point whose index coordinates
 // lie in the box [lo, hi] (any values; clamped to the grid, which also covers

@@ -441,7 +441,8 @@ __global__ void __launch_bounds__(NW * 32, MINB) fused_step_kernel(FusedArgs a) 
 
       // ---------------------------------------------------------------- sweep 1
       // Warps claim active chunks from a shared counter (a chunk with contacts costs
-      // more).  A simulation's forces in a chunk are summed over its lanes with a
+      // more); a chunk whose every point is cleared by its own pyramid entry is
+      // skipped before the lookups.  A simulation's forces in a chunk are summed over its lanes with a
       // fixed shuffle pattern and added to the CTA's sums in fixed point, so the
       // totals do not depend on which warp ran which chunk, nor on the order.
       {
@@ -460,6 +461,19 @@ __global__ void __launch_bounds__(NW * 32, MINB) fused_step_kernel(FusedArgs a) 
           const float4 sp = __ldg(H.pts + (valid ? i : base));
           float p[3];
           world_point(S.frame4[(int)sp.w], sp, p);
+          if (!(ANY && O.kind == kObjMesh)) {
+            // A chunk that passed the test of its bounding sphere is tested point by
+            // point (one pyramid entry each): if no point can have phi_m < 0 in any
+            // simulation, the chunk holds no contact and its lookups are skipped.
+            const float mn = point_min_bound(O, p);
+            const bool clear = !valid || mn - r - dtV * (1.0f + 1e-5f) - (1e-6f + 1e-5f * fabsf(mn)) > 0.0f;
+            if (__all_sync(kFull, clear)) {
+              if (MODE == kModeWrench && a.bits && lane < kSims)
+                a.bits[((size_t)c * kSims + lane) * nwords + (base >> 5)] = 0u;
+              idx = nidx;
+              continue;
+            }
+          }
           SdfSample smp;
           sdf_lookup<false, ANY>(O, p, smp);
           PointState ps;
@@ -727,6 +741,6 @@ cudaError_t launch_fused_cfg(const FusedArgs& a, cudaStream_t st) {
 // warps per candidate, the minimum resident CTAs per SM the register
 // allocation is held to, and points per thread in the adjoint sweep.  The autotuner times them on a workload.
 // (warps per candidate, min CTAs per SM, points per thread per adjoint iteration)
-#define FG_FUSED_CONFIGS(X) X(4, 4, 1) X(4, 5, 1) X(4, 6, 1) X(4, 8, 1) X(8, 3, 1) X(2, 8, 1) X(4, 3, 2) X(4, 4, 2) X(4, 5, 2) X(8, 2, 2)
+#define FG_FUSED_CONFIGS(X) X(4, 4, 1) X(4, 5, 1) X(4, 6, 1) X(4, 8, 1) X(8, 3, 1) X(2, 8, 1) X(4, 3, 2) X(4, 4, 2) X(4, 5, 2) X(8, 2, 2) X(4, 7, 1)
 
 }  // namespace fg

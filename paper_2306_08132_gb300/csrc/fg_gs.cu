@@ -548,12 +548,21 @@ __global__ void __launch_bounds__(kGW * 32, 3) gs_kernel(FusedArgs a) {
           float* sn = snap(dyn, jn, m);
           if (lane < 6) sn[lane] = pick6(st, lane);
           unsigned mask = 0u;
-          {
-            const int i = 32 * jn + lane;
-            const bool valid = i < P;
-            const float4 sp = __ldg(H.pts + (valid ? i : 32 * jn));
-            float p[3];
-            world_point(S.frame4[(int)sp.w], sp, p);
+          const int i = 32 * jn + lane;
+          const bool valid = i < P;
+          const float4 sp = __ldg(H.pts + (valid ? i : 32 * jn));
+          float p[3];
+          world_point(S.frame4[(int)sp.w], sp, p);
+          bool clear = !valid;
+          if (!(ANY && O.kind == kObjMesh) && valid) {
+            // point by point (one pyramid entry each): phi = phi_hat - n . D with
+            // phi_hat >= min - r and |n . D| <= |x~ + dx| + |dth| |p - x~|
+            const float mn = point_min_bound(O, p);
+            const float dl[3] = {p[0] - xt[0], p[1] - xt[1], p[2] - xt[2]};
+            const float bnd = fmaf(en, sqrtf(dl[0] * dl[0] + dl[1] * dl[1] + dl[2] * dl[2]), ex);
+            clear = mn - r - bnd * (1.0f + 1e-5f) - (1e-6f + 1e-5f * fabsf(mn)) > 0.0f;
+          }
+          if (!__all_sync(kFull, clear)) {
             SdfSample smp;
             sdf_lookup<false, ANY>(O, p, smp);
             PointState ps;

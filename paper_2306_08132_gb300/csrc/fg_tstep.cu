@@ -399,6 +399,11 @@ __global__ void __launch_bounds__(kTW * 32, 4) tstep_kernel(FusedArgs a) {
             float p[3], d[3], r[3];
             world_point(S.frame4[(int)sp.w], sp, p);
             step_query(st, p, d, r);
+            if (!(ANY && O.kind == kObjMesh)) {
+              // point by point (one pyramid entry each): phi_hat(r) >= min - rdil
+              const float mn = point_min_bound(O, r);
+              if (__all_sync(kFull, !valid || mn - rdil - (1e-6f + 1e-5f * fabsf(mn)) > 0.0f)) continue;
+            }
             SdfSample smp;
             sdf_lookup<false, ANY>(O, r, smp);
             PointState ps;
