@@ -776,7 +776,7 @@ __device__ __forceinline__ void contact_force(const PointState& ps, int m, float
   float un[3];
   cross3(d, ps.n, un);
   const float wn = fma_(O.inv_inertia, dot3(un, un), O.inv_mass);
-  const float lam_n = C / wn;
+  const float lam_n = C * rcp_fast(wn);       // w_n >= 1/m: a normal float
   f[0] = -lam_n * ps.n[0];
   f[1] = -lam_n * ps.n[1];
   f[2] = -lam_n * ps.n[2];
@@ -788,7 +788,7 @@ __device__ __forceinline__ void contact_force(const PointState& ps, int m, float
     cross3(d, t, ut);
     const float wt = fma_(O.inv_inertia, dot3(ut, ut), O.inv_mass);
     const float muC = mul_(P.mu, C);
-    const float lam_t = (sigma <= muC ? sigma : muC) / wt;
+    const float lam_t = (sigma <= muC ? sigma : muC) * rcp_fast(wt);
     f[0] -= lam_t * t[0];
     f[1] -= lam_t * t[1];
     f[2] -= lam_t * t[2];

@@ -116,9 +116,10 @@ __device__ __forceinline__ float gs_tangent(const float n[3], const float D[3], 
     t[0] = t[1] = t[2] = 0.0f;
     return 0.0f;
   }
-  const float sig = __fsqrt_rn(s2);
+  const float rs = rsqrtf(s2);
+  const float sig = mul_(s2, rs);
 #pragma unroll
-  for (int k = 0; k < 3; ++k) t[k] = __fdiv_rn(s[k], sig);
+  for (int k = 0; k < 3; ++k) t[k] = mul_(s[k], rs);
   return sig;
 }
 
@@ -130,7 +131,7 @@ __device__ __forceinline__ void gs_force(const PointState& ps, const float d[3],
   float un[3];
   cross3(d, ps.n, un);
   const float wn = fma_(O.inv_inertia, dot3(un, un), O.inv_mass);
-  const float lam_n = __fdiv_rn(C, wn);
+  const float lam_n = mul_(C, rcp_fast(wn));
 #pragma unroll
   for (int k = 0; k < 3; ++k) f[k] = -mul_(lam_n, ps.n[k]);
   float t[3], sn;
@@ -140,7 +141,7 @@ __device__ __forceinline__ void gs_force(const PointState& ps, const float d[3],
     cross3(d, t, ut);
     const float wt = fma_(O.inv_inertia, dot3(ut, ut), O.inv_mass);
     const float muC = mul_(P.mu, C);
-    const float lam_t = __fdiv_rn(sig <= muC ? sig : muC, wt);
+    const float lam_t = mul_(sig <= muC ? sig : muC, rcp_fast(wt));
 #pragma unroll
     for (int k = 0; k < 3; ++k) f[k] = fma_(-lam_t, t[k], f[k]);
   }
@@ -271,7 +272,7 @@ __device__ __forceinline__ void gs_contact_adjoint(const PointState& ps, const f
   float un[3];
   cross3(d, n, un);
   const float wn = fma_(O.inv_inertia, dot3(un, un), O.inv_mass);
-  const float rwn = 1.0f / wn;
+  const float rwn = rcp_fast(wn);
   const float lam_n = C * rwn;
   float t[3], sn;
   const float sig = gs_tangent(n, D, t, sn);
@@ -279,7 +280,7 @@ __device__ __forceinline__ void gs_contact_adjoint(const PointState& ps, const f
   bool stat = false;
   if (sig > 0.0f) {
     cross3(d, t, ut);
-    rwt = 1.0f / fma_(O.inv_inertia, dot3(ut, ut), O.inv_mass);
+    rwt = rcp_fast(fma_(O.inv_inertia, dot3(ut, ut), O.inv_mass));
     stat = sig <= mul_(P.mu, C);
     lam_t = (stat ? sig : P.mu * C) * rwt;
   }
@@ -330,7 +331,7 @@ __device__ __forceinline__ void gs_contact_adjoint(const PointState& ps, const f
     for (int k = 0; k < 3; ++k) tb[k] += tmp[k];
     // t = s/sigma, sigma = |s|, s = D - (D . n) n
     const float ttb = dot3(t, tb);
-    const float rs = 1.0f / sig;
+    const float rs = __fdividef(1.0f, sig);
     float sb[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) sb[k] = (tb[k] - ttb * t[k]) * rs + sigb * t[k];

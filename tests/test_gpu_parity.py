@@ -293,3 +293,48 @@ def test_every_fused_configuration_matches_oracle(fg, tiny):
         assert torch.equal(q, torch.tensor(w.q0, device=_dev()))     # the autotuner leaves q alone
     finally:
         fg.fused_config_select(-1)
+
+
+def test_host_buffer_step_equals_device_step(fg, tiny):
+    """fg_optimize_step_host (the library copies q in from host memory and q and the
+    loss back) gives the device entry point's results bit for bit, from pinned and
+    from pageable host buffers, in place (one host buffer) or not; B = 0 is a no-op."""
+    w = tiny.w
+    q0 = torch.tensor(w.q0, device=_dev())
+    q_ref = q0.clone()
+    l_ref = fg.optimize_step(tiny.hand, tiny.scene, q_ref, w.params, 2, w.steps, 2, obj_of_cand=tiny.oc)
+    torch.cuda.synchronize()
+    for pinned in (True, False):
+        hq = torch.tensor(w.q0)
+        if pinned:
+            hq = hq.pin_memory()
+        hout = torch.empty_like(hq)
+        hloss = torch.empty(w.B, dtype=torch.float32)
+        qd = torch.empty_like(q0)
+        fg.optimize_step_host(tiny.hand, tiny.scene, hq, qd, w.params, 2, w.steps, 2, obj_of_cand=tiny.oc,
+                              host_q_out=hout, host_loss=hloss)
+        torch.cuda.synchronize()
+        assert torch.equal(hout, q_ref.cpu()) and torch.equal(hloss, l_ref.cpu())
+        assert torch.equal(hq, torch.tensor(w.q0))          # the input is left alone
+        fg.optimize_step_host(tiny.hand, tiny.scene, hq, qd, w.params, 2, w.steps, 2, obj_of_cand=tiny.oc)
+        torch.cuda.synchronize()
+        assert torch.equal(hq, q_ref.cpu())                 # in place
+    e = torch.zeros(0, w.hand["D"])
+    fg.optimize_step_host(tiny.hand, tiny.scene, e, torch.zeros(0, w.hand["D"], device=_dev()), w.params, 0, 10, 1)
+
+
+def test_fp32_peak_kernel(fg):
+    """The FMA throughput kernel behind the ALU roofline's denominator: both forms run,
+    report their flops (blocks x 256 threads x iterations x 8 chains x 2 or 4), and
+    write one value per thread; invalid sizes are refused."""
+    from paper_2306_08132_gb300 import _lib
+    out = torch.full((4 * 256,), float("nan"), device=_dev())
+    f1 = fg.fp32_peak_launch(out, False, 100)
+    torch.cuda.synchronize()
+    assert f1 == 4 * 256 * 100 * 8 * 2 and torch.isfinite(out).all()
+    out.fill_(float("nan"))
+    f2 = fg.fp32_peak_launch(out, True, 100)
+    torch.cuda.synchronize()
+    assert f2 == 2 * f1 and torch.isfinite(out).all()
+    with pytest.raises(_lib.FgError):
+        fg.fp32_peak_launch(out, False, 0)
