@@ -876,12 +876,19 @@ def run_legs(fg, args, b, dev, world, flush, cand_steps):
     if args.mesh:
         mobjs = superquadric_meshes(w, args.mesh_res)
         mscene = fg.Scene([fg.Sdf.from_synth(m) for m in mobjs])
+        # the mesh kernels have their own best configuration (latency-bound searches
+        # favour more warps per SM): tune on this scene, put the main one back after
+        main_cfg = fg.fused_config_current()
+        mcfg, mcfg_ms = fg.autotune(b.hand, mscene, b.q0, w.params, 0, K, S_in, obj_of_cand=b.oc, reps=2)
         mms = timed(graphed(step_with(w.params, mscene)), max(3, args.steps // 4), 3, flush, world)
         m_ms = max_over_ranks(float(np.mean(mms)), world, dev)
+        cfgs = fg.fused_configs()
         out["mesh"] = {"ms_per_step": m_ms, "value": cand_steps / (m_ms / 1000.0), "unit": "candidate-steps/s",
                        "objects": "%d superquadric meshes, %d faces each, Phong SDF" % (len(mobjs),
                                                                                          len(mobjs[0]["faces"])),
-                       "fused_config": "%dw/%d/%dp" % fg.fused_configs()[fg.fused_config_current()]}
+                       "fused_config": "%dw/%d/%dp" % cfgs[mcfg],
+                       "autotune_ms": {"%dw/%d/%dp" % c: round(t, 4) for c, t in zip(cfgs, mcfg_ms)}}
+        fg.fused_config_select(main_cfg)
         if args.gs:                          # the paper's combination: Phong SDF of a mesh, Gauss-Seidel
             gms2 = timed(graphed(step_with(dict(w.params, gauss_seidel=1), mscene)), max(3, args.steps // 4), 3,
                          flush, world)

@@ -65,9 +65,20 @@ struct ObjDev {
   float phong_alpha;
   float phong_shift;             // bound on |r*_rho - r*| (the Phong point's distance from the flat closest point)
   const float4* bvh;             // 2 per node: (min, right child | first face), (max, face count; 0 = inner)
-  const float4* tri;             // 3 per face (BVH order): vertices a, b, c
-  const float4* face_nrm;        // 7 per face: vertex normals n_a, n_b, n_c, face normal, edge
-                                 // pseudonormals of (a,b), (b,c), (c,a)
+  // Per face, in BVH order; the w components hold ints (as bits) for the
+  // certified local search (mesh_local).
+  const float4* tri;             // 3: vertex k of (a, b, c); w: the face across edge (k, k+1)
+  const float4* face_nrm;        // 7: vertex normals of a, b, c (w: first edge of the vertex's
+                                 // ring); face normal (w: 1 for a face on the convex hull); edge
+                                 // pseudonormals of (a,b), (b,c), (c,a) (w: ring length of vertex
+                                 // k, bit 30 set when all its faces are hull faces)
+  const float4* wing;            // 3: vertex of the face across edge k opposite it (w: 1 when both
+                                 // faces of the edge are hull faces)
+  const float4* ring;            // per directed edge v -> u, grouped by v: u (w: the face holding it)
+  const int* start_face;         // [nz][ny][nx]: closest face at the nodes of a coarse grid
+  float start_org[3];            // its first node
+  float start_inv_h;             // 1 / node spacing
+  int start_n[3];                // nodes per axis
 };
 
 constexpr int kObjGrid = 0;
@@ -480,11 +491,14 @@ __device__ __forceinline__ float box_dist2(const float p[3], const float4& lo, c
 constexpr int kBvhStack = 64;
 
 // Closest face of the mesh to p: depth-first over the BVH, nearer child first,
-// subtrees farther than the best distance found so far skipped.
-__device__ inline int mesh_closest(const ObjDev& O, const float p[3], float bary[3], int& feature) {
+// subtrees farther than the best distance found so far skipped.  A face known to
+// be at squared distance init_d2 (init >= 0, with bary and feature set for it)
+// bounds the search from the start.
+__device__ inline int mesh_closest(const ObjDev& O, const float p[3], float bary[3], int& feature, int init = -1,
+                                   float init_d2 = 3.0e38f) {
   int stack[kBvhStack];
-  int sp = 0, node = 0, best = -1;
-  float best_d2 = 3.0e38f;
+  int sp = 0, node = 0, best = init;
+  float best_d2 = init >= 0 ? init_d2 : 3.0e38f;
   for (;;) {
     const float4 lo = __ldg(O.bvh + 2 * node), hi = __ldg(O.bvh + 2 * node + 1);
     const int count = __float_as_int(hi.w);
@@ -538,10 +552,13 @@ __device__ inline int mesh_closest(const ObjDev& O, const float p[3], float bary
 // not diverge.  The result per lane is the closest face, as in mesh_closest
 // (up to the choice among faces at exactly equal distance, which share the
 // closest edge or vertex).
-__device__ inline int mesh_closest_warp(const ObjDev& O, const float p[3], float bary[3], int& feature) {
+// Lanes with done set take part without searching (their result is -1); init
+// and init_d2 bound a lane's search as in mesh_closest.
+__device__ inline int mesh_closest_warp(const ObjDev& O, const float p[3], float bary[3], int& feature,
+                                        bool done = false, int init = -1, float init_d2 = 3.0e38f) {
   int stack[kBvhStack];
-  int sp = 0, node = 0, best = -1;
-  float best_d2 = 3.0e38f;
+  int sp = 0, node = 0, best = done ? -1 : init;
+  float best_d2 = done ? -1.0f : (init >= 0 ? init_d2 : 3.0e38f);
   for (;;) {
     const float4 lo = __ldg(O.bvh + 2 * node), hi = __ldg(O.bvh + 2 * node + 1);
     const int count = __float_as_int(hi.w);
@@ -594,12 +611,148 @@ __device__ inline int mesh_closest_warp(const ObjDev& O, const float p[3], float
   return best;
 }
 
+// ------------------------------------------------- certified local search
+//
+// The mesh solid lies inside the half-space of every face on its convex hull.  At
+// a point q of the surface whose incident faces are all hull faces, the hull's
+// tangent cone is the cone of the incident edges, so if p - q lies in its normal
+// cone ((p - q) . e <= 0 for every edge direction e out of q) q is the closest point
+// of the hull to p, and, being on the mesh, the closest point of the mesh.  The
+// search starts from the closest face at the nearest node of a coarse grid and
+// moves to a neighbouring face while one is strictly closer: across the edge
+// holding the closest point, or to the closest face around the vertex holding it.
+// A point inside the mesh, a feature off the hull, or a walk that stops without a
+// certificate is left to the BVH walk.  Edge directions within 1e-6 (relative) of
+// the cone's boundary pass: the closest point then moves by at most 1e-6 |p - q|.
+
+constexpr int kLocalHops = 16;
+
+// Index of the start face for p (-1 when p is not finite).
+__device__ __forceinline__ int mesh_start(const ObjDev& O, const float p[3]) {
+  if (!(isfinite(p[0]) && isfinite(p[1]) && isfinite(p[2]))) return -1;
+  int idx[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float u = (p[k] - O.start_org[k]) * O.start_inv_h;
+    idx[k] = __float2int_rn(fminf(fmaxf(u, 0.0f), (float)(O.start_n[k] - 1)));
+  }
+  return __ldg(O.start_face + (idx[2] * O.start_n[1] + idx[1]) * O.start_n[0] + idx[0]);
+}
+
+// Closest point of face f to p: squared distance, barycentric coordinates,
+// feature, the point, and the faces across the three edges.
+__device__ __forceinline__ float face_closest(const ObjDev& O, int f, const float p[3], float bary[3], int& feature,
+                                              float q[3], int nb[3]) {
+  const float4 A = __ldg(O.tri + 3 * f), B = __ldg(O.tri + 3 * f + 1), C = __ldg(O.tri + 3 * f + 2);
+  const float a[3] = {A.x, A.y, A.z}, b[3] = {B.x, B.y, B.z}, c[3] = {C.x, C.y, C.z};
+  nb[0] = __float_as_int(A.w);
+  nb[1] = __float_as_int(B.w);
+  nb[2] = __float_as_int(C.w);
+  const float d2 = closest_on_triangle(p, a, b, c, bary, feature);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) q[k] = bary[0] * a[k] + bary[1] * b[k] + bary[2] * c[k];
+  return d2;
+}
+
+// (p - q) . e > 0 beyond 1e-6 of |p - q| |e|: moving along e from q gets closer.
+__device__ __forceinline__ bool cone_violated(const float r[3], const float e[3]) {
+  const float re = dot3(r, e);
+  return re > 0.0f && re * re > 1e-12f * dot3(r, r) * dot3(e, e);
+}
+
+// The local search from face f: true when certified.  face, bary, feature and d2
+// describe the last face reached (face = -1 when p is too far for the test), the
+// closest one when certified.
+__device__ inline bool mesh_local(const ObjDev& O, const float p[3], int f, float bary[3], int& feature, float& d2,
+                                  int& face) {
+  float q[3];
+  int nb[3];
+  face = -1;
+  d2 = face_closest(O, f, p, bary, feature, q, nb);
+  if (!(d2 < 1e30f)) return false;
+  for (int hop = 0; hop < kLocalHops; ++hop) {
+    face = f;
+    const float r[3] = {p[0] - q[0], p[1] - q[1], p[2] - q[2]};
+    int g = -1;
+    if (feature == 0) {
+      const float4 N = __ldg(O.face_nrm + 7 * f + 3);
+      return (__float_as_int(N.w) & 1) && r[0] * N.x + r[1] * N.y + r[2] * N.z >= 0.0f;
+    } else if (feature <= 3) {
+      const int k = feature - 1;
+      const float4 W = __ldg(O.wing + 3 * f + k);
+      const float e[3] = {W.x - q[0], W.y - q[1], W.z - q[2]};
+      if (!cone_violated(r, e)) return __float_as_int(W.w) & 1;
+      g = nb[k];
+      float gb[3], gq[3];
+      int gf, gn[3];
+      const float gd2 = face_closest(O, g, p, gb, gf, gq, gn);
+      if (!(gd2 < d2)) return false;
+      d2 = gd2;
+      feature = gf;
+#pragma unroll
+      for (int t = 0; t < 3; ++t) {
+        bary[t] = gb[t];
+        q[t] = gq[t];
+        nb[t] = gn[t];
+      }
+      f = g;
+    } else {
+      const int k = feature - 4;
+      const int b0 = __float_as_int(__ldg(O.face_nrm + 7 * f + k).w);
+      const int info = __float_as_int(__ldg(O.face_nrm + 7 * f + 4 + k).w);
+      const int b1 = b0 + (info & ((1 << 30) - 1));
+      bool violated = false;
+#pragma unroll 2
+      for (int i = b0; i < b1; ++i) {
+        const float4 U = __ldg(O.ring + i);
+        const float e[3] = {U.x - q[0], U.y - q[1], U.z - q[2]};
+        violated |= cone_violated(r, e);
+      }
+      if (!violated) return (info >> 30) & 1;
+      // the closest of the other faces around the vertex
+      float bd2 = d2, bb[3] = {0.0f, 0.0f, 0.0f}, bq[3] = {0.0f, 0.0f, 0.0f};
+      int bf = 0, bn[3] = {0, 0, 0};
+      for (int i = b0; i < b1; ++i) {
+        const int h = __float_as_int(__ldg(O.ring + i).w);
+        if (h == f) continue;
+        float hb[3], hq[3];
+        int hf, hn[3];
+        const float hd2 = face_closest(O, h, p, hb, hf, hq, hn);
+        if (hd2 < bd2) {
+          bd2 = hd2;
+          g = h;
+          bf = hf;
+#pragma unroll
+          for (int t = 0; t < 3; ++t) {
+            bb[t] = hb[t];
+            bq[t] = hq[t];
+            bn[t] = hn[t];
+          }
+        }
+      }
+      if (g < 0) return false;
+      d2 = bd2;
+      feature = bf;
+#pragma unroll
+      for (int t = 0; t < 3; ++t) {
+        bary[t] = bb[t];
+        q[t] = bq[t];
+        nb[t] = bn[t];
+      }
+      f = g;
+    }
+  }
+  face = f;
+  return false;
+}
+
 // Signed distance from p to the flat mesh (sign by the closest feature's
 // pseudonormal, as in mesh_lookup); +inf when p is not finite.
 __device__ inline float mesh_flat_distance(const ObjDev& O, const float p[3]) {
-  float bary[3];
-  int feature = 0;
-  const int f = mesh_closest(O, p, bary, feature);
+  float bary[3], d2 = 3.0e38f;
+  int feature = 0, f = -1;
+  const int f0 = mesh_start(O, p);
+  if (!(f0 >= 0 && mesh_local(O, p, f0, bary, feature, d2, f))) f = mesh_closest(O, p, bary, feature, f, d2);
   if (f < 0) return 3.0e38f;
   const float4 A = __ldg(O.tri + 3 * f), B = __ldg(O.tri + 3 * f + 1), C = __ldg(O.tri + 3 * f + 2);
   const float q[3] = {bary[0] * A.x + bary[1] * B.x + bary[2] * C.x, bary[0] * A.y + bary[1] * B.y + bary[2] * C.y,
@@ -611,11 +764,18 @@ __device__ inline float mesh_flat_distance(const ObjDev& O, const float p[3]) {
   return dq[0] * N.x + dq[1] * N.y + dq[2] * N.z < 0.0f ? -dist : dist;
 }
 
-// Phong SDF at p for the 32 points of a warp (every lane must call it).
+// Phong SDF at p for the 32 points of a warp (every lane must call it): the
+// certified local search per lane, the warp's BVH walk for the lanes it leaves.
 __device__ inline void mesh_lookup(const ObjDev& O, const float p[3], SdfSample& s) {
-  float bary[3];
-  int feature = 0;
-  const int f = mesh_closest_warp(O, p, bary, feature);
+  float bary[3], fd2 = 3.0e38f;
+  int feature = 0, f = -1;
+  const int f0 = mesh_start(O, p);
+  const bool done = f0 >= 0 && mesh_local(O, p, f0, bary, feature, fd2, f);
+  if (!__all_sync(0xffffffffu, done)) {
+    // the lanes left search the BVH, bounded by the face their local search reached
+    const int wf = mesh_closest_warp(O, p, bary, feature, done, f, fd2);
+    if (!done) f = wf;
+  }
   if (f < 0) {                                  // p not finite: no face compares closer
     const float nan = __int_as_float(0x7fc00000);
     s.phi = s.curv = s.e = nan;

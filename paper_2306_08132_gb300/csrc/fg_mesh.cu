@@ -1,7 +1,9 @@
 // Mesh objects (Sec. III-B): a watertight triangle mesh queried directly through
 // a bounding volume hierarchy, with the Phong-smoothed SDF.  Everything here runs
-// on the host at object creation: validation, normals, pseudonormals and the
-// BVH; the device arrays are then copied once (one allocation per object).
+// on the host at object creation: validation, normals, pseudonormals, the BVH,
+// and the data of the certified local search (faces on the convex hull, face
+// adjacency, vertex rings, a coarse table of start faces); the device arrays are
+// then copied once (one allocation per object).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -20,6 +22,7 @@ namespace fg {
 namespace {
 
 constexpr int kLeafFaces = 4;
+constexpr int kStartCells = 32;    // nodes of the start-face table along the longest axis
 constexpr int kMaxDepth = 48;      // the device traversal keeps at most one entry per level
 
 struct Vec {
@@ -143,6 +146,105 @@ struct Builder {
   }
 };
 
+// Closest point of p on triangle (a, b, c) (double precision, Voronoi regions of
+// the vertices, edges and face): squared distance.
+double closest_sq(const Vec& p, const Vec& a, const Vec& b, const Vec& c) {
+  const Vec ab = sub(b, a), ac = sub(c, a), ap = sub(p, a), bp = sub(p, b), cp = sub(p, c);
+  const double d1 = dot(ab, ap), d2 = dot(ac, ap), d3 = dot(ab, bp), d4 = dot(ac, bp), d5 = dot(ab, cp),
+               d6 = dot(ac, cp);
+  const double vc = d1 * d4 - d3 * d2, vb = d5 * d2 - d1 * d6, va = d3 * d6 - d5 * d4;
+  Vec q;
+  if (d1 <= 0 && d2 <= 0) q = a;
+  else if (d3 >= 0 && d4 <= d3) q = b;
+  else if (vc <= 0 && d1 >= 0 && d3 <= 0) q = add(a, scale(ab, d1 / (d1 - d3)));
+  else if (d6 >= 0 && d5 <= d6) q = c;
+  else if (vb <= 0 && d2 >= 0 && d6 <= 0) q = add(a, scale(ac, d2 / (d2 - d6)));
+  else if (va <= 0 && d4 - d3 >= 0 && d5 - d6 >= 0) q = add(b, scale(sub(c, b), (d4 - d3) / ((d4 - d3) + (d5 - d6))));
+  else {
+    const double den = 1.0 / (va + vb + vc);
+    q = add(a, add(scale(ab, vb * den), scale(ac, vc * den)));
+  }
+  const Vec r = sub(p, q);
+  return dot(r, r);
+}
+
+inline double box_sq(const Vec& p, const Node& n) {
+  const double c[3] = {p.x, p.y, p.z};
+  double s = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    const double d = std::max(std::max((double)n.lo[k] - c[k], c[k] - (double)n.hi[k]), 0.0);
+    s += d * d;
+  }
+  return s;
+}
+
+// Closest face of p (position in BVH order), depth first over the host BVH.
+int closest_face(const Builder& B, const Vec& p) {
+  int stack[2 * kMaxDepth + 4];
+  int sp = 0, node = 0, best = -1;
+  double best_d2 = 1e300;
+  for (;;) {
+    const Node& n = B.nodes[node];
+    if (n.count > 0) {
+      for (int j = n.link; j < n.link + n.count; ++j) {
+        const int f = B.order[j];
+        const double d2 = closest_sq(p, B.V[B.F[3 * f]], B.V[B.F[3 * f + 1]], B.V[B.F[3 * f + 2]]);
+        if (d2 < best_d2) {
+          best_d2 = d2;
+          best = j;
+        }
+      }
+    } else {
+      const int l = node + 1, r = n.link;
+      const double dl = box_sq(p, B.nodes[l]), dr = box_sq(p, B.nodes[r]);
+      const int nearc = dl <= dr ? l : r, farc = dl <= dr ? r : l;
+      if (std::max(dl, dr) < best_d2) stack[sp++] = farc;
+      if (std::min(dl, dr) < best_d2) {
+        node = nearc;
+        continue;
+      }
+    }
+    bool found = false;
+    while (sp > 0) {
+      const int c = stack[--sp];
+      if (box_sq(p, B.nodes[c]) < best_d2) {
+        node = c;
+        found = true;
+        break;
+      }
+    }
+    if (!found) break;
+  }
+  return best;
+}
+
+// True when no vertex of the mesh lies more than tol outside the plane n . x = off
+// (the face is then on the boundary of the convex hull): a search over the BVH
+// boxes, whose highest corner bounds n . x of everything inside them.
+bool below_plane(const Builder& B, const Vec& n, double off, double tol) {
+  int stack[2 * kMaxDepth + 4];
+  int sp = 0;
+  stack[sp++] = 0;
+  while (sp > 0) {
+    const Node& nd = B.nodes[stack[--sp]];
+    const double ub = std::max(n.x * nd.lo[0], n.x * nd.hi[0]) + std::max(n.y * nd.lo[1], n.y * nd.hi[1]) +
+                      std::max(n.z * nd.lo[2], n.z * nd.hi[2]);
+    if (ub <= off + tol) continue;
+    if (nd.count > 0) {
+      for (int j = nd.link; j < nd.link + nd.count; ++j) {
+        const int f = B.order[j];
+        for (int k = 0; k < 3; ++k)
+          if (dot(n, B.V[B.F[3 * f + k]]) > off + tol) return false;
+      }
+    } else {
+      const int self = (int)(&nd - B.nodes.data());
+      stack[sp++] = self + 1;
+      stack[sp++] = nd.link;
+    }
+  }
+  return true;
+}
+
 fg_status mesh_invalid(const std::string& msg) {
   set_error("fg_sdf_create_mesh: " + msg);
   return FG_ERR_INVALID;
@@ -227,10 +329,58 @@ extern "C" fg_status fg_sdf_create_mesh(const float* vertices, int nv, const int
   Builder bld(V, F);
   bld.build(0, nf, 0);
   const size_t nn = bld.nodes.size();
-  std::vector<float4> buf(2 * nn + 3 * (size_t)nf + 7 * (size_t)nf);
+  std::vector<int> pos(nf);                       // BVH position of each face
+  for (int j = 0; j < nf; ++j) pos[bld.order[j]] = j;
+
+  // Certified local search.  A face is on the convex hull when no vertex lies more
+  // than tol outside its plane (tol far below float32 rounding of a coordinate);
+  // the mesh then lies inside the half-space of every hull face, so at a point of
+  // the surface whose incident faces are all hull faces the convex hull's tangent
+  // cone is the cone of the incident edges, and p - q in its normal cone proves q
+  // the closest point of the whole mesh (up to tol).
+  const double tol = 1e-9 * extent;
+  std::vector<char> hull(nf);
+  for (int f = 0; f < nf; ++f) hull[f] = below_plane(bld, fn[f], dot(fn[f], V[F[3 * f]]), tol);
+  // vertex rings: per directed edge v -> u, the neighbour u and the face holding the edge
+  std::vector<int> ring_start(nv + 1, 0);
+  for (int i = 0; i < 3 * nf; ++i) ++ring_start[F[i] + 1];
+  for (int v = 0; v < nv; ++v) ring_start[v + 1] += ring_start[v];
+  std::vector<int> ring_u(3 * (size_t)nf), ring_f(3 * (size_t)nf), fill(ring_start.begin(), ring_start.end() - 1);
+  std::vector<char> vert_hull(nv, 1);
+  for (int f = 0; f < nf; ++f)
+    for (int k = 0; k < 3; ++k) {
+      const int v = F[3 * f + k];
+      ring_u[fill[v]] = F[3 * f + (k + 1) % 3];
+      ring_f[fill[v]++] = f;
+      if (!hull[f]) vert_hull[v] = 0;
+    }
+  // start faces: the closest face at the nodes of a coarse grid over the mesh's box
+  // grown by its largest side on every side
+  double blo[3] = {1e300, 1e300, 1e300}, bhi[3] = {-1e300, -1e300, -1e300};
+  for (const Vec& p : V) {
+    const double c[3] = {p.x, p.y, p.z};
+    for (int a = 0; a < 3; ++a) {
+      blo[a] = std::min(blo[a], c[a]);
+      bhi[a] = std::max(bhi[a], c[a]);
+    }
+  }
+  const double side = std::max(bhi[0] - blo[0], std::max(bhi[1] - blo[1], bhi[2] - blo[2]));
+  const double sh = 3.0 * side / (kStartCells - 1);
+  int sn[3];
+  for (int a = 0; a < 3; ++a) {
+    blo[a] -= side;
+    sn[a] = std::min(kStartCells, (int)std::ceil((bhi[a] - blo[a] + side) / sh) + 1);
+  }
+  const size_t nstart = (size_t)sn[0] * sn[1] * sn[2];
+
+  const size_t n_wing = 3 * (size_t)nf, n_ring = 3 * (size_t)nf, n_start = (nstart + 3) / 4;
+  std::vector<float4> buf(2 * nn + 3 * (size_t)nf + 7 * (size_t)nf + n_wing + n_ring + n_start);
   float4* bvh = buf.data();
   float4* tri = bvh + 2 * nn;
   float4* nrm = tri + 3 * (size_t)nf;
+  float4* wing = nrm + 7 * (size_t)nf;
+  float4* ring = wing + n_wing;
+  float4* start = ring + n_ring;
   for (size_t i = 0; i < nn; ++i) {
     const Node& n = bld.nodes[i];
     int link = n.link, count = n.count;
@@ -240,16 +390,44 @@ extern "C" fg_status fg_sdf_create_mesh(const float* vertices, int nv, const int
     bvh[2 * i] = make_float4(n.lo[0], n.lo[1], n.lo[2], lw);
     bvh[2 * i + 1] = make_float4(n.hi[0], n.hi[1], n.hi[2], hw);
   }
-  auto f4 = [](const Vec& v) { return make_float4((float)v.x, (float)v.y, (float)v.z, 0.0f); };
+  auto bits = [](int x) {
+    float y;
+    std::memcpy(&y, &x, 4);
+    return y;
+  };
+  auto f4 = [](const Vec& v, float w) { return make_float4((float)v.x, (float)v.y, (float)v.z, w); };
   for (int j = 0; j < nf; ++j) {
     const int f = bld.order[j];
     for (int k = 0; k < 3; ++k) {
-      tri[3 * j + k] = make_float4(vertices[3 * F[3 * f + k]], vertices[3 * F[3 * f + k] + 1],
-                                   vertices[3 * F[3 * f + k] + 2], 0.0f);
-      nrm[7 * j + k] = f4(vn[F[3 * f + k]]);
-      nrm[7 * j + 4 + k] = f4(unit(add(fn[f], fn[across[3 * f + k]])));   // edge (k, k+1)
+      const int v = F[3 * f + k], g = across[3 * f + k];
+      // vertex k and the face across edge (k, k+1)
+      tri[3 * j + k] = make_float4(vertices[3 * v], vertices[3 * v + 1], vertices[3 * v + 2], bits(pos[g]));
+      // vertex normal and the ring of vertex k: first edge; edge pseudonormal and the
+      // ring's length, bit 30 set when every face around the vertex is a hull face
+      nrm[7 * j + k] = f4(vn[v], bits(ring_start[v]));
+      const int len = ring_start[v + 1] - ring_start[v];
+      nrm[7 * j + 4 + k] = f4(unit(add(fn[f], fn[g])), bits(len | (vert_hull[v] ? 1 << 30 : 0)));
+      // the vertex of g opposite edge (k, k+1); 1 when both faces are hull faces
+      const int u = F[3 * f + (k + 1) % 3];
+      int opp = F[3 * g];
+      for (int t = 0; t < 3; ++t)
+        if (F[3 * g + t] != v && F[3 * g + t] != u) opp = F[3 * g + t];
+      wing[3 * j + k] = make_float4(vertices[3 * opp], vertices[3 * opp + 1], vertices[3 * opp + 2],
+                                    bits(hull[f] && hull[g] ? 1 : 0));
     }
-    nrm[7 * j + 3] = f4(fn[f]);
+    nrm[7 * j + 3] = f4(fn[f], bits(hull[f] ? 1 : 0));   // face normal; 1 for a hull face
+  }
+  for (size_t i = 0; i < n_ring; ++i) {
+    const int u = ring_u[i];
+    ring[i] = make_float4(vertices[3 * u], vertices[3 * u + 1], vertices[3 * u + 2], bits(pos[ring_f[i]]));
+  }
+  {
+    std::vector<int> sf(nstart);
+    for (int z = 0; z < sn[2]; ++z)
+      for (int y = 0; y < sn[1]; ++y)
+        for (int x = 0; x < sn[0]; ++x)
+          sf[((size_t)z * sn[1] + y) * sn[0] + x] = closest_face(bld, Vec{blo[0] + sh * x, blo[1] + sh * y, blo[2] + sh * z});
+    std::memcpy(start, sf.data(), sizeof(int) * nstart);
   }
   fg_sdf* s = new (std::nothrow) fg_sdf;
   if (!s) return FG_ERR_OOM;
@@ -270,8 +448,16 @@ extern "C" fg_status fg_sdf_create_mesh(const float* vertices, int nv, const int
   o.phong_alpha = phong_alpha;
   o.phong_shift = (float)(shift * (1.0 + 1e-5)) + 1e-7f;
   o.bvh = dev;
-  o.tri = dev + 2 * nn;
-  o.face_nrm = dev + 2 * nn + 3 * (size_t)nf;
+  o.tri = dev + (tri - bvh);
+  o.face_nrm = dev + (nrm - bvh);
+  o.wing = dev + (wing - bvh);
+  o.ring = dev + (ring - bvh);
+  o.start_face = reinterpret_cast<const int*>(dev + (start - bvh));
+  for (int a = 0; a < 3; ++a) {
+    o.start_org[a] = (float)blo[a];
+    o.start_n[a] = sn[a];
+  }
+  o.start_inv_h = (float)(1.0 / sh);
   o.inv_mass = 1.0f / mass;
   o.inv_inertia = 1.0f / inertia;
   o.h = 1.0f;          // unused by mesh queries

@@ -94,10 +94,20 @@ def superquadric_mesh(semi_axes, eps1: float, eps2: float, n_lat: int, n_lon: in
     for j in range(n_lon):
         F.append((0, ring(1, j + 1), ring(1, j)))
         F.append((top, ring(n_lat - 1, j), ring(n_lat - 1, j + 1)))
+    V32 = V.astype(np.float32).astype(np.float64)
     for i in range(1, n_lat - 1):
         for j in range(n_lon):
             a0, a1, b0, b1 = ring(i, j), ring(i, j + 1), ring(i + 1, j), ring(i + 1, j + 1)
-            F += [(a0, a1, b1), (a0, b1, b0)]
+            # a quad of four sampled points is rarely planar: split it along the diagonal
+            # that folds outwards (the fourth vertex below the first triangle's plane, on
+            # the float32 coordinates), so that the mesh of a convex surface is convex
+            n = np.cross(V32[a1] - V32[a0], V32[b1] - V32[a0])
+            if n @ (V32[a0] + V32[a1] + V32[b1]) < 0:
+                n = -n
+            if n @ (V32[b0] - V32[a0]) <= 0:
+                F += [(a0, a1, b1), (a0, b1, b0)]
+            else:
+                F += [(a0, a1, b0), (a1, b1, b0)]
     return _pack("superquadric_mesh", V, _orient_outward(V, F),
                  {"semi_axes": a.tolist(), "eps1": eps1, "eps2": eps2, "n_lat": n_lat, "n_lon": n_lon})
 

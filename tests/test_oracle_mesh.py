@@ -206,3 +206,24 @@ def test_sign_on_a_non_convex_mesh_matches_the_winding_number(n_major, n_minor):
     # the hole: points on the axis are outside
     axis = np.stack([np.zeros(20), np.zeros(20), np.linspace(-r, r, 20)], -1)
     assert (MS.mesh_query(mesh, axis)["sign"] > 0).all()
+
+
+@pytest.mark.parametrize("eps", [(0.5, 0.5), (1.0, 1.0), (0.7, 1.3), (1.5, 1.5)])
+def test_superquadric_meshes_of_convex_surfaces_are_convex(eps):
+    """The generator splits each latitude/longitude quad along its outward-folding
+    diagonal, so the mesh of a convex superquadric (exponents <= 2) is convex on its
+    float32 coordinates: no vertex lies outside any face's plane beyond double
+    rounding.  The library's certified local search relies on faces on the hull."""
+    m = SM.superquadric_mesh((0.05, 0.03, 0.04), eps[0], eps[1], 24, 48)
+    V = m["vertices"].astype(np.float64)
+    F = np.asarray(m["faces"])
+    n = np.cross(V[F[:, 1]] - V[F[:, 0]], V[F[:, 2]] - V[F[:, 0]])
+    n /= np.linalg.norm(n, axis=1)[:, None]
+    gap = (V @ n.T - (n * V[F[:, 0]]).sum(1)[None, :]).max(axis=0)
+    assert gap.max() <= 1e-12 * np.abs(V).max(), gap.max()
+    # the quads are not planar, so the diagonal matters: the first quad's fourth
+    # vertex lies off the plane of its other three
+    n_lon = 48
+    a0, a1, b0, b1 = 1, 2, 1 + n_lon, 2 + n_lon
+    t = np.cross(V[a1] - V[a0], V[b1] - V[a0])
+    assert t @ (V[b0] - V[a0]) != 0
