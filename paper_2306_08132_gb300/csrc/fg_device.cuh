@@ -490,11 +490,15 @@ __device__ __forceinline__ float box_dist2(const float p[3], const float4& lo, c
 
 constexpr int kBvhStack = 64;
 
+// The mesh searches below are called out of line (one copy per kernel): inlined
+// at every lookup site of the fused kernel they overflowed the instruction cache
+// (ncu: 42% of the stall samples waiting for an instruction fetch).
+
 // Closest face of the mesh to p: depth-first over the BVH, nearer child first,
 // subtrees farther than the best distance found so far skipped.  A face known to
 // be at squared distance init_d2 (init >= 0, with bary and feature set for it)
 // bounds the search from the start.
-__device__ inline int mesh_closest(const ObjDev& O, const float p[3], float bary[3], int& feature, int init = -1,
+static __device__ __noinline__ int mesh_closest(const ObjDev& O, const float p[3], float bary[3], int& feature, int init = -1,
                                    float init_d2 = 3.0e38f) {
   int stack[kBvhStack];
   int sp = 0, node = 0, best = init;
@@ -554,7 +558,7 @@ __device__ inline int mesh_closest(const ObjDev& O, const float p[3], float bary
 // closest edge or vertex).
 // Lanes with done set take part without searching (their result is -1); init
 // and init_d2 bound a lane's search as in mesh_closest.
-__device__ inline int mesh_closest_warp(const ObjDev& O, const float p[3], float bary[3], int& feature,
+static __device__ __noinline__ int mesh_closest_warp(const ObjDev& O, const float p[3], float bary[3], int& feature,
                                         bool done = false, int init = -1, float init_d2 = 3.0e38f) {
   int stack[kBvhStack];
   int sp = 0, node = 0, best = done ? -1 : init;
@@ -620,10 +624,12 @@ __device__ inline int mesh_closest_warp(const ObjDev& O, const float p[3], float
 // of the hull to p, and, being on the mesh, the closest point of the mesh.  The
 // search starts from the closest face at the nearest node of a coarse grid and
 // moves to a neighbouring face while one is strictly closer: across the edge
-// holding the closest point, or to the closest face around the vertex holding it.
-// A point inside the mesh, a feature off the hull, or a walk that stops without a
-// certificate is left to the BVH walk.  Edge directions within 1e-6 (relative) of
-// the cone's boundary pass: the closest point then moves by at most 1e-6 |p - q|.
+// holding the closest point, or, from a vertex, to the closer of the two faces on
+// the edge along which the distance falls fastest.  A point inside the mesh, a
+// feature off the hull, or a walk that stops without a certificate is left to the
+// BVH walk.  Edge directions within 1e-6 (relative) of the cone's boundary pass
+// (cone_violated); moves are taken by the gain in squared distance computed from
+// the difference of the two points (closer_by).
 
 constexpr int kLocalHops = 16;
 
@@ -641,7 +647,7 @@ __device__ __forceinline__ int mesh_start(const ObjDev& O, const float p[3]) {
 
 // Closest point of face f to p: squared distance, barycentric coordinates,
 // feature, the point, and the faces across the three edges.
-__device__ __forceinline__ float face_closest(const ObjDev& O, int f, const float p[3], float bary[3], int& feature,
+static __device__ __noinline__ float face_closest(const ObjDev& O, int f, const float p[3], float bary[3], int& feature,
                                               float q[3], int nb[3]) {
   const float4 A = __ldg(O.tri + 3 * f), B = __ldg(O.tri + 3 * f + 1), C = __ldg(O.tri + 3 * f + 2);
   const float a[3] = {A.x, A.y, A.z}, b[3] = {B.x, B.y, B.z}, c[3] = {C.x, C.y, C.z};
@@ -655,15 +661,24 @@ __device__ __forceinline__ float face_closest(const ObjDev& O, int f, const floa
 }
 
 // (p - q) . e > 0 beyond 1e-6 of |p - q| |e|: moving along e from q gets closer.
+// Below that the closest point along e is within 1e-6 |p - q| of q.
 __device__ __forceinline__ bool cone_violated(const float r[3], const float e[3]) {
   const float re = dot3(r, e);
   return re > 0.0f && re * re > 1e-12f * dot3(r, r) * dot3(e, e);
 }
 
+// |p - q|^2 - |p - q'|^2 = (q' - q) . (r + r'), r = p - q, r' = p - q': the gain of
+// moving from q to q', from the difference of the points (no cancellation between
+// two nearly equal squared distances, so float32 resolves gains far below |p - q|^2).
+__device__ __forceinline__ float closer_by(const float q[3], const float r[3], const float q2[3], const float p[3]) {
+  return (q2[0] - q[0]) * (r[0] + p[0] - q2[0]) + (q2[1] - q[1]) * (r[1] + p[1] - q2[1]) +
+         (q2[2] - q[2]) * (r[2] + p[2] - q2[2]);
+}
+
 // The local search from face f: true when certified.  face, bary, feature and d2
 // describe the last face reached (face = -1 when p is too far for the test), the
 // closest one when certified.
-__device__ inline bool mesh_local(const ObjDev& O, const float p[3], int f, float bary[3], int& feature, float& d2,
+static __device__ __noinline__ bool mesh_local(const ObjDev& O, const float p[3], int f, float bary[3], int& feature, float& d2,
                                   int& face) {
   float q[3];
   int nb[3];
@@ -686,7 +701,7 @@ __device__ inline bool mesh_local(const ObjDev& O, const float p[3], int f, floa
       float gb[3], gq[3];
       int gf, gn[3];
       const float gd2 = face_closest(O, g, p, gb, gf, gq, gn);
-      if (!(gd2 < d2)) return false;
+      if (!(closer_by(q, r, gq, p) > 0.0f)) return false;
       d2 = gd2;
       feature = gf;
 #pragma unroll
@@ -700,45 +715,54 @@ __device__ inline bool mesh_local(const ObjDev& O, const float p[3], int f, floa
       const int k = feature - 4;
       const int b0 = __float_as_int(__ldg(O.face_nrm + 7 * f + k).w);
       const int info = __float_as_int(__ldg(O.face_nrm + 7 * f + 4 + k).w);
-      const int b1 = b0 + (info & ((1 << 30) - 1));
-      bool violated = false;
+      const int m = info & ((1 << 29) - 1);
+      // the edge out of the vertex along which the distance falls fastest
+      int bi = -1;
+      float bre = 0.0f, be2 = 1.0f;
 #pragma unroll 2
-      for (int i = b0; i < b1; ++i) {
-        const float4 U = __ldg(O.ring + i);
+      for (int i = 0; i < m; ++i) {
+        const float4 U = __ldg(O.ring + b0 + i);
         const float e[3] = {U.x - q[0], U.y - q[1], U.z - q[2]};
-        violated |= cone_violated(r, e);
+        if (cone_violated(r, e)) {
+          const float re = dot3(r, e), e2 = dot3(e, e);
+          if (bi < 0 || re * re * be2 > bre * bre * e2) {
+            bi = i;
+            bre = re;
+            be2 = e2;
+          }
+        }
       }
-      if (!violated) return (info >> 30) & 1;
-      // the closest of the other faces around the vertex
-      float bd2 = d2, bb[3] = {0.0f, 0.0f, 0.0f}, bq[3] = {0.0f, 0.0f, 0.0f};
-      int bf = 0, bn[3] = {0, 0, 0};
-      for (int i = b0; i < b1; ++i) {
-        const int h = __float_as_int(__ldg(O.ring + i).w);
+      if (bi < 0) return (info >> 30) & 1;
+      if (!((info >> 29) & 1)) return false;
+      // the two faces on that edge: ring entries bi and bi - 1 (fan order)
+      const int h0 = __float_as_int(__ldg(O.ring + b0 + bi).w);
+      const int h1 = __float_as_int(__ldg(O.ring + b0 + (bi > 0 ? bi - 1 : m - 1)).w);
+      float bd2 = d2, gain = 0.0f, bq[3] = {q[0], q[1], q[2]};
+#pragma unroll 1
+      for (int t2 = 0; t2 < 2; ++t2) {
+        const int h = t2 == 0 ? h0 : h1;
         if (h == f) continue;
         float hb[3], hq[3];
         int hf, hn[3];
         const float hd2 = face_closest(O, h, p, hb, hf, hq, hn);
-        if (hd2 < bd2) {
+        const float gh = closer_by(q, r, hq, p);
+        if (gh > gain) {
+          gain = gh;
           bd2 = hd2;
           g = h;
-          bf = hf;
+          feature = hf;
 #pragma unroll
           for (int t = 0; t < 3; ++t) {
-            bb[t] = hb[t];
+            bary[t] = hb[t];
             bq[t] = hq[t];
-            bn[t] = hn[t];
+            nb[t] = hn[t];
           }
         }
       }
       if (g < 0) return false;
-      d2 = bd2;
-      feature = bf;
 #pragma unroll
-      for (int t = 0; t < 3; ++t) {
-        bary[t] = bb[t];
-        q[t] = bq[t];
-        nb[t] = bn[t];
-      }
+      for (int t = 0; t < 3; ++t) q[t] = bq[t];
+      d2 = bd2;
       f = g;
     }
   }
@@ -766,7 +790,7 @@ __device__ inline float mesh_flat_distance(const ObjDev& O, const float p[3]) {
 
 // Phong SDF at p for the 32 points of a warp (every lane must call it): the
 // certified local search per lane, the warp's BVH walk for the lanes it leaves.
-__device__ inline void mesh_lookup(const ObjDev& O, const float p[3], SdfSample& s) {
+static __device__ __noinline__ void mesh_lookup(const ObjDev& O, const float p[3], SdfSample& s) {
   float bary[3], fd2 = 3.0e38f;
   int feature = 0, f = -1;
   const int f0 = mesh_start(O, p);

@@ -354,6 +354,37 @@ extern "C" fg_status fg_sdf_create_mesh(const float* vertices, int nv, const int
       ring_f[fill[v]++] = f;
       if (!hull[f]) vert_hull[v] = 0;
     }
+  // Each ring in fan order: entry i's face (v, u_i, u_(i+1)) holds v -> u_i, so the two
+  // faces on edge (v, u_i) are the faces of entries i and i - 1.  A vertex whose faces
+  // form more than one fan keeps its ring unordered.
+  std::vector<char> vert_fan(nv, 1);
+  {
+    std::vector<int> ou, of;
+    for (int v = 0; v < nv; ++v) {
+      const int b = ring_start[v], m = ring_start[v + 1] - b;
+      if (m == 0) continue;
+      ou.assign(1, ring_u[b]);
+      of.assign(1, ring_f[b]);
+      for (int step = 1; step < m; ++step) {
+        const int f = of.back(), u = ou.back();
+        int w = -1;
+        for (int t = 0; t < 3; ++t)
+          if (F[3 * f + t] == u) w = F[3 * f + (t + 1) % 3];
+        int next = -1;
+        for (int i = b; i < b + m; ++i)
+          if (ring_u[i] == w) next = i;
+        if (next < 0 || ring_f[next] == of[0]) break;
+        ou.push_back(ring_u[next]);
+        of.push_back(ring_f[next]);
+      }
+      if ((int)ou.size() == m) {
+        std::copy(ou.begin(), ou.end(), ring_u.begin() + b);
+        std::copy(of.begin(), of.end(), ring_f.begin() + b);
+      } else {
+        vert_fan[v] = 0;
+      }
+    }
+  }
   // start faces: the closest face at the nodes of a coarse grid over the mesh's box
   // grown by its largest side on every side
   double blo[3] = {1e300, 1e300, 1e300}, bhi[3] = {-1e300, -1e300, -1e300};
@@ -403,10 +434,12 @@ extern "C" fg_status fg_sdf_create_mesh(const float* vertices, int nv, const int
       // vertex k and the face across edge (k, k+1)
       tri[3 * j + k] = make_float4(vertices[3 * v], vertices[3 * v + 1], vertices[3 * v + 2], bits(pos[g]));
       // vertex normal and the ring of vertex k: first edge; edge pseudonormal and the
-      // ring's length, bit 30 set when every face around the vertex is a hull face
+      // ring's length, bit 30 set when every face around the vertex is a hull face,
+      // bit 29 when the ring is in fan order
       nrm[7 * j + k] = f4(vn[v], bits(ring_start[v]));
       const int len = ring_start[v + 1] - ring_start[v];
-      nrm[7 * j + 4 + k] = f4(unit(add(fn[f], fn[g])), bits(len | (vert_hull[v] ? 1 << 30 : 0)));
+      nrm[7 * j + 4 + k] =
+          f4(unit(add(fn[f], fn[g])), bits(len | (vert_hull[v] ? 1 << 30 : 0) | (vert_fan[v] ? 1 << 29 : 0)));
       // the vertex of g opposite edge (k, k+1); 1 when both faces are hull faces
       const int u = F[3 * f + (k + 1) % 3];
       int opp = F[3 * g];
