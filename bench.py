@@ -725,13 +725,13 @@ def main():
             # the other forms of the step on this batch: Gauss-Seidel, T-step (T = 1), mesh objects, quality
             sub_args = argparse.Namespace(**dict(vars(args), tstep="1", gs=True, quality=True, mesh=True,
                                                  order_quality=False, serving=0))
-            sub.update(run_legs(fg, sub_args, b2, dev, 1, flush, w2.B * S_in))
+            sub.update(run_legs(fg, sub_args, b2, dev, 1, flush, w2.B * S_in, peak))
             for k in ("order_quality", "serving", "serving_sweep"):
                 sub.pop(k, None)
         del b2
         fg.autotune(b.hand, b.scene, b.q0, w.params, 0, K, S_in, obj_of_cand=b.oc, reps=3)   # back to the main workload
 
-    legs = run_legs(fg, args, b, dev, world, flush, cand_steps)
+    legs = run_legs(fg, args, b, dev, world, flush, cand_steps, peak)
     grid_bytes = int(sum_over_ranks(part["grid_bytes"], world, dev))
 
     # multi-GPU: one optimisation step of every rank's candidates, gathered on rank 0
@@ -818,7 +818,7 @@ def superquadric_meshes(w, mesh_res):
     return out
 
 
-def run_legs(fg, args, b, dev, world, flush, cand_steps):
+def run_legs(fg, args, b, dev, world, flush, cand_steps, peak=None):
     """The optional legs on the bound workload (each None unless asked for)."""
     import torch
     w, K, S_in = b.w, b.w.steps, args.inner_steps
@@ -887,7 +887,20 @@ def run_legs(fg, args, b, dev, world, flush, cand_steps):
                        "objects": "%d superquadric meshes, %d faces each, Phong SDF" % (len(mobjs),
                                                                                          len(mobjs[0]["faces"])),
                        "fused_config": "%dw/%d/%dp" % cfgs[mcfg],
-                       "autotune_ms": {"%dw/%d/%dp" % c: round(t, 4) for c, t in zip(cfgs, mcfg_ms)}}
+                       "autotune_ms": {"%dw/%d/%dp" % c: round(t, 4) for c, t in zip(cfgs, mcfg_ms)},
+                       "roofline": None}
+        mprof = load_profile("fused_step_mesh", w.name)
+        if peak is not None and mprof and "executed_fp32_flops_per_point_step" in mprof:
+            # no operation count of the method exists for a BVH / local search (its work depends
+            # on the geometry): the FP32 operations the kernel executes, from ncu, per point-step
+            x = mprof["executed_fp32_flops_per_point_step"]
+            ach = x * units / (m_ms / 1e3) / 1e12
+            out["mesh"]["roofline"] = {"bound": "alu", "achieved": ach, "peak": peak["tflops"], "unit": "TFLOP/s",
+                                       "frac": ach / peak["tflops"], "flops_per_point_step": x,
+                                       "basis": "executed FP32 operations per point-step (FADD, FMUL 1, FFMA 2) "
+                                                "from ncu on this launch, the mesh search included; of measured "
+                                                "FP32 peak",
+                                       "traffic": mprof["traffic"]}
         fg.fused_config_select(main_cfg)
         if args.gs:                          # the paper's combination: Phong SDF of a mesh, Gauss-Seidel
             gms2 = timed(graphed(step_with(dict(w.params, gauss_seidel=1), mscene)), max(3, args.steps // 4), 3,
