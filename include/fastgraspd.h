@@ -184,9 +184,14 @@ fg_status fg_sdf_destroy(fg_sdf* sdf);
  *             outward normal; every edge shared by exactly two faces (watertight,
  *             consistently oriented), no zero-area face.
  * The handle is an fg_sdf: fg_sdf_query, scenes, fg_contact_wrench, fg_loss_and_grad,
- * fg_optimize_step and the request queue take it; the T-step metric and the
- * per-stage form take grid objects only (FG_ERR_INVALID).  Built on the host,
- * copied to the current device (synchronous).
+ * fg_optimize_step (both projection orders and the T-step metric) and the request
+ * queue take it; the per-stage form takes grid objects only (FG_ERR_INVALID).
+ * Built on the host, copied to the current device (synchronous): validation,
+ * normals and pseudonormals, the BVH, and for the certified local search that
+ * answers most queries before the BVH walk, the faces on the convex hull, the
+ * vertex rings in fan order and a table of start faces (the closest face at the
+ * nodes of a 32-node grid over the mesh's box grown by its largest side).  Device
+ * memory: about 280 bytes per face plus up to 128 KB.
  * Errors: FG_ERR_INVALID (with the reason), FG_ERR_OOM, FG_ERR_CUDA. */
 fg_status fg_sdf_create_mesh(const float* host_vertices, int n_vertices, const int* host_faces, int n_faces,
                              float phong_alpha, float mass, float inertia, fg_sdf** out);

@@ -13,6 +13,7 @@
 #include <new>
 #include <string>
 #include <unordered_map>
+#include <utility>
 #include <vector>
 
 #include "fg_internal.h"
@@ -360,9 +361,13 @@ extern "C" fg_status fg_sdf_create_mesh(const float* vertices, int nv, const int
   std::vector<char> vert_fan(nv, 1);
   {
     std::vector<int> ou, of;
+    std::vector<std::pair<int, int>> by_u;       // (neighbour, entry) of the current ring, sorted
     for (int v = 0; v < nv; ++v) {
       const int b = ring_start[v], m = ring_start[v + 1] - b;
       if (m == 0) continue;
+      by_u.clear();
+      for (int i = b; i < b + m; ++i) by_u.emplace_back(ring_u[i], i);
+      std::sort(by_u.begin(), by_u.end());
       ou.assign(1, ring_u[b]);
       of.assign(1, ring_f[b]);
       for (int step = 1; step < m; ++step) {
@@ -370,9 +375,8 @@ extern "C" fg_status fg_sdf_create_mesh(const float* vertices, int nv, const int
         int w = -1;
         for (int t = 0; t < 3; ++t)
           if (F[3 * f + t] == u) w = F[3 * f + (t + 1) % 3];
-        int next = -1;
-        for (int i = b; i < b + m; ++i)
-          if (ring_u[i] == w) next = i;
+        auto it = std::lower_bound(by_u.begin(), by_u.end(), std::make_pair(w, -1));
+        const int next = it != by_u.end() && it->first == w ? it->second : -1;
         if (next < 0 || ring_f[next] == of[0]) break;
         ou.push_back(ring_u[next]);
         of.push_back(ring_f[next]);
