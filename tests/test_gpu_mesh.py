@@ -77,6 +77,72 @@ def test_mesh_query_matches_oracle(fg, name):
         assert np.median(gerr) < 1e-5
 
 
+def _cone_mesh(n=200, r=0.04, h=0.06):
+    """A cone of n side faces and n base faces: its apex and base centre have valence n."""
+    V = [(0.0, 0.0, 2 * h / 3), (0.0, 0.0, -h / 3)]
+    V += [(r * np.cos(2 * np.pi * i / n), r * np.sin(2 * np.pi * i / n), -h / 3) for i in range(n)]
+    F = []
+    for i in range(n):
+        a, b = 2 + i, 2 + (i + 1) % n
+        F += [(0, a, b), (1, b, a)]
+    return {"vertices": np.asarray(V, np.float32), "faces": np.asarray(F, np.int32), "mass": 1.0,
+            "inertia": 0.4 * r * r}
+
+
+def _bowtie_mesh(s=0.03):
+    """Two tetrahedra that share one vertex and no edge: the shared vertex's faces form
+    two fans (a vertex that is not manifold)."""
+    V = np.array([(0, 0, 0), (s, 0, s), (s, s, -s), (s, -s, -s),
+                  (-s, 0, s), (-s, -s, -s), (-s, s, -s)], dtype=np.float64)
+    F = [(0, 1, 2), (0, 2, 3), (0, 3, 1), (1, 3, 2), (0, 4, 5), (0, 5, 6), (0, 6, 4), (4, 6, 5)]
+    F = np.asarray(F)
+    for t in range(len(F)):                      # orient each face away from its tetrahedron's centroid
+        A, B, C = V[F[t]]
+        cen = V[[1, 2, 3]].mean(0) if F[t][1] in (1, 2, 3) or F[t][0] in (1, 2, 3) else V[[4, 5, 6]].mean(0)
+        if np.cross(B - A, C - A) @ ((A + B + C) / 3 - cen) < 0:
+            F[t] = F[t][[0, 2, 1]]
+    return {"vertices": V.astype(np.float32), "faces": F.astype(np.int32), "mass": 1.0, "inertia": 4e-4}
+
+
+@pytest.mark.parametrize("name", ["cone200", "bowtie"])
+def test_mesh_query_high_valence_and_non_manifold_vertices(fg, name):
+    """The local search scans a vertex's whole ring (valence 200 at the cone's apex and base
+    centre) and leaves a vertex whose faces form two fans (the bow-tie's shared vertex) to
+    the BVH walk: values and signs match the oracle as in the query test, and so do the
+    bow-tie's directions.  On the flat meshes (alpha = 0), and without the cone's
+    directions: its side faces are long and thin near the apex, where float32 rounding of
+    the closest point on the right face already exceeds the query tolerances (the Phong
+    value by 1.5x, the direction at 37 of these 2,000 points, both computed in float32
+    on the oracle's own face choice), which says nothing about the search."""
+    m = _cone_mesh() if name == "cone200" else _bowtie_mesh()
+    sdf = fg.Sdf.from_mesh(m["vertices"], m["faces"], m["mass"], m["inertia"], phong_alpha=0.0)
+    ref_mesh = MS.MeshObj.from_synth(m, alpha=0.0)
+    rng = np.random.default_rng(5)
+    V = m["vertices"].astype(np.float64)
+    # far points, points around the vertices of highest valence, and points near every vertex
+    far = rng.normal(size=(800, 3)) * 0.08
+    hub = V[[0, 1]] if name == "cone200" else V[[0]]
+    near_hub = hub[rng.integers(0, len(hub), 800)] + rng.normal(size=(800, 3)) * 0.01
+    near_v = V[rng.integers(0, len(V), 400)] + rng.normal(size=(400, 3)) * 0.004
+    p32 = np.concatenate([far, near_hub, near_v]).astype(np.float32)
+    phi, g = fg.sdf_query(sdf, torch.tensor(p32.T.copy(), device=_dev()), 0.0)
+    res = MS.mesh_query(ref_mesh, p32.astype(np.float64))
+    diff = p32.astype(np.float64) - res["q_rho"]
+    d = np.linalg.norm(diff, axis=1)
+    rho = res["sign"] * d
+    grad = res["sign"][:, None] * diff / d[:, None]
+    clean = (res["gap"] > 1e-6) & (res["dist"] > 1e-6) & (d > 1e-6)
+    assert clean.sum() >= 0.8 * len(p32)
+    got = phi.cpu().numpy().astype(np.float64)
+    err = np.abs(got - rho)[clean]
+    assert (err < 2e-6 + 1e-4 * d[clean]).all(), (name, err.max())
+    assert np.array_equal((got < 0)[clean], (rho < 0)[clean]), name
+    if name == "bowtie":
+        cdir = clean & ~_direction_ambiguous(ref_mesh, p32.astype(np.float64), res)
+        gerr = np.abs(g.cpu().numpy().T.astype(np.float64) - grad).max(axis=1)[cdir]
+        assert (gerr < 5e-4 + 2e-8 / d[cdir]).all(), (name, gerr.max())
+
+
 def _torus_points(m, rng, n=600):
     """Points that probe a torus's sign: the bounding box (the hole included), within
     0.2-3 mm of the smooth torus on both sides, and around the mesh's vertices and
