@@ -196,6 +196,17 @@ fg_status fg_sdf_destroy(fg_sdf* sdf);
 fg_status fg_sdf_create_mesh(const float* host_vertices, int n_vertices, const int* host_faces, int n_faces,
                              float phong_alpha, float mass, float inertia, fg_sdf** out);
 
+/* Host only, no GPU needed: runs fg_sdf_create_mesh's validation and host build on
+ * the same arguments and reports how much of the mesh the certified local search
+ * can answer.  out6 (host, 6 ints): faces, faces on the convex hull (no vertex
+ * more than 1e-9 of the mesh's extent outside the face's plane), vertices whose
+ * faces form one fan, BVH nodes, BVH depth, nodes of the start-face table.  A query
+ * whose closest feature has a face off the hull, or a vertex not in one fan, takes
+ * the BVH walk.
+ * Errors: FG_ERR_INVALID (with the reason, as fg_sdf_create_mesh). */
+fg_status fg_mesh_describe(const float* host_vertices, int n_vertices, const int* host_faces, int n_faces,
+                           int* host_out6);
+
 /* A scene is an ordered table of objects; candidates select theirs by index
  * (obj_of_cand).  The scene keeps pointers to the objects' grids: destroy the
  * scene before its objects.  Errors: FG_ERR_INVALID, FG_ERR_OOM, FG_ERR_CUDA. */

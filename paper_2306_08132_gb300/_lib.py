@@ -71,6 +71,7 @@ SIGNATURES = {
     "fg_sdf_create": [_vp, _i, _i, _i, C.POINTER(_f), _f, _f, _f, C.POINTER(_vp)],
     "fg_sdf_destroy": [_vp],
     "fg_sdf_create_mesh": [C.POINTER(_f), _i, C.POINTER(_i), _i, _f, _f, _f, C.POINTER(_vp)],
+    "fg_mesh_describe": [C.POINTER(_f), _i, C.POINTER(_i), _i, C.POINTER(_i)],
     "fg_scene_create": [C.POINTER(_vp), _i, C.POINTER(_vp)],
     "fg_scene_destroy": [_vp],
     "fg_fk": [_vp, _vp, _i, _vp, _vp],

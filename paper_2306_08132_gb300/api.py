@@ -115,6 +115,20 @@ class Sdf:
                                      float(mass), float(inertia), C.byref(h)), "fg_sdf_create_mesh")
         return cls(None, _handle=h)
 
+    @staticmethod
+    def describe_mesh(vertices, faces) -> dict:
+        """fg_mesh_describe (host only): how much of a mesh the certified local search covers."""
+        lib = _lib.load()
+        V = np.ascontiguousarray(np.asarray(vertices, dtype=np.float32))
+        F = np.ascontiguousarray(np.asarray(faces, dtype=np.int32))
+        if V.ndim != 2 or V.shape[1] != 3 or F.ndim != 2 or F.shape[1] != 3:
+            raise ValueError("vertices and faces must be [n, 3]")
+        out = (C.c_int * 6)()
+        check(lib.fg_mesh_describe(V.ctypes.data_as(C.POINTER(C.c_float)), V.shape[0],
+                                   F.ctypes.data_as(C.POINTER(C.c_int)), F.shape[0], out), "fg_mesh_describe")
+        keys = ("faces", "hull_faces", "fan_vertices", "bvh_nodes", "bvh_depth", "start_nodes")
+        return dict(zip(keys, [int(x) for x in out]))
+
     @classmethod
     def from_synth(cls, o: dict) -> "Sdf":
         if "faces" in o:

@@ -257,19 +257,34 @@ fg_status mesh_invalid(const std::string& msg) {
 
 using namespace fg;
 
-extern "C" fg_status fg_sdf_create_mesh(const float* vertices, int nv, const int* faces, int nf, float phong_alpha,
-                                        float mass, float inertia, fg_sdf** out) {
-  if (!vertices || !faces || !out) return mesh_invalid("NULL argument");
-  *out = nullptr;
-  if (nv < 4 || nf < 4) return mesh_invalid("a closed mesh needs at least 4 vertices and 4 faces");
-  if (nf > (1 << 24) || nv > (1 << 24)) return mesh_invalid("more than 2^24 vertices or faces");
-  if (!(phong_alpha >= 0.0f && phong_alpha <= 1.0f)) return mesh_invalid("phong_alpha must be in [0, 1]");
-  if (!(mass > 0.0f) || !(inertia > 0.0f) || !std::isfinite(mass) || !std::isfinite(inertia))
-    return mesh_invalid("mass and inertia must be > 0");
+namespace fg {
+
+namespace {
+
+// Everything the host builds for a mesh object: the device image (one float4 array)
+// and where its parts start, the start-face grid, the Phong shift bound, and counts.
+struct MeshBuild {
+  std::vector<float4> buf;
+  size_t tri = 0, nrm = 0, wing = 0, ring = 0, start = 0;   // offsets in float4
+  double blo[3] = {0.0, 0.0, 0.0}, sh = 1.0, shift = 0.0;
+  int sn[3] = {0, 0, 0};
+  int hull_faces = 0, fan_vertices = 0, nodes = 0, depth = 0;
+};
+
+fg_status build_mesh(const char* who, const float* vertices, int nv, const int* faces, int nf, float phong_alpha,
+                     MeshBuild& M) {
+  auto invalid = [&](const std::string& msg) {
+    set_error(std::string(who) + ": " + msg);
+    return FG_ERR_INVALID;
+  };
+  if (!vertices || !faces) return invalid("NULL argument");
+  if (nv < 4 || nf < 4) return invalid("a closed mesh needs at least 4 vertices and 4 faces");
+  if (nf > (1 << 24) || nv > (1 << 24)) return invalid("more than 2^24 vertices or faces");
+  if (!(phong_alpha >= 0.0f && phong_alpha <= 1.0f)) return invalid("phong_alpha must be in [0, 1]");
   std::vector<Vec> V(nv);
   for (int i = 0; i < nv; ++i) {
     const float* p = vertices + 3 * i;
-    if (!std::isfinite(p[0]) || !std::isfinite(p[1]) || !std::isfinite(p[2])) return mesh_invalid("non-finite vertex");
+    if (!std::isfinite(p[0]) || !std::isfinite(p[1]) || !std::isfinite(p[2])) return invalid("non-finite vertex");
     V[i] = {p[0], p[1], p[2]};
   }
   std::vector<int> F(faces, faces + 3 * (size_t)nf);
@@ -282,26 +297,26 @@ extern "C" fg_status fg_sdf_create_mesh(const float* vertices, int nv, const int
   double volume = 0.0;
   for (int f = 0; f < nf; ++f) {
     const int a = F[3 * f], b = F[3 * f + 1], c = F[3 * f + 2];
-    if (a < 0 || b < 0 || c < 0 || a >= nv || b >= nv || c >= nv) return mesh_invalid("face index out of range");
-    if (a == b || b == c || c == a) return mesh_invalid("face with a repeated vertex");
+    if (a < 0 || b < 0 || c < 0 || a >= nv || b >= nv || c >= nv) return invalid("face index out of range");
+    if (a == b || b == c || c == a) return invalid("face with a repeated vertex");
     const Vec n = cross(sub(V[b], V[a]), sub(V[c], V[a]));
-    if (!(norm(n) > 1e-12 * extent * extent)) return mesh_invalid("degenerate (zero-area) face");
+    if (!(norm(n) > 1e-12 * extent * extent)) return invalid("degenerate (zero-area) face");
     fn[f] = unit(n);
     volume += dot(V[a], cross(V[b], V[c])) / 6.0;
     const int e[3][2] = {{a, b}, {b, c}, {c, a}};
     for (int k = 0; k < 3; ++k) {
       const uint64_t key = ((uint64_t)(uint32_t)e[k][0] << 32) | (uint32_t)e[k][1];
       if (!edge_owner.emplace(key, 3 * f + k).second)
-        return mesh_invalid("a directed edge is used twice (inconsistent orientation or non-manifold)");
+        return invalid("a directed edge is used twice (inconsistent orientation or non-manifold)");
     }
   }
-  if (!(volume > 0.0)) return mesh_invalid("faces must be counter-clockwise about the outward normal");
+  if (!(volume > 0.0)) return invalid("faces must be counter-clockwise about the outward normal");
   std::vector<int> across(3 * (size_t)nf);
   for (int f = 0; f < nf; ++f) {
     for (int k = 0; k < 3; ++k) {
       const int u = F[3 * f + k], v = F[3 * f + (k + 1) % 3];
       auto it = edge_owner.find(((uint64_t)(uint32_t)v << 32) | (uint32_t)u);
-      if (it == edge_owner.end()) return mesh_invalid("mesh is not watertight (an edge has one face)");
+      if (it == edge_owner.end()) return invalid("mesh is not watertight (an edge has one face)");
       across[3 * f + k] = it->second / 3;
     }
   }
@@ -466,13 +481,45 @@ extern "C" fg_status fg_sdf_create_mesh(const float* vertices, int nv, const int
           sf[((size_t)z * sn[1] + y) * sn[0] + x] = closest_face(bld, Vec{blo[0] + sh * x, blo[1] + sh * y, blo[2] + sh * z});
     std::memcpy(start, sf.data(), sizeof(int) * nstart);
   }
+  for (int f = 0; f < nf; ++f) M.hull_faces += hull[f] ? 1 : 0;
+  for (int v = 0; v < nv; ++v) M.fan_vertices += (vert_fan[v] && ring_start[v + 1] > ring_start[v]) ? 1 : 0;
+  M.nodes = (int)nn;
+  M.depth = bld.depth_reached;
+  M.tri = tri - bvh;
+  M.nrm = nrm - bvh;
+  M.wing = wing - bvh;
+  M.ring = ring - bvh;
+  M.start = start - bvh;
+  for (int a = 0; a < 3; ++a) {
+    M.blo[a] = blo[a];
+    M.sn[a] = sn[a];
+  }
+  M.sh = sh;
+  M.shift = shift;
+  M.buf = std::move(buf);
+  return FG_OK;
+}
+
+}  // namespace
+
+}  // namespace fg
+
+extern "C" fg_status fg_sdf_create_mesh(const float* vertices, int nv, const int* faces, int nf, float phong_alpha,
+                                        float mass, float inertia, fg_sdf** out) {
+  if (!vertices || !faces || !out) return mesh_invalid("NULL argument");
+  *out = nullptr;
+  if (!(mass > 0.0f) || !(inertia > 0.0f) || !std::isfinite(mass) || !std::isfinite(inertia))
+    return mesh_invalid("mass and inertia must be > 0");
+  MeshBuild M;
+  const fg_status st = build_mesh("fg_sdf_create_mesh", vertices, nv, faces, nf, phong_alpha, M);
+  if (st != FG_OK) return st;
   fg_sdf* s = new (std::nothrow) fg_sdf;
   if (!s) return FG_ERR_OOM;
   std::memset(s, 0, sizeof(*s));
-  s->bytes = sizeof(float4) * buf.size();
+  s->bytes = sizeof(float4) * M.buf.size();
   float4* dev = nullptr;
   cudaError_t e = cudaMalloc(&dev, s->bytes);
-  if (e == cudaSuccess) e = cudaMemcpy(dev, buf.data(), s->bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dev, M.buf.data(), s->bytes, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     cudaFree(dev);
     delete s;
@@ -483,22 +530,39 @@ extern "C" fg_status fg_sdf_create_mesh(const float* vertices, int nv, const int
   o.kind = kObjMesh;
   o.n_faces = nf;
   o.phong_alpha = phong_alpha;
-  o.phong_shift = (float)(shift * (1.0 + 1e-5)) + 1e-7f;
+  o.phong_shift = (float)(M.shift * (1.0 + 1e-5)) + 1e-7f;
   o.bvh = dev;
-  o.tri = dev + (tri - bvh);
-  o.face_nrm = dev + (nrm - bvh);
-  o.wing = dev + (wing - bvh);
-  o.ring = dev + (ring - bvh);
-  o.start_face = reinterpret_cast<const int*>(dev + (start - bvh));
+  o.tri = dev + M.tri;
+  o.face_nrm = dev + M.nrm;
+  o.wing = dev + M.wing;
+  o.ring = dev + M.ring;
+  o.start_face = reinterpret_cast<const int*>(dev + M.start);
   for (int a = 0; a < 3; ++a) {
-    o.start_org[a] = (float)blo[a];
-    o.start_n[a] = sn[a];
+    o.start_org[a] = (float)M.blo[a];
+    o.start_n[a] = M.sn[a];
   }
-  o.start_inv_h = (float)(1.0 / sh);
+  o.start_inv_h = (float)(1.0 / M.sh);
   o.inv_mass = 1.0f / mass;
   o.inv_inertia = 1.0f / inertia;
   o.h = 1.0f;          // unused by mesh queries
   o.inv_h = 1.0f;
   *out = s;
+  return FG_OK;
+}
+
+extern "C" fg_status fg_mesh_describe(const float* vertices, int nv, const int* faces, int nf, int* out6) {
+  if (!out6) {
+    set_error("fg_mesh_describe: NULL argument");
+    return FG_ERR_INVALID;
+  }
+  MeshBuild M;
+  const fg_status st = build_mesh("fg_mesh_describe", vertices, nv, faces, nf, 0.0f, M);
+  if (st != FG_OK) return st;
+  out6[0] = nf;
+  out6[1] = M.hull_faces;
+  out6[2] = M.fan_vertices;
+  out6[3] = M.nodes;
+  out6[4] = M.depth;
+  out6[5] = M.sn[0] * M.sn[1] * M.sn[2];
   return FG_OK;
 }

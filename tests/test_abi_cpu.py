@@ -142,3 +142,41 @@ def test_valid_meshes_pass_host_validation(lib):
             assert lib.fg_sdf_destroy(out) == 0
         else:
             assert st == 5 and b"device copy" in _last(lib), (m["kind"], st, _last(lib))
+
+
+def test_mesh_description_on_the_host(lib):
+    """fg_mesh_describe runs the mesh build on the host: on a convex superquadric mesh (outward-folding quad
+    diagonals) and a convex hull every face is on the hull and every vertex's faces form one fan; on a torus
+    the inner half is off the hull; on two tetrahedra sharing a vertex, that vertex has two fans; invalid
+    meshes are refused with the creation call's messages."""
+    import numpy as np
+    from synth import meshes as SM
+    import paper_2306_08132_gb300 as fg
+
+    def desc(m):
+        return fg.Sdf.describe_mesh(m["vertices"], m["faces"])
+
+    sq = SM.superquadric_mesh((0.05, 0.03, 0.04), 0.7, 1.3, 24, 48)
+    d = desc(sq)
+    assert d["faces"] == len(sq["faces"]) == d["hull_faces"]
+    assert d["fan_vertices"] == len(sq["vertices"])
+    assert d["bvh_nodes"] >= 2 * (d["faces"] // 4) - 1 and 1 <= d["bvh_depth"] <= 48
+    assert 2 <= d["start_nodes"] <= 32 ** 3
+    hull = SM.hull_mesh(np.random.default_rng(3).normal(size=(60, 3)) * 0.04)
+    assert desc(hull)["hull_faces"] == len(hull["faces"])
+    torus = SM.torus_mesh(0.04, 0.015, 24, 12)
+    dt = desc(torus)
+    assert 0 < dt["hull_faces"] < len(torus["faces"]) // 2 + len(torus["faces"]) // 4
+    assert dt["fan_vertices"] == len(torus["vertices"])
+    s = 0.03
+    V = np.array([(0, 0, 0), (s, 0, s), (s, s, -s), (s, -s, -s), (-s, 0, s), (-s, -s, -s), (-s, s, -s)], np.float32)
+    F = np.array([(0, 1, 2), (0, 2, 3), (0, 3, 1), (1, 3, 2), (0, 4, 5), (0, 5, 6), (0, 6, 4), (4, 6, 5)])
+    for t in range(len(F)):                       # each face away from its tetrahedron's centroid
+        A, B, Cc = V[F[t]].astype(np.float64)
+        cen = V[[1, 2, 3]].mean(0) if 1 in F[t] or 2 in F[t] or 3 in F[t] else V[[4, 5, 6]].mean(0)
+        if np.cross(B - A, Cc - A) @ ((A + B + Cc) / 3 - cen) < 0:
+            F[t] = F[t][[0, 2, 1]]
+    db = fg.Sdf.describe_mesh(V, F)
+    assert db["fan_vertices"] == len(V) - 1            # the shared vertex: two fans
+    with pytest.raises(Exception, match="watertight"):
+        fg.Sdf.describe_mesh(sq["vertices"], sq["faces"][:-1])
